@@ -1,0 +1,145 @@
+"""CPU oracle for the progressive spatio-temporal filtering hot path.
+
+TEST INFRASTRUCTURE ONLY: the test suite, the package smoke check and the
+benchmark's CPU-baseline leg are the only callers.  The product path never
+imports this package and shares no code with it.  See psf_oracle.cpp for the
+definitions it follows and how each function is pinned.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "psf_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+STATUS_TABLE_FULL = 1
+STATUS_RANGE = 2
+
+RECORD_DTYPE = np.dtype([("key", "<u8"), ("sum", "<i8", (3,)), ("c_new", "<i8"), ("c_old", "<i8"),
+                         ("L", "<f8", (3,))])
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("pos_bits_q", ctypes.c_uint32), ("dir_bits_d", ctypes.c_uint32),
+                ("use_normal", ctypes.c_uint32), ("frac_bits", ctypes.c_uint32),
+                ("blend_mode", ctypes.c_uint32), ("cv_max_depth", ctypes.c_uint32),
+                ("alpha_min", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with g++ (IEEE single-rounding semantics: no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               _SRC, "-o", _LIB + ".tmp"]
+        subprocess.run(cmd, check=True)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+        L.oracle_create.restype = vp
+        L.oracle_create.argtypes = [ctypes.POINTER(_Config)]
+        L.oracle_destroy.argtypes = [vp]
+        L.oracle_key.restype = ctypes.c_int
+        L.oracle_key.argtypes = [ctypes.POINTER(_Config), vp, ctypes.POINTER(u64)]
+        L.oracle_insert.restype = u32
+        L.oracle_insert.argtypes = [vp, vp, u64]
+        L.oracle_update.restype = u32
+        L.oracle_update.argtypes = [vp]
+        L.oracle_reset.argtypes = [vp]
+        L.oracle_query_cv.argtypes = [vp, vp, u32, u32, vp]
+        L.oracle_size.restype = u64
+        L.oracle_size.argtypes = [vp]
+        L.oracle_counters.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.oracle_export.restype = u64
+        L.oracle_export.argtypes = [vp, vp, u64]
+        L.oracle_import.argtypes = [vp, vp, u64]
+        _lib = L
+    return _lib
+
+
+def make_config(pos_bits: int = 4, dir_bits: int = 2, use_normal: bool = True, frac_bits: int = 24,
+                blend_mode: int = 0, cv_max_depth: int = 0xFFFFFFFF, alpha_min: float = 0.1,
+                beta: float = 1.0) -> _Config:
+    return _Config(pos_bits, dir_bits, int(bool(use_normal)), frac_bits, blend_mode, cv_max_depth,
+                   float(alpha_min), float(beta))
+
+
+def _verts(v: np.ndarray) -> np.ndarray:
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    if v.ndim != 2 or v.shape[1] != 16:
+        raise ValueError("vertices must be (n, 16) float32")
+    return v
+
+
+def vertex_key(cfg: _Config, v16) -> int | None:
+    """Packed cell key of one vertex record, or None if the vertex has no valid cell."""
+    v = np.ascontiguousarray(v16, dtype=np.float32).reshape(16)
+    out = ctypes.c_uint64()
+    ok = lib().oracle_key(ctypes.byref(cfg), v.ctypes.data, ctypes.byref(out))
+    return int(out.value) if ok else None
+
+
+class Oracle:
+    """std::map-backed reference table (one render session)."""
+
+    def __init__(self, cfg: _Config | None = None, **kw):
+        self.cfg = cfg if cfg is not None else make_config(**kw)
+        self._h = lib().oracle_create(ctypes.byref(self.cfg))
+        if not self._h:
+            raise ValueError("invalid oracle configuration")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().oracle_destroy(h)
+            self._h = None
+
+    def insert(self, verts: np.ndarray) -> int:
+        v = _verts(verts)
+        return int(lib().oracle_insert(self._h, v.ctypes.data, v.shape[0]))
+
+    def update(self) -> int:
+        return int(lib().oracle_update(self._h))
+
+    def reset(self) -> None:
+        lib().oracle_reset(self._h)
+
+    def query_cv(self, verts: np.ndarray, P: int, D: int) -> np.ndarray:
+        v = _verts(verts)
+        if v.shape[0] != P * D:
+            raise ValueError("vertex count must be P*D")
+        out = np.empty((P * D, 3), dtype=np.float64)
+        lib().oracle_query_cv(self._h, v.ctypes.data, P, D, out.ctypes.data)
+        return out
+
+    def __len__(self) -> int:
+        return int(lib().oracle_size(self._h))
+
+    def counters(self) -> tuple[int, int]:
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        lib().oracle_counters(self._h, ctypes.byref(a), ctypes.byref(b))
+        return int(a.value), int(b.value)
+
+    def export(self) -> np.ndarray:
+        n = len(self)
+        out = np.zeros(n, dtype=RECORD_DTYPE)
+        got = lib().oracle_export(self._h, out.ctypes.data, n)
+        return out[:got]
+
+    def import_records(self, recs: np.ndarray) -> None:
+        r = np.ascontiguousarray(recs, dtype=RECORD_DTYPE)
+        lib().oracle_import(self._h, r.ctypes.data, r.shape[0])

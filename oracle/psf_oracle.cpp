@@ -1,0 +1,347 @@
+// psf_oracle.cpp -- CPU oracle for the progressive spatio-temporal filtering hot path.
+//
+// TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and the
+// benchmark's CPU-baseline leg may load this library.  It shares no code, header,
+// table or constant generator with the CUDA library: everything below is written
+// out again from the paper's definitions.  Inputs come from the seeded generator
+// module or from the tests themselves, never from the CUDA path.
+//
+// It is deliberately plain and slow: a std::map keyed by the full quantised cell
+// tuple, one vertex at a time, FP64 blend and FP64 control variate.
+//
+// Passages followed (Pantaleoni, "Online path sampling control with progressive
+// spatio-temporal filtering"):
+//   * cell keys: Section "Basis functions and data structures: spatio-directional
+//     hashing" -- basis functions are a grid over position times a grid over the
+//     outgoing direction omega_o (the normal bin is an optional extra key field);
+//   * accumulation: eq. (5) (c_h = sum of b_h * w) and eq. (6) (weighted sum of the
+//     vertex values), in the order of Alg. 1 (increment_counters / update_approx);
+//   * blend: Section "Temporal averaging", eq. (10) and eq. (11), with the global
+//     counter reset described after eq. (11);
+//   * query: Section "Control variates", equation CVEstimator, restated in the
+//     estimator-value form out = L - beta * (t * C_next) + beta * C_self.
+//
+// Precision: the decisions that produce integers (cell indices, direction bins,
+// fixed-point codes) are taken in FP32 with one correctly rounded IEEE operation
+// per step, in the order written below, because the kernel takes them in FP32.
+// This file must be compiled with -ffp-contract=off and without -ffast-math.
+// Everything downstream of the integer sums (blend, query) is FP64.
+//
+// Parity status: every function is pinned by the CPU test suite (brute force,
+// sum invariants, constant field, blend closed form, control-variate mean,
+// hand-derived keys, octahedral decode/encode round trip).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+namespace {
+
+constexpr uint32_t ST_TABLE_FULL = 1u;  // not produced by the oracle (unbounded map)
+constexpr uint32_t ST_RANGE = 2u;
+
+struct Config {
+    uint32_t pos_bits_q;
+    uint32_t dir_bits_d;
+    uint32_t use_normal;
+    uint32_t frac_bits;
+    uint32_t blend_mode;  // 0: eq. (11) square-root hybrid; 1: constant alpha = alpha_min
+    uint32_t cv_max_depth;
+    double alpha_min;
+    double beta;
+};
+
+// (level, normal bin, direction bin u, direction bin v, cell x, cell y, cell z);
+// cell indices are stored biased by 2^15 so that they are non-negative.
+using CellKey = std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t>;
+
+struct Cell {
+    int64_t sum[3] = {0, 0, 0};  // this iteration: sum of round(w * L_c * 2^F)
+    int64_t c_new = 0;           // this iteration: sum of round(w * 2^F)   (eq. 5)
+    int64_t c_old = 0;           // all earlier iterations (eq. 10-11)
+    double L[3] = {0.0, 0.0, 0.0};  // the approximant L~_{o,h}
+};
+
+struct Oracle {
+    Config cfg;
+    std::map<CellKey, Cell> cells;
+    uint64_t dropped = 0;       // vertices rejected by the range rule
+    uint64_t zero_weight = 0;   // vertices whose weight rounds to zero in fixed point
+};
+
+bool finite3(const float* a) { return std::isfinite(a[0]) && std::isfinite(a[1]) && std::isfinite(a[2]); }
+
+// floor(p * 2^q) for one coordinate; false when outside the 16-bit biased range.
+bool cell_index(float p, uint32_t q, uint32_t* biased) {
+    double t = std::floor(static_cast<double>(p) * std::ldexp(1.0, static_cast<int>(q)));
+    if (t < -32768.0 || t > 32767.0) return false;
+    *biased = static_cast<uint32_t>(static_cast<int64_t>(t) + 32768);
+    return true;
+}
+
+// Dominant axis of the normal (ties prefer x, then y) and its sign: 2*axis + (negative).
+uint32_t normal_bin(float nx, float ny, float nz) {
+    float ax = std::fabs(nx), ay = std::fabs(ny), az = std::fabs(nz);
+    if (ax >= ay && ax >= az) return nx >= 0.0f ? 0u : 1u;
+    if (ay >= az) return ny >= 0.0f ? 2u : 3u;
+    return nz >= 0.0f ? 4u : 5u;
+}
+
+// Octahedral map of a direction onto [-1,1]^2 followed by a 2^d x 2^d grid.
+// Upper hemisphere (z >= 0): (u, v) = (x, y) / (|x| + |y| + |z|).
+// Lower hemisphere: the triangles are folded outwards,
+//   (u, v) <- ((1 - |v|) * sgn(u), (1 - |u|) * sgn(v)), with sgn(0) = +1.
+// Bin = floor((u + 1) * 2^(d-1)), clamped to [0, 2^d - 1].
+bool direction_bins(float wx, float wy, float wz, uint32_t d, uint32_t* bu, uint32_t* bv) {
+    float ax = std::fabs(wx), ay = std::fabs(wy), az = std::fabs(wz);
+    float s = ax + ay;
+    s = s + az;
+    if (!(s > 0.0f) || !std::isfinite(s)) return false;
+    float u = wx / s;
+    float v = wy / s;
+    if (wz < 0.0f) {
+        float su = (u >= 0.0f) ? 1.0f : -1.0f;
+        float sv = (v >= 0.0f) ? 1.0f : -1.0f;
+        float fu = 1.0f - std::fabs(v);
+        float fv = 1.0f - std::fabs(u);
+        u = fu * su;
+        v = fv * sv;
+    }
+    const float half = std::ldexp(1.0f, static_cast<int>(d) - 1);
+    const int top = (1 << d) - 1;
+    float gu = u + 1.0f;
+    float gv = v + 1.0f;
+    gu = gu * half;
+    gv = gv * half;
+    int iu = static_cast<int>(std::floor(gu));
+    int iv = static_cast<int>(std::floor(gv));
+    *bu = static_cast<uint32_t>(std::min(std::max(iu, 0), top));
+    *bv = static_cast<uint32_t>(std::min(std::max(iv, 0), top));
+    return true;
+}
+
+// The basis function b_h a vertex lands on (a single cell: b_h is an indicator).
+bool vertex_cell(const Config& c, const float* v, CellKey* key) {
+    const float* p = v;
+    const float* n = v + 4;
+    const float* d = v + 8;
+    if (!finite3(p) || !finite3(n) || !finite3(d)) return false;
+    uint32_t bx, by, bz;
+    if (!cell_index(p[0], c.pos_bits_q, &bx) || !cell_index(p[1], c.pos_bits_q, &by) ||
+        !cell_index(p[2], c.pos_bits_q, &bz))
+        return false;
+    uint32_t nb = c.use_normal ? normal_bin(n[0], n[1], n[2]) : 0u;
+    uint32_t bu, bv;
+    // omega_o = -d (Alg. 1: the outgoing direction is the reversed incoming ray)
+    if (!direction_bins(-d[0], -d[1], -d[2], c.dir_bits_d, &bu, &bv)) return false;
+    *key = CellKey(0u, nb, bu, bv, bx, by, bz);
+    return true;
+}
+
+uint64_t pack_key(const Config& c, const CellKey& k) {
+    uint64_t level = std::get<0>(k), nb = std::get<1>(k), bu = std::get<2>(k), bv = std::get<3>(k);
+    uint64_t bx = std::get<4>(k), by = std::get<5>(k), bz = std::get<6>(k);
+    uint64_t dbin = (bu << c.dir_bits_d) | bv;
+    return (level << 61) | (nb << 58) | (dbin << 48) | (bx << 32) | (by << 16) | bz;
+}
+
+int64_t sat_add(int64_t a, int64_t b) {
+    // both operands are non-negative counters
+    if (a > INT64_MAX - b) return INT64_MAX;
+    return a + b;
+}
+
+}  // namespace
+
+extern "C" {
+
+typedef struct {
+    uint32_t pos_bits_q;
+    uint32_t dir_bits_d;
+    uint32_t use_normal;
+    uint32_t frac_bits;
+    uint32_t blend_mode;
+    uint32_t cv_max_depth;
+    double alpha_min;
+    double beta;
+} oracle_config;
+
+typedef struct {
+    uint64_t key;
+    int64_t sum[3];
+    int64_t c_new;
+    int64_t c_old;
+    double L[3];
+} oracle_record;
+
+void* oracle_create(const oracle_config* cfg) {
+    if (!cfg || cfg->dir_bits_d > 5 || cfg->pos_bits_q > 20 || cfg->frac_bits < 8 || cfg->frac_bits > 32)
+        return nullptr;
+    Oracle* o = new Oracle();
+    std::memcpy(&o->cfg, cfg, sizeof(Config));
+    return o;
+}
+
+void oracle_destroy(void* h) { delete static_cast<Oracle*>(h); }
+
+// Packed key of one 16-float vertex record; returns 1 if the vertex has a cell.
+int oracle_key(const oracle_config* cfg, const float* v, uint64_t* key) {
+    Config c;
+    std::memcpy(&c, cfg, sizeof(Config));
+    CellKey k;
+    if (!vertex_cell(c, v, &k)) return 0;
+    *key = pack_key(c, k);
+    return 1;
+}
+
+// Scatter n vertices (eq. 5 and 6 accumulated in fixed point).  Returns status bits.
+uint32_t oracle_insert(void* h, const float* verts, uint64_t n) {
+    Oracle* o = static_cast<Oracle*>(h);
+    const Config& c = o->cfg;
+    const double scale = std::ldexp(1.0, static_cast<int>(c.frac_bits));
+    uint32_t status = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        const float* v = verts + 16 * i;
+        CellKey key;
+        bool ok = vertex_cell(c, v, &key);
+        const float w = v[3];
+        ok = ok && (w >= 0.0f) && (w <= 32768.0f);
+        float prod[3] = {0.0f, 0.0f, 0.0f};
+        for (int ch = 0; ch < 3 && ok; ++ch) {
+            prod[ch] = w * v[12 + ch];  // one FP32 rounding of w * L_c
+            ok = std::isfinite(prod[ch]) && std::fabs(prod[ch]) <= 32768.0f;
+        }
+        if (!ok) {
+            status |= ST_RANGE;
+            o->dropped++;
+            continue;
+        }
+        const int64_t cw = std::llrint(static_cast<double>(w) * scale);
+        if (cw == 0) {
+            o->zero_weight++;
+            continue;
+        }
+        Cell& cell = o->cells[key];
+        for (int ch = 0; ch < 3; ++ch) cell.sum[ch] += std::llrint(static_cast<double>(prod[ch]) * scale);
+        cell.c_new += cw;
+    }
+    return status;
+}
+
+// End-of-iteration temporal blend, eq. (10)-(11), for every cell touched this iteration.
+uint32_t oracle_update(void* h) {
+    Oracle* o = static_cast<Oracle*>(h);
+    const Config& c = o->cfg;
+    for (auto& kv : o->cells) {
+        Cell& cell = kv.second;
+        if (cell.c_new == 0) continue;  // not touched this iteration: left as it is
+        const double cn = static_cast<double>(cell.c_new);
+        const double co = static_cast<double>(cell.c_old);
+        double alpha;
+        if (c.blend_mode == 0)
+            alpha = std::max(std::sqrt(cn / (co + cn)), c.alpha_min);
+        else
+            alpha = c.alpha_min;
+        for (int ch = 0; ch < 3; ++ch) {
+            const double mean = static_cast<double>(cell.sum[ch]) / cn;
+            cell.L[ch] = (1.0 - alpha) * cell.L[ch] + alpha * mean;
+            cell.sum[ch] = 0;
+        }
+        cell.c_old = sat_add(cell.c_old, cell.c_new);
+        cell.c_new = 0;
+    }
+    return 0;
+}
+
+// Global counter reset (the text after eq. (11)): c_old := 0 everywhere, approximant kept.
+void oracle_reset(void* h) {
+    Oracle* o = static_cast<Oracle*>(h);
+    for (auto& kv : o->cells) kv.second.c_old = 0;
+}
+
+// Control-variate query (Section "Control variates", equation CVEstimator) for P paths of
+// depth D in depth-major order; out receives D*P*3 doubles in the same order.
+// For vertex j of a path, C_j is the approximant of the cell the vertex lands on (0 when the
+// cell is absent) and t_j the RGB throughput to vertex j+1:
+//   out_j = L_j - beta * t_j * C_{j+1} + beta * C_j   for j < min(D - 1, cv_max_depth),
+//   out_j = L_j                                        otherwise.
+void oracle_query_cv(void* h, const float* verts, uint32_t P, uint32_t D, double* out) {
+    Oracle* o = static_cast<Oracle*>(h);
+    const Config& c = o->cfg;
+    for (uint64_t p = 0; p < P; ++p) {
+        double C_next[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = static_cast<int64_t>(D) - 1; j >= 0; --j) {
+            const uint64_t idx = static_cast<uint64_t>(j) * P + p;
+            const float* v = verts + 16 * idx;
+            double C[3] = {0.0, 0.0, 0.0};
+            CellKey key;
+            if (vertex_cell(c, v, &key)) {
+                auto it = o->cells.find(key);
+                if (it != o->cells.end())
+                    for (int ch = 0; ch < 3; ++ch) C[ch] = it->second.L[ch];
+            }
+            const double t[3] = {v[7], v[11], v[15]};
+            const bool cv = (j + 1 < static_cast<int64_t>(D)) && (static_cast<uint64_t>(j) < c.cv_max_depth);
+            for (int ch = 0; ch < 3; ++ch) {
+                const double L = v[12 + ch];
+                out[3 * idx + ch] = cv ? (L - c.beta * (t[ch] * C_next[ch]) + c.beta * C[ch]) : L;
+            }
+            for (int ch = 0; ch < 3; ++ch) C_next[ch] = C[ch];
+        }
+    }
+}
+
+uint64_t oracle_size(void* h) { return static_cast<Oracle*>(h)->cells.size(); }
+
+void oracle_counters(void* h, uint64_t* dropped, uint64_t* zero_weight) {
+    Oracle* o = static_cast<Oracle*>(h);
+    *dropped = o->dropped;
+    *zero_weight = o->zero_weight;
+}
+
+// All cells in ascending packed-key order; returns the number written (at most cap).
+uint64_t oracle_export(void* h, oracle_record* out, uint64_t cap) {
+    Oracle* o = static_cast<Oracle*>(h);
+    uint64_t i = 0;
+    for (const auto& kv : o->cells) {
+        if (i >= cap) break;
+        oracle_record& r = out[i++];
+        r.key = pack_key(o->cfg, kv.first);
+        for (int ch = 0; ch < 3; ++ch) {
+            r.sum[ch] = kv.second.sum[ch];
+            r.L[ch] = kv.second.L[ch];
+        }
+        r.c_new = kv.second.c_new;
+        r.c_old = kv.second.c_old;
+    }
+    return i;
+}
+
+// Import cells (for setting up query cases directly): records with the same meaning as export.
+// The packed key is unpacked with this file's own layout.
+void oracle_import(void* h, const oracle_record* recs, uint64_t n) {
+    Oracle* o = static_cast<Oracle*>(h);
+    const uint32_t d = o->cfg.dir_bits_d;
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t k = recs[i].key;
+        const uint32_t dbin = static_cast<uint32_t>((k >> 48) & 0x3FFu);
+        CellKey key(static_cast<uint32_t>((k >> 61) & 3u), static_cast<uint32_t>((k >> 58) & 7u),
+                    dbin >> d, dbin & ((1u << d) - 1u), static_cast<uint32_t>((k >> 32) & 0xFFFFu),
+                    static_cast<uint32_t>((k >> 16) & 0xFFFFu), static_cast<uint32_t>(k & 0xFFFFu));
+        Cell& cell = o->cells[key];
+        for (int ch = 0; ch < 3; ++ch) {
+            cell.sum[ch] = recs[i].sum[ch];
+            cell.L[ch] = recs[i].L[ch];
+        }
+        cell.c_new = recs[i].c_new;
+        cell.c_old = recs[i].c_old;
+    }
+}
+
+uint32_t oracle_status_range() { return ST_RANGE; }
+uint32_t oracle_status_table_full() { return ST_TABLE_FULL; }
+
+}  // extern "C"
