@@ -1,0 +1,445 @@
+"""Benchmark: path vertices filtered per second (insert + update + query per iteration).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl psf|reference]
+
+One step is one whole iteration of the hot path (psf_insert, psf_update,
+psf_query_cv) over one batch of synthetic path vertices shaped like a 1280x720,
+1-spp, depth-4 path tracer's output (3,686,400 vertices; each step gets a fresh
+236 MB batch, larger than the 126 MB L2).  Under torchrun every rank runs its own
+render session on its own GPU (weak scaling, no collective on the data path); the
+step time is the maximum over ranks.
+
+--impl reference times the CPU oracle (test infrastructure: a single-threaded
+std::map implementation) on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "path vertices filtered/sec (insert+update+query)"
+UNIT = "vertices/s"
+DEFAULT_WORKLOAD = "1280x720_d4"
+KERNEL_SOURCES = ["paper_2005_07547_b300/csrc/psf.cu", "paper_2005_07547_b300/csrc/psf_device.cuh"]
+
+
+# ---------------------------------------------------------------------------
+# helpers shared with the tests (host logic only)
+# ---------------------------------------------------------------------------
+
+def dist_env() -> tuple[int, int, int]:
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def rank_seed_offset(rank: int) -> int:
+    """Each rank renders its own session: iterations are drawn from a disjoint range."""
+    return 100000 * rank
+
+
+def aggregate(per_rank_ms: list[float], vertices_per_step_per_rank: int, steps: int, world: int) -> dict:
+    """Whole-job throughput: every rank's vertices over the slowest rank's time."""
+    t_ms = max(per_rank_ms)
+    total = vertices_per_step_per_rank * steps * world
+    return {"ms_per_step": t_ms / steps, "value": total / (t_ms / 1e3)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_bytes(V: int, touched: float, cache_fp16: bool) -> dict:
+    """Bytes each kernel must move at minimum (per launch).
+
+    insert: read the 64-B vertex record of every vertex; per touched cell read its
+            8-B key and read-modify-write its 32-B accumulator (8 + 64).
+    update: per touched cell read + zero the 32-B accumulator, read + write the 16-B
+            approximant and the 8-B c_old, write the 8-B FP16 copy (112 or 120).
+    query:  read the 64-B record and write the 12-B output of every vertex; per
+            touched cell read its key and its approximant (8 + 16, or 8 + 8 for FP16).
+    """
+    return {
+        "k_insert": 64.0 * V + 72.0 * touched,
+        "k_update": (120.0 if cache_fp16 else 112.0) * touched,
+        "k_query": 76.0 * V + (16.0 if cache_fp16 else 24.0) * touched,
+    }
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "source": "fallback"}
+
+
+def load_traffic(kernel: str) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return float(k["bytes_per_launch"]) if k else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        sm.append(float(parts[1]))
+                        mx.append(float(parts[2]))
+                    except ValueError:
+                        continue
+                    for name, val in zip(names, parts[5:9]):
+                        if val.lower() == "active":
+                            reasons.add(name)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# input generation (host, seeded; before any CUDA work)
+# ---------------------------------------------------------------------------
+
+def _gen_one(args):
+    name, iteration = args
+    from synth.scene import iteration_vertices, workload
+
+    return iteration_vertices(workload(name), iteration)
+
+
+def generate(name: str, iterations: list[int], procs: int) -> list[np.ndarray]:
+    if procs <= 1 or len(iterations) == 1:
+        return [_gen_one((name, it)) for it in iterations]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(procs, len(iterations))) as pool:
+        return pool.map(_gen_one, [(name, it) for it in iterations])
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample
+# ---------------------------------------------------------------------------
+
+def oracle_rate(w: dict, batches: list[np.ndarray], budget_s: float = 20.0) -> dict:
+    import oracle
+
+    P, D = w["width"] * w["height"], w["depth"]
+    o = oracle.Oracle(pos_bits=w["pos_bits"], dir_bits=w["dir_bits"], alpha_min=float(np.float32(w["alpha_min"])))
+    done = 0
+    t0 = time.perf_counter()
+    for v in batches:
+        o.insert(v)
+        o.update()
+        o.query_cv(v, P, D)
+        done += v.shape[0]
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done // v.shape[0]} iterations ({done} vertices) of {w['name']}, std::map oracle, "
+                      f"insert+update+query, single thread, {dt:.1f} s"}
+
+
+def run_reference(args) -> None:
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from synth.scene import workload
+
+    w = workload(args.workload)
+    batches = generate(args.workload, list(range(args.warmup + args.steps)), os.cpu_count() or 1)
+    # warm-up steps: untimed oracle iterations (bounded)
+    import oracle
+
+    P, D = w["width"] * w["height"], w["depth"]
+    o = oracle.Oracle(pos_bits=w["pos_bits"], dir_bits=w["dir_bits"], alpha_min=float(np.float32(w["alpha_min"])))
+    for v in batches[:min(args.warmup, 1)]:
+        o.insert(v)
+        o.update()
+        o.query_cv(v, P, D)
+    # each timed step is a bounded sample: the first 1/8 of the paths of that iteration
+    frac_paths = max(1, P // 8)
+    times = []
+    done = 0
+    for v in batches[args.warmup:args.warmup + args.steps]:
+        sample = v.reshape(D, P, 16)[:, :frac_paths].reshape(-1, 16).copy()
+        t0 = time.perf_counter()
+        o.insert(sample)
+        o.update()
+        o.query_cv(sample, frac_paths, D)
+        times.append(time.perf_counter() - t0)
+        done += sample.shape[0]
+    total = sum(times)
+    value = done / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "paths": P, "depth": D, "vertices_per_step": frac_paths * D,
+                   "sample": f"first {frac_paths} of {P} paths per iteration"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} iterations x {frac_paths} paths x depth {D} of {w['name']}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_psf(args) -> None:
+    rank, world, local = dist_env()
+    from synth.scene import workload
+
+    w = workload(args.workload)
+    P, D = w["width"] * w["height"], w["depth"]
+    V = P * D
+    off = rank_seed_offset(rank)
+    n_iter = args.warmup + args.steps
+    host = generate(args.workload, [off + i for i in range(n_iter)], os.cpu_count() or 1)
+    cpu_sample = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_sample = host[:3]
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2005_07547_b300 as psf
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    psf.load()
+    cfg = psf.make_config(log2_capacity=w["log2_capacity"], pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],
+                          alpha_min=w["alpha_min"], cache_fp16=args.fp16 or w["cache_fp16"])
+    table = psf.Table(cfg)
+    dev = [torch.from_numpy(v).cuda() for v in host]
+    out = torch.empty((V, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for k in range(args.warmup):
+        table.insert(dev[k])
+        table.update()
+        table.query_cv(dev[k], P, D, out=out)
+    torch.cuda.synchronize()
+    before = table.stats()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        for k in range(args.steps):
+            v = dev[args.warmup + k]
+            e = ev[k]
+            e[0].record(stream)
+            table.insert(v)
+            e[1].record(stream)
+            table.update()
+            e[2].record(stream)
+            table.query_cv(v, P, D, out=out)
+            e[3].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    elapsed_ms = start.elapsed_time(end)
+    after = table.stats()
+    if after["status"] != 0:
+        raise RuntimeError(f"device status {after['status']} during the benchmark")
+
+    kt = {"k_insert": [e[0].elapsed_time(e[1]) for e in ev], "k_update": [e[1].elapsed_time(e[2]) for e in ev],
+          "k_query": [e[2].elapsed_time(e[3]) for e in ev]}
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    touched = (after["touched_cells"] - before["touched_cells"]) / args.steps
+
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+        gathered = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(gathered, t)
+        per_rank = [float(x.item()) for x in gathered]
+    else:
+        per_rank = [elapsed_ms]
+    agg = aggregate(per_rank, V, args.steps, world)
+
+    # end to end through the public API: pinned host vertices in, host CV outputs back,
+    # copies inside the timed region, H2D of step k+1 overlapped with compute of step k
+    e2e = run_e2e(psf, table, host, P, D, args.e2e_steps) if rank == 0 else None
+
+    peaks = load_peaks()
+    fp16 = bool(cfg.cache_fp16)
+    alg = algorithmic_bytes(V, touched, fp16)
+    avg = {k: sum(v) / len(v) for k, v in kt.items()}
+    dominant = max(avg, key=avg.get)
+    achieved = alg[dominant] / (avg[dominant] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
+                "algorithmic_bytes_per_launch": alg[dominant], "traffic": load_traffic(dominant)}
+    kernels = {k: {"avg_ms": avg[k], "share": avg[k] / sum(avg.values()),
+                   "algorithmic_GBps": alg[k] / (avg[k] / 1e3) / 1e9,
+                   "frac_of_hbm": alg[k] / (avg[k] / 1e3) / 1e9 / peaks["hbm_gbs"]} for k in avg}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        table.close()
+        return
+    line = {
+        "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": agg["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+i64 fixed point", "data": "synthetic",
+        "config": {"workload": w["name"], "paths": P, "depth": D, "vertices_per_step": V,
+                   "log2_capacity": w["log2_capacity"], "cache": "fp16" if fp16 else "fp32",
+                   "touched_cells_per_step": touched, "live_cells": after["live_cells"],
+                   "l2": "inputs larger than L2: a fresh 236 MB vertex batch every step",
+                   "parallelism": f"sessions x{world}"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "mean": float(np.mean(step_ms))},
+        "roofline": roofline,
+        "kernels": kernels,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+    }
+    if cpu_sample is not None:
+        line["cpu_baseline"] = oracle_rate(w, cpu_sample)
+    print(json.dumps(line), flush=True)
+    table.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(psf, table, host: list[np.ndarray], P: int, D: int, steps: int) -> dict:
+    """Vertices/s through Table.insert/update/query_cv with host buffers: each step copies its
+    batch from pinned host memory and reads the CV outputs back into pinned host memory."""
+    import torch
+
+    V = P * D
+    nb = min(len(host), 3)
+    pinned = [torch.from_numpy(host[i]).pin_memory() for i in range(nb)]
+    out_host = [torch.empty((V, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
+    dev_in = [torch.empty((V, 16), dtype=torch.float32, device="cuda") for _ in range(2)]
+    dev_out = [torch.empty((V, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    compute = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    ready = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(compute)
+    for s in range(steps + 1):
+        b = s % 2
+        if s < steps:  # stage step s on the copy stream
+            with torch.cuda.stream(copy):
+                if s >= 2:
+                    copy.wait_event(free[b])
+                dev_in[b].copy_(pinned[s % nb], non_blocking=True)
+                ready[b].record(copy)
+        if s >= 1:  # compute step s - 1
+            pb = (s - 1) % 2
+            compute.wait_event(ready[pb])
+            table.insert(dev_in[pb])
+            table.update()
+            table.query_cv(dev_in[pb], P, D, out=dev_out[pb])
+            out_host[pb].copy_(dev_out[pb], non_blocking=True)
+            free[pb].record(compute)
+    end.record(compute)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    return {"value": V * steps / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": V * 64,
+            "d2h_bytes_per_step": V * 12, "steps": steps,
+            "note": "pinned host buffers; H2D of step k+1 overlapped with step k on a second stream"}
+
+
+def main(argv=None) -> None:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--impl", default="psf", choices=["psf", "reference"])
+    ap.add_argument("--fp16", action="store_true", help="FP16 copy of the approximant for the query")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps are required")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_psf(args)
+
+
+if __name__ == "__main__":
+    main()

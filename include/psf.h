@@ -1,0 +1,176 @@
+/*
+ * psf.h -- C ABI of the progressive spatio-temporal filtering hot path (B300, sm_103a).
+ *
+ * One table per render session holds a sparse spatio-directional field: for every
+ * basis function (cell) the per-iteration fixed-point accumulators, the cumulative
+ * counter c_old and the approximant L~ (Pantaleoni, "Online path sampling control
+ * with progressive spatio-temporal filtering", Section "Progressive Spatio-Temporal
+ * Filtering").  Each iteration:
+ *
+ *   psf_insert    scatter path vertices into their cells         (eq. 5-6, Alg. 1)
+ *   psf_update    blend each touched cell into its approximant   (eq. 10-11)
+ *   psf_query_cv  apply the approximant as a control variate     (Section "Control variates")
+ *
+ * Conventions shared by every call
+ *   - All pointers named d_* are device pointers on the current CUDA device; h_* are
+ *     host pointers.  The caller owns every buffer it passes, including the table
+ *     memory given to psf_create; the library owns only a small host-side header.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Calls enqueue work on it and return without waiting, except psf_export and
+ *     psf_get_stats, which synchronise that stream.
+ *   - Return value: PSF_OK (0) or a negative PSF_ERR_* code for errors detected on the
+ *     host (nothing is enqueued then).  Conditions detected on the device set sticky
+ *     bits (PSF_STATUS_*) in the table's device status word; psf_update returns them
+ *     as last copied back to the host (non-blocking, may lag the device by one call)
+ *     and psf_get_stats returns them synchronised.
+ *   - Calls on one table must be ordered on one stream (or synchronised by the
+ *     caller); tables are independent of each other.
+ *
+ * Vertex record: 64 bytes = 16 float32, four 16-byte vectors,
+ *   v0 = (px, py, pz, w)    position, MIS weight w (eq. 5)
+ *   v1 = (nx, ny, nz, tr)   geometric normal, throughput red
+ *   v2 = (dx, dy, dz, tg)   incoming ray direction (towards the surface), throughput green
+ *   v3 = (Lr, Lg, Lb, tb)   the vertex's value L-bar (eq. 3 / 9), throughput blue
+ * The outgoing direction is omega_o = -d (Alg. 1).  t = (tr, tg, tb) is f*cos*w/p to the
+ * next vertex of the path.  Vertex arrays must be 16-byte aligned.  For queries the
+ * array is depth-major: record j*P + p is vertex j of path p.
+ *
+ * Cell key (Section "Basis functions and data structures: spatio-directional hashing":
+ * a grid over position times a grid over omega_o; the dominant-axis normal bin is an
+ * optional extra field).  Packed in 64 bits, bit 63 always 0:
+ *   level:2 (61-62, always 0) | normal bin:3 (58-60) | direction bin:2d (48..) |
+ *   x:16 (32-47) | y:16 (16-31) | z:16 (0-15)
+ * x = floor(px * 2^q) + 2^15 (likewise y, z); the direction bin is the octahedral map of
+ * omega_o on a 2^d x 2^d grid (sgn(0) = +1, lower hemisphere folded outwards, bins
+ * clamped to [0, 2^d - 1]), taken in FP32 with correctly rounded operations.
+ *
+ * Range rule: a vertex is dropped (PSF_STATUS_RANGE, counted in dropped_vertices) if
+ * any of p, n, d, L, w is non-finite, d is zero, a cell index leaves [-2^15, 2^15),
+ * w < 0, w > 2^15 or |fl32(w * L_c)| > 2^15.  A vertex whose fixed-point weight
+ * round(w * 2^F) is 0 carries no weight and is skipped silently (zero_weight_vertices).
+ */
+#ifndef PSF_H
+#define PSF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSF_OK 0
+#define PSF_ERR_INVALID_ARG (-1) /* bad pointer, size, alignment or configuration */
+#define PSF_ERR_NO_MEM (-2)      /* table memory or host buffer too small */
+#define PSF_ERR_CUDA (-3)        /* a CUDA runtime call failed; see psf_last_cuda_error */
+
+#define PSF_STATUS_TABLE_FULL 1u /* a key found no slot within the probe bound; its vertices were dropped */
+#define PSF_STATUS_RANGE 2u      /* at least one vertex failed the range rule */
+#define PSF_STATUS_TIMEOUT 4u    /* a bounded device-side wait gave up (batched step) */
+
+#define PSF_MAX_PROBE 4096u      /* slots a probe visits before declaring the table full */
+#define PSF_MAX_BATCH 256u       /* tables per psf_batch_step call */
+
+typedef struct psf_table psf_table;
+
+typedef struct {
+    uint32_t log2_capacity; /* slots = 2^log2_capacity, 4..30 */
+    uint32_t pos_bits_q;    /* cell size 2^-q in scene units, 0..20 */
+    uint32_t dir_bits_d;    /* octahedral direction grid 2^d x 2^d, 0..5 */
+    uint32_t use_normal;    /* 1: key includes the dominant-axis normal bin; 0: the paper's 5-d key */
+    float alpha_min;        /* 1 / T_max of eq. (11), in [0, 1] */
+    float beta;             /* control-variate coefficient (the paper uses [0.5, 1]) */
+    uint32_t cv_max_depth;  /* the CV is applied to vertices j < cv_max_depth only */
+    uint32_t frac_bits;     /* F: fixed-point fraction bits of the accumulators, 8..32 */
+    uint32_t cache_fp16;    /* 1: the update also writes an FP16 copy of L~ and queries read it */
+    uint32_t blend_mode;    /* 0: eq. (11) square-root blend; 1: constant alpha = alpha_min */
+} psf_config;
+
+/* One exported cell (psf_export), in ascending key order. */
+typedef struct {
+    uint64_t key;
+    int64_t sum[3];       /* this iteration's sum of round(w * L_c * 2^F) (0 after psf_update) */
+    int64_t c_new;        /* this iteration's sum of round(w * 2^F) (eq. 5) (0 after psf_update) */
+    int64_t c_old;        /* cumulative counter of all blended iterations (eq. 10-11), saturating */
+    float L[3];           /* the FP32 approximant */
+    uint16_t L_fp16[3];   /* its FP16 copy (IEEE binary16 bits; 0 when cache_fp16 = 0) */
+    uint16_t pad;
+} psf_cell_record;
+
+typedef struct {
+    uint64_t capacity;             /* slots */
+    uint64_t live_cells;           /* occupied slots */
+    uint64_t dropped_vertices;     /* range rule or full table */
+    uint64_t zero_weight_vertices; /* skipped: fixed-point weight 0 */
+    uint64_t iterations;           /* psf_update calls executed on the device */
+    uint32_t status;               /* sticky PSF_STATUS_* bits */
+    uint32_t max_probe;            /* longest probe sequence seen by an insert */
+    uint64_t table_bytes;          /* psf_table_bytes of the configuration */
+    uint64_t touched_cells;        /* cells blended by all psf_update calls so far */
+} psf_stats;
+
+/* Bytes of device memory a table with this configuration needs (0 if the
+ * configuration is invalid).  The caller allocates them (256-byte aligned). */
+size_t psf_table_bytes(const psf_config* cfg);
+
+/* Bind a table to caller memory d_mem (>= psf_table_bytes, 256-byte aligned) and
+ * enqueue its initialisation (all slots empty, L~ = 0, counters 0) on `stream`.
+ * On success *out receives the handle.  d_mem must outlive the table. */
+int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, psf_table** out);
+
+/* Scatter n vertices (any order) into the table: for each vertex, find or claim its
+ * cell and add round(w * L_c * 2^F) to the cell's three sums and round(w * 2^F) to
+ * its counter c_new -- eq. (5) and the numerator of eq. (6), in 64-bit fixed point so
+ * the result does not depend on the order of the additions.  Several calls may be made
+ * per iteration.  n = 0 is a no-op. */
+int psf_insert(psf_table* t, const float* d_vertices, uint64_t n, void* stream);
+
+/* End of iteration: every cell with c_new > 0 gets
+ *   alpha = max(sqrt(c_new / (c_old + c_new)), alpha_min)        (eq. 11; blend_mode 0)
+ *   L~ = (1 - alpha) L~ + alpha * sum / c_new                    (eq. 10)
+ *   c_old = c_old + c_new (saturating), sums = c_new = 0,
+ * in FP32, plus the FP16 copy when cache_fp16 = 1; untouched cells keep their state.
+ * Returns the sticky status bits as last copied back (>= 0), or a negative error. */
+int psf_update(psf_table* t, void* stream);
+
+/* Control-variate estimate for P paths of depth D (d_vertices: D*P records, depth-major).
+ * With C_j the approximant of vertex j's cell (0 when absent; FP16 copy when cache_fp16):
+ *   out_j = L_j - beta * t_j * C_{j+1} + beta * C_j   for j < min(D - 1, cv_max_depth)
+ *   out_j = L_j                                        otherwise
+ * (Section "Control variates", equation CVEstimator: h = t * C_{j+1} is f * L~_i at the
+ * next vertex, whose known integral is C_j.)  d_out_rgb receives D*P*3 float32 in the vertex order. */
+int psf_query_cv(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float* d_out_rgb,
+                 void* stream);
+
+/* One whole iteration: psf_insert of the D*P vertices, psf_update, psf_query_cv. */
+int psf_step(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float* d_out_rgb,
+             void* stream);
+
+/* Global counter reset (Section "Temporal averaging", after eq. 11): c_old := 0 in every cell; L~ is kept,
+ * so the next update of a cell takes alpha = 1. */
+int psf_reset(psf_table* t, void* stream);
+
+/* Copy every occupied cell to h_out in ascending key order.  *n_out receives the number
+ * of cells; if it exceeds cap nothing is written and PSF_ERR_NO_MEM is returned.
+ * Synchronises `stream`.  Uses a temporary device buffer (stream-ordered allocation). */
+int psf_export(psf_table* t, psf_cell_record* h_out, size_t cap, size_t* n_out, void* stream);
+
+/* Synchronised statistics and sticky status.  Synchronises `stream`. */
+int psf_get_stats(psf_table* t, psf_stats* out, void* stream);
+
+/* Release the host header (the caller frees d_mem).  All work enqueued on the table must
+ * have completed (synchronise its stream first), as for freeing d_mem.  NULL is a no-op. */
+int psf_destroy(psf_table* t);
+
+/* Text of the last CUDA error seen by this thread's calls (empty if none). */
+const char* psf_last_cuda_error(void);
+
+/* ABI version of this header: bump on any incompatible change. */
+#define PSF_ABI_VERSION 1
+int psf_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSF_H */

@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
         L.oracle_update.argtypes = [vp]
         L.oracle_reset.argtypes = [vp]
         L.oracle_query_cv.argtypes = [vp, vp, u32, u32, vp]
+        L.oracle_lookup.argtypes = [vp, vp, u64, vp]
         L.oracle_size.restype = u64
         L.oracle_size.argtypes = [vp]
         L.oracle_counters.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
@@ -124,6 +125,13 @@ class Oracle:
             raise ValueError("vertex count must be P*D")
         out = np.empty((P * D, 3), dtype=np.float64)
         lib().oracle_query_cv(self._h, v.ctypes.data, P, D, out.ctypes.data)
+        return out
+
+    def lookup(self, verts: np.ndarray) -> np.ndarray:
+        """(n, 3) approximant of each vertex's cell, 0 where the cell is absent."""
+        v = _verts(verts)
+        out = np.empty((v.shape[0], 3), dtype=np.float64)
+        lib().oracle_lookup(self._h, v.ctypes.data, v.shape[0], out.ctypes.data)
         return out
 
     def __len__(self) -> int:

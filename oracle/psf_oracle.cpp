@@ -294,6 +294,21 @@ void oracle_query_cv(void* h, const float* verts, uint32_t P, uint32_t D, double
     }
 }
 
+// The approximant of each vertex's cell (0 when absent), as the query reads it: C_out
+// receives n*3 doubles.  Used by tests to form the norm-wise error bound of the query.
+void oracle_lookup(void* h, const float* verts, uint64_t n, double* C_out) {
+    Oracle* o = static_cast<Oracle*>(h);
+    for (uint64_t i = 0; i < n; ++i) {
+        double* C = C_out + 3 * i;
+        C[0] = C[1] = C[2] = 0.0;
+        CellKey key;
+        if (!vertex_cell(o->cfg, verts + 16 * i, &key)) continue;
+        auto it = o->cells.find(key);
+        if (it != o->cells.end())
+            for (int ch = 0; ch < 3; ++ch) C[ch] = it->second.L[ch];
+    }
+}
+
 uint64_t oracle_size(void* h) { return static_cast<Oracle*>(h)->cells.size(); }
 
 void oracle_counters(void* h, uint64_t* dropped, uint64_t* zero_weight) {

@@ -1,0 +1,436 @@
+// psf.cu -- kernels and C ABI of the progressive spatio-temporal filtering hot path.
+//
+// Per iteration (one table = one render session):
+//   k_insert  one thread per vertex, lanes with equal keys merged by match_any, one
+//             leader per key probes the open-addressing table and adds the group's
+//             64-bit fixed-point sums with four atomics (eq. 5-6, Alg. 1)
+//   k_update  one warp per 1024 slots of the dirty bitmap, set bits compacted across
+//             the warp, one lane per touched cell applies eq. (10)-(11)
+//   k_query   one thread per path, walking its vertices from the last to the first,
+//             one probe per vertex (Section "Control variates", CVEstimator)
+// Grids are persistent (grid-stride) and sized as a multiple of the SM count.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "psf.h"
+#include "psf_device.cuh"
+
+using psf::Acc;
+using psf::DevHeader;
+using psf::TableView;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr int kThreads = 256;
+
+}  // namespace
+
+struct psf_table {
+    psf_config cfg;
+    TableView view;
+    void* mem;
+    size_t bytes;
+    unsigned* h_status;  // host-mapped pinned word written by k_update
+    int device;
+    int sms;
+    int insert_blocks_per_sm;
+    int update_blocks_per_sm;
+    int query_blocks_per_sm;
+};
+
+namespace {
+
+bool cuda_ok(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return true;
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return false;
+}
+
+struct Layout {
+    size_t hdr, keys, acc, lst, cold, mirror, dirty, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+bool config_valid(const psf_config* c) {
+    if (!c) return false;
+    if (c->log2_capacity < 4 || c->log2_capacity > 30) return false;
+    if (c->pos_bits_q > 20 || c->dir_bits_d > 5) return false;
+    if (c->frac_bits < 8 || c->frac_bits > 32) return false;
+    if (!(c->alpha_min >= 0.0f && c->alpha_min <= 1.0f)) return false;
+    if (!(c->beta == c->beta) || c->blend_mode > 1 || c->use_normal > 1 || c->cache_fp16 > 1) return false;
+    return true;
+}
+
+Layout layout_of(const psf_config* c) {
+    const size_t cap = size_t{1} << c->log2_capacity;
+    Layout L{};
+    size_t off = 0;
+    L.hdr = off;
+    off = align256(off + sizeof(DevHeader));
+    L.keys = off;
+    off = align256(off + cap * sizeof(unsigned long long));
+    L.acc = off;
+    off = align256(off + cap * sizeof(Acc));
+    L.lst = off;
+    off = align256(off + cap * sizeof(float4));
+    L.cold = off;
+    off = align256(off + cap * sizeof(long long));
+    L.mirror = off;
+    if (c->cache_fp16) off = align256(off + cap * sizeof(uint2));
+    L.dirty = off;
+    off = align256(off + ((cap + 31) / 32) * sizeof(unsigned));
+    L.total = off;
+    return L;
+}
+
+int grid_for(const psf_table* t, int per_sm, unsigned long long work_items) {
+    const unsigned long long need = (work_items + kThreads - 1) / kThreads;
+    const unsigned long long full = static_cast<unsigned long long>(t->sms) * static_cast<unsigned long long>(per_sm);
+    return static_cast<int>(std::max<unsigned long long>(1, std::min(need, full)));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* __restrict__ v, unsigned long long n) {
+    __shared__ unsigned s_max_probe;
+    if (threadIdx.x == 0) s_max_probe = 0;
+    __syncthreads();
+    unsigned max_len = 0;
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+    for (unsigned long long base = static_cast<unsigned long long>(blockIdx.x) * blockDim.x; base < n; base += stride) {
+        const unsigned long long i = base + threadIdx.x;
+        const bool valid = i < n;
+        float4 v0 = make_float4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
+        if (valid) {
+            const float4* r = v + 4 * i;
+            v0 = __ldg(r);
+            v1 = __ldg(r + 1);
+            v2 = __ldg(r + 2);
+            v3 = __ldg(r + 3);
+        }
+        psf::insert_warp(t, valid, v0, v1, v2, v3, &max_len);
+    }
+    if (max_len) atomicMax(&s_max_probe, max_len);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_max_probe) atomicMax(&t.hdr->max_probe, s_max_probe);
+}
+
+__global__ void __launch_bounds__(kThreads) k_update(TableView t) {
+    __shared__ unsigned long long s_touched;
+    if (threadIdx.x == 0) s_touched = 0;
+    __syncthreads();
+    const unsigned long long nwords = ((1ull << t.log2cap) + 31ull) >> 5;
+    const unsigned long long warp = (static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = (static_cast<unsigned long long>(gridDim.x) * blockDim.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // every earlier kernel on this stream has finished: publish the sticky status
+        if (t.h_status) *reinterpret_cast<volatile unsigned*>(t.h_status) = t.hdr->status;
+        t.hdr->iterations += 1;
+    }
+    unsigned long long touched = 0;
+    for (unsigned long long w0 = warp * 32ull; w0 < nwords; w0 += nwarps * 32ull) touched += psf::update_words(t, w0, nwords);
+    if ((threadIdx.x & 31u) == 0 && touched) atomicAdd(&s_touched, touched);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_touched) atomicAdd(&t.hdr->touched, s_touched);
+}
+
+__global__ void __launch_bounds__(kThreads) k_query(TableView t, const float4* __restrict__ v, unsigned P, unsigned D,
+                                                    float* __restrict__ out) {
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+    for (unsigned long long p = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < P;
+         p += stride) {
+        float3 c_next = make_float3(0.0f, 0.0f, 0.0f);
+        for (int j = static_cast<int>(D) - 1; j >= 0; --j) {
+            const unsigned long long i = static_cast<unsigned long long>(j) * P + p;
+            const float4* r = v + 4 * i;
+            const float4 v0 = __ldg(r), v1 = __ldg(r + 1), v2 = __ldg(r + 2), v3 = __ldg(r + 3);
+            const float3 c = psf::cell_value(t, v0, v1, v2);
+            float o0 = v3.x, o1 = v3.y, o2 = v3.z;
+            if (j + 1 < static_cast<int>(D) && static_cast<unsigned>(j) < t.cv_max_depth) {
+                o0 = psf::cv_combine(v3.x, v1.w, c_next.x, c.x, t.beta);
+                o1 = psf::cv_combine(v3.y, v2.w, c_next.y, c.y, t.beta);
+                o2 = psf::cv_combine(v3.z, v3.w, c_next.z, c.z, t.beta);
+            }
+            float* o = out + 3 * i;
+            o[0] = o0;
+            o[1] = o1;
+            o[2] = o2;
+            c_next = c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_export(TableView t, unsigned long long s0, unsigned long long s1,
+                                                     psf_cell_record* out, unsigned* count) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+    for (unsigned long long base = s0 + static_cast<unsigned long long>(blockIdx.x) * blockDim.x; base < s1;
+         base += stride) {
+        const unsigned long long s = base + threadIdx.x;
+        const unsigned long long key = s < s1 ? t.keys[s] : psf::kEmpty;
+        const bool live = key != psf::kEmpty;
+        const unsigned m = __ballot_sync(psf::kFull, live);
+        if (!m) continue;
+        unsigned first = 0;
+        if (lane == 0) first = atomicAdd(count, __popc(m));
+        first = __shfl_sync(psf::kFull, first, 0);
+        if (!live) continue;
+        psf_cell_record r;
+        r.key = key;
+        const Acc a = t.acc[s];
+        r.sum[0] = a.s[0];
+        r.sum[1] = a.s[1];
+        r.sum[2] = a.s[2];
+        r.c_new = a.c;
+        r.c_old = t.cold[s];
+        const float4 L = t.lst[s];
+        r.L[0] = L.x;
+        r.L[1] = L.y;
+        r.L[2] = L.z;
+        if (t.mirror) {
+            const uint2 h = t.mirror[s];
+            r.L_fp16[0] = static_cast<uint16_t>(h.x & 0xffffu);
+            r.L_fp16[1] = static_cast<uint16_t>(h.x >> 16);
+            r.L_fp16[2] = static_cast<uint16_t>(h.y & 0xffffu);
+        } else {
+            r.L_fp16[0] = r.L_fp16[1] = r.L_fp16[2] = 0;
+        }
+        r.pad = 0;
+        out[first + __popc(m & ((1u << lane) - 1u))] = r;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_count_live(TableView t, unsigned long long* count) {
+    __shared__ unsigned long long s_count;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    const unsigned long long cap = 1ull << t.log2cap;
+    unsigned long long mine = 0;
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+    for (unsigned long long s = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; s < cap; s += stride)
+        mine += t.keys[s] != psf::kEmpty;
+    if (mine) atomicAdd(&s_count, mine);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_count) atomicAdd(count, s_count);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+int psf_abi_version(void) { return PSF_ABI_VERSION; }
+
+const char* psf_last_cuda_error(void) { return g_last_error.c_str(); }
+
+size_t psf_table_bytes(const psf_config* cfg) {
+    if (!config_valid(cfg)) return 0;
+    return layout_of(cfg).total;
+}
+
+int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, psf_table** out) {
+    if (!out || !config_valid(cfg) || !d_mem) return PSF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (reinterpret_cast<uintptr_t>(d_mem) & 255u) return PSF_ERR_INVALID_ARG;
+    const Layout L = layout_of(cfg);
+    if (bytes < L.total) return PSF_ERR_NO_MEM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    psf_table* t = new (std::nothrow) psf_table();
+    if (!t) return PSF_ERR_NO_MEM;
+    t->cfg = *cfg;
+    t->mem = d_mem;
+    t->bytes = bytes;
+    if (!cuda_ok(cudaGetDevice(&t->device), "cudaGetDevice") ||
+        !cuda_ok(cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device), "cudaDeviceGetAttribute") ||
+        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->insert_blocks_per_sm, k_insert, kThreads, 0), "occupancy") ||
+        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->update_blocks_per_sm, k_update, kThreads, 0), "occupancy") ||
+        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->query_blocks_per_sm, k_query, kThreads, 0), "occupancy") ||
+        !cuda_ok(cudaHostAlloc(reinterpret_cast<void**>(&t->h_status), sizeof(unsigned), cudaHostAllocMapped),
+                 "cudaHostAlloc")) {
+        delete t;
+        return PSF_ERR_CUDA;
+    }
+    *t->h_status = 0;
+    char* base = static_cast<char*>(d_mem);
+    TableView& v = t->view;
+    v.hdr = reinterpret_cast<DevHeader*>(base + L.hdr);
+    v.keys = reinterpret_cast<unsigned long long*>(base + L.keys);
+    v.acc = reinterpret_cast<Acc*>(base + L.acc);
+    v.lst = reinterpret_cast<float4*>(base + L.lst);
+    v.cold = reinterpret_cast<long long*>(base + L.cold);
+    v.mirror = cfg->cache_fp16 ? reinterpret_cast<uint2*>(base + L.mirror) : nullptr;
+    v.dirty = reinterpret_cast<unsigned*>(base + L.dirty);
+    unsigned* dev_status = nullptr;
+    if (!cuda_ok(cudaHostGetDevicePointer(reinterpret_cast<void**>(&dev_status), t->h_status, 0), "cudaHostGetDevicePointer")) {
+        cudaFreeHost(t->h_status);
+        delete t;
+        return PSF_ERR_CUDA;
+    }
+    v.h_status = dev_status;
+    v.log2cap = cfg->log2_capacity;
+    v.max_probe = std::min<uint32_t>(PSF_MAX_PROBE, 1u << std::min<uint32_t>(cfg->log2_capacity, 31u));
+    v.q = cfg->pos_bits_q;
+    v.d = cfg->dir_bits_d;
+    v.use_normal = cfg->use_normal;
+    v.frac_bits = cfg->frac_bits;
+    v.cv_max_depth = cfg->cv_max_depth;
+    v.blend_mode = cfg->blend_mode;
+    v.alpha_min = cfg->alpha_min;
+    v.beta = cfg->beta;
+
+    const size_t cap = size_t{1} << cfg->log2_capacity;
+    bool ok = cuda_ok(cudaMemsetAsync(base, 0, L.total, st), "cudaMemsetAsync") &&
+              cuda_ok(cudaMemsetAsync(base + L.keys, 0xff, cap * sizeof(unsigned long long), st), "cudaMemsetAsync");
+    if (!ok) {
+        cudaFreeHost(t->h_status);
+        delete t;
+        return PSF_ERR_CUDA;
+    }
+    *out = t;
+    return PSF_OK;
+}
+
+int psf_insert(psf_table* t, const float* d_vertices, uint64_t n, void* stream) {
+    if (!t) return PSF_ERR_INVALID_ARG;
+    if (n == 0) return PSF_OK;
+    if (!d_vertices || (reinterpret_cast<uintptr_t>(d_vertices) & 15u)) return PSF_ERR_INVALID_ARG;
+    const int grid = grid_for(t, t->insert_blocks_per_sm, n);
+    k_insert<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view, reinterpret_cast<const float4*>(d_vertices), n);
+    return cuda_ok(cudaGetLastError(), "k_insert") ? PSF_OK : PSF_ERR_CUDA;
+}
+
+int psf_update(psf_table* t, void* stream) {
+    if (!t) return PSF_ERR_INVALID_ARG;
+    const unsigned long long nwords = ((1ull << t->cfg.log2_capacity) + 31ull) >> 5;
+    const int grid = grid_for(t, t->update_blocks_per_sm, nwords);  // one warp per 32 words
+    k_update<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view);
+    if (!cuda_ok(cudaGetLastError(), "k_update")) return PSF_ERR_CUDA;
+    return static_cast<int>(*reinterpret_cast<volatile unsigned*>(t->h_status) & 0x7fffffffu);
+}
+
+int psf_query_cv(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float* d_out_rgb, void* stream) {
+    if (!t) return PSF_ERR_INVALID_ARG;
+    if (P == 0 || D == 0) return PSF_OK;
+    if (!d_vertices || !d_out_rgb || (reinterpret_cast<uintptr_t>(d_vertices) & 15u) ||
+        (reinterpret_cast<uintptr_t>(d_out_rgb) & 3u))
+        return PSF_ERR_INVALID_ARG;
+    const int grid = grid_for(t, t->query_blocks_per_sm, P);
+    k_query<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view, reinterpret_cast<const float4*>(d_vertices), P,
+                                                                      D, d_out_rgb);
+    return cuda_ok(cudaGetLastError(), "k_query") ? PSF_OK : PSF_ERR_CUDA;
+}
+
+int psf_step(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float* d_out_rgb, void* stream) {
+    int rc = psf_insert(t, d_vertices, static_cast<uint64_t>(P) * D, stream);
+    if (rc != PSF_OK) return rc;
+    rc = psf_update(t, stream);
+    if (rc < 0) return rc;
+    return psf_query_cv(t, d_vertices, P, D, d_out_rgb, stream);
+}
+
+int psf_reset(psf_table* t, void* stream) {
+    if (!t) return PSF_ERR_INVALID_ARG;
+    const size_t cap = size_t{1} << t->cfg.log2_capacity;
+    return cuda_ok(cudaMemsetAsync(t->view.cold, 0, cap * sizeof(long long), static_cast<cudaStream_t>(stream)),
+                   "cudaMemsetAsync")
+               ? PSF_OK
+               : PSF_ERR_CUDA;
+}
+
+int psf_export(psf_table* t, psf_cell_record* h_out, size_t cap_out, size_t* n_out, void* stream) {
+    if (!t || !n_out || (cap_out && !h_out)) return PSF_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned long long cap = 1ull << t->cfg.log2_capacity;
+    const unsigned long long chunk = std::min<unsigned long long>(cap, 1ull << 20);
+    void* scratch = nullptr;
+    const size_t scratch_bytes = chunk * sizeof(psf_cell_record) + 256;
+    if (!cuda_ok(cudaMallocAsync(&scratch, scratch_bytes, st), "cudaMallocAsync")) return PSF_ERR_CUDA;
+    psf_cell_record* d_rec = reinterpret_cast<psf_cell_record*>(static_cast<char*>(scratch) + 256);
+    unsigned* d_count = static_cast<unsigned*>(scratch);
+    std::vector<psf_cell_record> all;
+    int rc = PSF_OK;
+    for (unsigned long long s0 = 0; s0 < cap && rc == PSF_OK; s0 += chunk) {
+        unsigned n = 0;
+        const int grid = grid_for(t, 4, chunk);
+        if (!cuda_ok(cudaMemsetAsync(d_count, 0, sizeof(unsigned), st), "cudaMemsetAsync")) {
+            rc = PSF_ERR_CUDA;
+            break;
+        }
+        k_export<<<grid, kThreads, 0, st>>>(t->view, s0, s0 + chunk, d_rec, d_count);
+        if (!cuda_ok(cudaGetLastError(), "k_export") ||
+            !cuda_ok(cudaMemcpyAsync(&n, d_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") ||
+            !cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize")) {
+            rc = PSF_ERR_CUDA;
+            break;
+        }
+        const size_t old = all.size();
+        all.resize(old + n);
+        if (n && !cuda_ok(cudaMemcpyAsync(all.data() + old, d_rec, n * sizeof(psf_cell_record), cudaMemcpyDeviceToHost, st),
+                          "cudaMemcpyAsync"))
+            rc = PSF_ERR_CUDA;
+        if (rc == PSF_OK && !cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize")) rc = PSF_ERR_CUDA;
+    }
+    cudaFreeAsync(scratch, st);
+    if (!cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize") && rc == PSF_OK) rc = PSF_ERR_CUDA;
+    if (rc != PSF_OK) return rc;
+    std::sort(all.begin(), all.end(), [](const psf_cell_record& a, const psf_cell_record& b) { return a.key < b.key; });
+    *n_out = all.size();
+    if (all.size() > cap_out) return PSF_ERR_NO_MEM;
+    if (!all.empty()) std::memcpy(h_out, all.data(), all.size() * sizeof(psf_cell_record));
+    return PSF_OK;
+}
+
+int psf_get_stats(psf_table* t, psf_stats* out, void* stream) {
+    if (!t || !out) return PSF_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* scratch = nullptr;
+    if (!cuda_ok(cudaMallocAsync(&scratch, 256 + sizeof(DevHeader), st), "cudaMallocAsync")) return PSF_ERR_CUDA;
+    unsigned long long* d_count = static_cast<unsigned long long*>(scratch);
+    DevHeader h{};
+    unsigned long long live = 0;
+    bool ok = cuda_ok(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st), "cudaMemsetAsync");
+    if (ok) {
+        k_count_live<<<grid_for(t, 4, 1ull << t->cfg.log2_capacity), kThreads, 0, st>>>(t->view, d_count);
+        ok = cuda_ok(cudaGetLastError(), "k_count_live") &&
+             cuda_ok(cudaMemcpyAsync(&live, d_count, sizeof(live), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") &&
+             cuda_ok(cudaMemcpyAsync(&h, t->view.hdr, sizeof(h), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    }
+    cudaFreeAsync(scratch, st);
+    ok = cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize") && ok;
+    if (!ok) return PSF_ERR_CUDA;
+    out->capacity = 1ull << t->cfg.log2_capacity;
+    out->live_cells = live;
+    out->dropped_vertices = h.dropped;
+    out->zero_weight_vertices = h.zero_weight;
+    out->iterations = h.iterations;
+    out->status = h.status;
+    out->max_probe = h.max_probe;
+    out->table_bytes = layout_of(&t->cfg).total;
+    out->touched_cells = h.touched;
+    return PSF_OK;
+}
+
+int psf_destroy(psf_table* t) {
+    if (!t) return PSF_OK;
+    cudaFreeHost(t->h_status);
+    delete t;
+    return PSF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,386 @@
+// psf_device.cuh -- device-side building blocks of the filtering hot path (sm_103a).
+//
+// Table memory (one contiguous caller-owned allocation, every array 256-byte aligned):
+//   DevHeader                       status word and counters
+//   keys   u64[cap]                 packed cell key or kEmpty (open addressing, linear probe)
+//   acc    Acc[cap]   (32 B)        this iteration's fixed-point sums and counter c_new
+//   lst    float4[cap](16 B)        the FP32 approximant (r, g, b, 0)
+//   cold   i64[cap]                 cumulative counter c_old
+//   mirror uint2[cap] (8 B)         FP16 copy of the approximant (only with cache_fp16)
+//   dirty  u32[cap/32]              one bit per slot: touched this iteration
+// The split keeps every per-slot access inside one 32-byte sector: inserts touch
+// keys + acc, the update touches acc + lst + cold (+ mirror), queries touch keys +
+// lst (or mirror).
+
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace psf {
+
+constexpr unsigned long long kEmpty = ~0ull;  // bit 63 set: never a valid key
+constexpr unsigned kFull = 0xffffffffu;
+
+constexpr unsigned kStatusTableFull = 1u;
+constexpr unsigned kStatusRange = 2u;
+constexpr unsigned kStatusTimeout = 4u;
+
+struct DevHeader {
+    unsigned int status;
+    unsigned int max_probe;
+    unsigned long long dropped;
+    unsigned long long zero_weight;
+    unsigned long long iterations;
+    unsigned long long touched;  // cells blended by all updates so far
+    unsigned int barrier_count;  // grid barrier of the batched kernel
+    unsigned int barrier_gen;
+    unsigned int pad[52];
+};
+static_assert(sizeof(DevHeader) == 256, "header is one 256-byte block");
+
+struct alignas(32) Acc {
+    long long s[3];
+    long long c;
+};
+
+struct TableView {
+    DevHeader* hdr;
+    unsigned long long* keys;
+    Acc* acc;
+    float4* lst;
+    long long* cold;
+    uint2* mirror;  // nullptr unless cache_fp16
+    unsigned* dirty;
+    unsigned* h_status;  // host-mapped copy of the status word (may be nullptr)
+    uint32_t log2cap;
+    uint32_t max_probe;
+    uint32_t q;
+    uint32_t d;
+    uint32_t use_normal;
+    uint32_t frac_bits;
+    uint32_t cv_max_depth;
+    uint32_t blend_mode;
+    float alpha_min;
+    float beta;
+};
+
+// ---------------------------------------------------------------------------
+// Cell key: Section "Basis functions and data structures: spatio-directional
+// hashing".  Every decision that yields an integer is taken in FP32 with explicitly
+// rounded operations (no contraction), in a fixed order.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// floor(p * 2^q) biased by 2^15; false outside [-2^15, 2^15) or for NaN.
+__device__ __forceinline__ bool quantise_axis(float p, float scale, unsigned* out) {
+    const float f = floorf(__fmul_rn(p, scale));  // exact: power-of-two scale
+    if (!(f >= -32768.0f && f <= 32767.0f)) return false;
+    *out = static_cast<unsigned>(static_cast<int>(f) + 32768);
+    return true;
+}
+
+__device__ __forceinline__ unsigned dominant_axis_bin(float nx, float ny, float nz) {
+    const float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
+    if (ax >= ay && ax >= az) return nx >= 0.0f ? 0u : 1u;
+    if (ay >= az) return ny >= 0.0f ? 2u : 3u;
+    return nz >= 0.0f ? 4u : 5u;
+}
+
+__device__ __forceinline__ unsigned octa_bin(float g, float half, int top) {
+    int b = static_cast<int>(floorf(__fmul_rn(g, half)));
+    b = b < 0 ? 0 : b;
+    return static_cast<unsigned>(b > top ? top : b);
+}
+
+// Packed key of the vertex (v0 = position, v1 = normal, v2 = incoming direction).
+__device__ __forceinline__ bool cell_key(const TableView& t, const float4& v0, const float4& v1,
+                                         const float4& v2, unsigned long long* key) {
+    if (!(isfinite(v1.x) && isfinite(v1.y) && isfinite(v1.z) && isfinite(v2.x) && isfinite(v2.y) &&
+          isfinite(v2.z)))
+        return false;
+    const float scale = pow2f(static_cast<int>(t.q));
+    unsigned bx, by, bz;
+    // quantise_axis rejects NaN and +-inf positions through its range test
+    if (!quantise_axis(v0.x, scale, &bx) || !quantise_axis(v0.y, scale, &by) ||
+        !quantise_axis(v0.z, scale, &bz))
+        return false;
+    const unsigned nb = t.use_normal ? dominant_axis_bin(v1.x, v1.y, v1.z) : 0u;
+    // omega_o = -d; octahedral map onto [-1, 1]^2
+    const float wx = -v2.x, wy = -v2.y, wz = -v2.z;
+    const float s = __fadd_rn(__fadd_rn(fabsf(wx), fabsf(wy)), fabsf(wz));
+    if (!(s > 0.0f) || isinf(s)) return false;
+    float u = __fdiv_rn(wx, s);
+    float v = __fdiv_rn(wy, s);
+    if (wz < 0.0f) {  // lower hemisphere: fold the triangles outwards, sgn(0) = +1
+        const float su = u >= 0.0f ? 1.0f : -1.0f;
+        const float sv = v >= 0.0f ? 1.0f : -1.0f;
+        const float fu = __fsub_rn(1.0f, fabsf(v));
+        const float fv = __fsub_rn(1.0f, fabsf(u));
+        u = __fmul_rn(fu, su);
+        v = __fmul_rn(fv, sv);
+    }
+    const float half = pow2f(static_cast<int>(t.d) - 1);
+    const int top = (1 << t.d) - 1;
+    const unsigned bu = octa_bin(__fadd_rn(u, 1.0f), half, top);
+    const unsigned bv = octa_bin(__fadd_rn(v, 1.0f), half, top);
+    const unsigned long long dbin = (static_cast<unsigned long long>(bu) << t.d) | bv;
+    *key = (static_cast<unsigned long long>(nb) << 58) | (dbin << 48) |
+           (static_cast<unsigned long long>(bx) << 32) | (static_cast<unsigned long long>(by) << 16) | bz;
+    return true;
+}
+
+// Fixed-point contributions of an accepted vertex (eq. 5-6): round(fl32(w L_c) 2^F), round(w 2^F).
+// Returns 1 = accepted, 2 = range rule, 3 = zero fixed-point weight.
+__device__ __forceinline__ int vertex_values(const TableView& t, const float4& v0, const float4& v3,
+                                             long long* s, long long* cw) {
+    const float w = v0.w;
+    if (!(w >= 0.0f && w <= 32768.0f)) return 2;
+    const float p0 = __fmul_rn(w, v3.x), p1 = __fmul_rn(w, v3.y), p2 = __fmul_rn(w, v3.z);
+    if (!(fabsf(p0) <= 32768.0f && fabsf(p1) <= 32768.0f && fabsf(p2) <= 32768.0f)) return 2;
+    const float sc = pow2f(static_cast<int>(t.frac_bits));
+    *cw = __float2ll_rn(__fmul_rn(w, sc));
+    if (*cw == 0) return 3;
+    s[0] = __float2ll_rn(__fmul_rn(p0, sc));
+    s[1] = __float2ll_rn(__fmul_rn(p1, sc));
+    s[2] = __float2ll_rn(__fmul_rn(p2, sc));
+    return 1;
+}
+
+// MurmurHash3's 64-bit finaliser (Appleby, public domain): a bijective avalanche mix.
+__device__ __forceinline__ unsigned long long fmix64(unsigned long long k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+__device__ __forceinline__ unsigned long long home_slot(const TableView& t, unsigned long long key) {
+    return fmix64(key) >> (64 - t.log2cap);
+}
+
+// Find or claim the slot of `key` (linear probing, claim by CAS on kEmpty).
+// Returns the slot, or -1 when max_probe slots were visited without success.
+__device__ __forceinline__ long long probe_claim(const TableView& t, unsigned long long key, unsigned* len) {
+    const unsigned long long mask = (1ull << t.log2cap) - 1ull;
+    unsigned long long s = home_slot(t, key);
+    for (unsigned i = 0; i < t.max_probe; ++i) {
+        const unsigned long long k = __ldcg(t.keys + s);
+        if (k == key) {
+            *len = i + 1;
+            return static_cast<long long>(s);
+        }
+        if (k == kEmpty) {
+            const unsigned long long old = atomicCAS(t.keys + s, kEmpty, key);
+            if (old == kEmpty || old == key) {
+                *len = i + 1;
+                return static_cast<long long>(s);
+            }
+        }
+        s = (s + 1) & mask;
+    }
+    *len = t.max_probe;
+    return -1;
+}
+
+// Read-only lookup: slot of `key` or -1 if absent.
+__device__ __forceinline__ long long probe_find(const TableView& t, unsigned long long key) {
+    const unsigned long long mask = (1ull << t.log2cap) - 1ull;
+    unsigned long long s = home_slot(t, key);
+    for (unsigned i = 0; i < t.max_probe; ++i) {
+        const unsigned long long k = __ldcg(t.keys + s);
+        if (k == key) return static_cast<long long>(s);
+        if (k == kEmpty) return -1;
+        s = (s + 1) & mask;
+    }
+    return -1;
+}
+
+// Sum a 64-bit value over the lanes of `group` exactly: split into a 24-bit unsigned low
+// part and a signed high part so that both 32-bit warp reductions cannot overflow
+// (|v| < 2^48, at most 32 lanes).
+__device__ __forceinline__ long long group_sum64(unsigned group, long long v) {
+    const unsigned lo = static_cast<unsigned>(v & 0xFFFFFFll);
+    const int hi = static_cast<int>(v >> 24);
+    const unsigned slo = __reduce_add_sync(group, lo);
+    const int shi = __reduce_add_sync(group, hi);
+    return static_cast<long long>(shi) * (1ll << 24) + static_cast<long long>(slo);
+}
+
+// Leader of a group of lanes holding the same key: probe once, add the group's sums.
+__device__ __forceinline__ void scatter_group(const TableView& t, unsigned long long key, unsigned members,
+                                              const long long sums[4], unsigned* max_len) {
+    unsigned len = 0;
+    const long long slot = probe_claim(t, key, &len);
+    *max_len = len > *max_len ? len : *max_len;
+    if (slot < 0) {
+        atomicOr(&t.hdr->status, kStatusTableFull);
+        atomicAdd(&t.hdr->dropped, static_cast<unsigned long long>(__popc(members)));
+        return;
+    }
+    Acc* a = t.acc + slot;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[0]), static_cast<unsigned long long>(sums[0]));
+    atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[1]), static_cast<unsigned long long>(sums[1]));
+    atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[2]), static_cast<unsigned long long>(sums[2]));
+    const unsigned long long old =
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a->c), static_cast<unsigned long long>(sums[3]));
+    if (old == 0ull)  // first touch this iteration (every accepted vertex adds weight >= 1)
+        atomicOr(t.dirty + (slot >> 5), 1u << (slot & 31));
+}
+
+// One warp's worth of vertices (one per lane, `valid` lanes only): classify, aggregate
+// lanes with equal keys (match_any), let one leader per key probe and add.
+__device__ __forceinline__ void insert_warp(const TableView& t, bool valid, const float4& v0, const float4& v1,
+                                            const float4& v2, const float4& v3, unsigned* max_len) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned long long key = 0;
+    long long sums[4] = {0, 0, 0, 0};
+    int cls = 0;
+    if (valid) {
+        if (!cell_key(t, v0, v1, v2, &key))
+            cls = 2;
+        else
+            cls = vertex_values(t, v0, v3, sums, &sums[3]);
+    }
+    const unsigned accepted = __ballot_sync(kFull, cls == 1);
+    const unsigned ranged = __ballot_sync(kFull, cls == 2);
+    const unsigned zero_w = __ballot_sync(kFull, cls == 3);
+    if (lane == 0 && (ranged | zero_w)) {
+        if (ranged) {
+            atomicOr(&t.hdr->status, kStatusRange);
+            atomicAdd(&t.hdr->dropped, static_cast<unsigned long long>(__popc(ranged)));
+        }
+        if (zero_w) atomicAdd(&t.hdr->zero_weight, static_cast<unsigned long long>(__popc(zero_w)));
+    }
+    if (cls == 1) {
+        const unsigned group = __match_any_sync(accepted, key);
+        long long red[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) red[k] = group_sum64(group, sums[k]);
+        if (lane == static_cast<unsigned>(__ffs(group) - 1)) scatter_group(t, key, group, red, max_len);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Temporal blend of one touched cell: eq. (10)-(11).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint2 pack_half4(float a, float b, float c) {
+    const float lim = 65504.0f;  // largest finite binary16: saturate instead of overflowing to inf
+    const __half ha = __float2half_rn(fminf(fmaxf(a, -lim), lim));
+    const __half hb = __float2half_rn(fminf(fmaxf(b, -lim), lim));
+    const __half hc = __float2half_rn(fminf(fmaxf(c, -lim), lim));
+    uint2 r;
+    r.x = static_cast<unsigned>(__half_as_ushort(ha)) | (static_cast<unsigned>(__half_as_ushort(hb)) << 16);
+    r.y = static_cast<unsigned>(__half_as_ushort(hc));
+    return r;
+}
+
+__device__ __forceinline__ void blend_slot(const TableView& t, unsigned long long s) {
+    const longlong2* ap = reinterpret_cast<const longlong2*>(t.acc + s);
+    const longlong2 a01 = __ldcg(ap);
+    const longlong2 a23 = __ldcg(ap + 1);
+    const long long cn = a23.y;
+    longlong2* wp = reinterpret_cast<longlong2*>(t.acc + s);
+    const longlong2 z = make_longlong2(0, 0);
+    if (cn <= 0) {  // not reachable for accepted vertices; keep the cell unchanged
+        __stcg(wp, z);
+        __stcg(wp + 1, z);
+        return;
+    }
+    const long long co = t.cold[s];
+    const long long ctot = co > (0x7fffffffffffffffll - cn) ? 0x7fffffffffffffffll : co + cn;
+    const float fcn = __ll2float_rn(cn);
+    float alpha = t.alpha_min;
+    if (t.blend_mode == 0) alpha = fmaxf(sqrtf(__fdiv_rn(fcn, __ll2float_rn(ctot))), t.alpha_min);
+    const float keep = 1.0f - alpha;
+    float4 L = t.lst[s];
+    L.x = fmaf(alpha, __fdiv_rn(__ll2float_rn(a01.x), fcn), keep * L.x);
+    L.y = fmaf(alpha, __fdiv_rn(__ll2float_rn(a01.y), fcn), keep * L.y);
+    L.z = fmaf(alpha, __fdiv_rn(__ll2float_rn(a23.x), fcn), keep * L.z);
+    t.lst[s] = L;
+    t.cold[s] = ctot;
+    __stcg(wp, z);
+    __stcg(wp + 1, z);
+    if (t.mirror) t.mirror[s] = pack_half4(L.x, L.y, L.z);
+}
+
+// Position of the n-th (0-based) set bit of w (n < popc(w)).
+__device__ __forceinline__ unsigned select_bit(unsigned w, unsigned n) {
+    unsigned pos = 0;
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        const unsigned low = __popc(w & ((1u << sh) - 1u));
+        if (n >= low) {
+            n -= low;
+            w >>= sh;
+            pos += sh;
+        }
+    }
+    return pos;
+}
+
+// One warp blends every touched slot of dirty words [w0, w0 + 32): the set bits are
+// compacted across the warp (prefix sum of popcounts) so all 32 lanes stay busy.
+// Returns the number of cells blended (the same value in every lane).
+__device__ __forceinline__ unsigned update_words(const TableView& t, unsigned long long w0, unsigned long long nwords) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long wi = w0 + lane;
+    unsigned word = wi < nwords ? __ldcg(t.dirty + wi) : 0u;
+    if (word) t.dirty[wi] = 0u;
+    const unsigned cnt = __popc(word);
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned x = __shfl_up_sync(kFull, incl, o);
+        if (lane >= static_cast<unsigned>(o)) incl += x;
+    }
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    const unsigned excl = incl - cnt;
+    for (unsigned r = 0; r < total; r += 32) {
+        const unsigned idx = r + lane;
+        unsigned owner = 0;  // number of lanes whose inclusive count is <= idx
+#pragma unroll
+        for (unsigned step = 16; step > 0; step >>= 1) {
+            const unsigned v = __shfl_sync(kFull, incl, owner + step - 1);
+            if (v <= idx) owner += step;
+        }
+        owner &= 31u;
+        const unsigned ow = __shfl_sync(kFull, word, owner);
+        const unsigned oe = __shfl_sync(kFull, excl, owner);
+        if (idx < total) blend_slot(t, (w0 + owner) * 32ull + select_bit(ow, idx - oe));
+    }
+    return total;
+}
+
+// ---------------------------------------------------------------------------
+// Control-variate query: Section "Control variates", equation CVEstimator.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 cell_value(const TableView& t, const float4& v0, const float4& v1,
+                                             const float4& v2) {
+    float3 c = make_float3(0.0f, 0.0f, 0.0f);
+    unsigned long long key;
+    if (!cell_key(t, v0, v1, v2, &key)) return c;
+    const long long s = probe_find(t, key);
+    if (s < 0) return c;
+    if (t.mirror) {
+        const uint2 h = __ldcg(t.mirror + s);
+        c.x = __half2float(__ushort_as_half(static_cast<unsigned short>(h.x & 0xffffu)));
+        c.y = __half2float(__ushort_as_half(static_cast<unsigned short>(h.x >> 16)));
+        c.z = __half2float(__ushort_as_half(static_cast<unsigned short>(h.y & 0xffffu)));
+    } else {
+        const float4 L = __ldcg(t.lst + s);
+        c = make_float3(L.x, L.y, L.z);
+    }
+    return c;
+}
+
+// out_j = L_j - beta * t_j * C_{j+1} + beta * C_j  (or L_j without a control variate)
+__device__ __forceinline__ float cv_combine(float L, float tj, float c_next, float c_self, float beta) {
+    const float h = __fmul_rn(tj, c_next);
+    return __fadd_rn(__fsub_rn(L, __fmul_rn(beta, h)), __fmul_rn(beta, c_self));
+}
+
+}  // namespace psf

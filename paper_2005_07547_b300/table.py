@@ -1,0 +1,123 @@
+"""Python view of one filtering table (one render session) over the C ABI.
+
+PyTorch supplies the device memory (the caching allocator) and the stream; every
+step of the computation runs in the CUDA library.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _check_vertices(verts, what: str):
+    import torch
+
+    if not isinstance(verts, torch.Tensor) or not verts.is_cuda:
+        raise TypeError(f"{what}: vertices must be a CUDA tensor")
+    if verts.dtype != torch.float32 or verts.dim() != 2 or verts.shape[1] != 16 or not verts.is_contiguous():
+        raise ValueError(f"{what}: vertices must be a contiguous (n, 16) float32 tensor")
+
+
+class Table:
+    """A spatio-directional field table in caller-owned (torch) device memory."""
+
+    def __init__(self, cfg: _abi.Config | None = None, device=None, stream=None, **kw):
+        import torch
+
+        lib = _abi.load()
+        self.cfg = cfg if cfg is not None else _abi.make_config(**kw)
+        self.nbytes = int(lib.psf_table_bytes(ctypes.byref(self.cfg)))
+        if self.nbytes == 0:
+            raise ValueError("invalid psf configuration")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        _abi.check(lib.psf_create(ctypes.byref(self.cfg), self.mem.data_ptr(), self.nbytes,
+                                  _stream_handle(stream), ctypes.byref(h)), "psf_create")
+        self._h = h
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def insert(self, verts, stream=None) -> None:
+        _check_vertices(verts, "insert")
+        _abi.check(_abi.load().psf_insert(self._h, verts.data_ptr(), verts.shape[0], _stream_handle(stream)),
+                   "psf_insert")
+
+    def update(self, stream=None) -> int:
+        return _abi.check(_abi.load().psf_update(self._h, _stream_handle(stream)), "psf_update")
+
+    def query_cv(self, verts, P: int, D: int, out=None, stream=None):
+        import torch
+
+        _check_vertices(verts, "query_cv")
+        if verts.shape[0] != P * D:
+            raise ValueError("query_cv: vertex count must be P*D")
+        if out is None:
+            out = torch.empty((P * D, 3), dtype=torch.float32, device=verts.device)
+        _abi.check(_abi.load().psf_query_cv(self._h, verts.data_ptr(), P, D, out.data_ptr(),
+                                            _stream_handle(stream)), "psf_query_cv")
+        return out
+
+    def step(self, verts, P: int, D: int, out=None, stream=None):
+        import torch
+
+        _check_vertices(verts, "step")
+        if verts.shape[0] != P * D:
+            raise ValueError("step: vertex count must be P*D")
+        if out is None:
+            out = torch.empty((P * D, 3), dtype=torch.float32, device=verts.device)
+        _abi.check(_abi.load().psf_step(self._h, verts.data_ptr(), P, D, out.data_ptr(), _stream_handle(stream)),
+                   "psf_step")
+        return out
+
+    def reset(self, stream=None) -> None:
+        _abi.check(_abi.load().psf_reset(self._h, _stream_handle(stream)), "psf_reset")
+
+    def export(self, stream=None) -> np.ndarray:
+        """All occupied cells in ascending key order (synchronises the stream)."""
+        lib = _abi.load()
+        n = ctypes.c_size_t()
+        rc = lib.psf_export(self._h, None, 0, ctypes.byref(n), _stream_handle(stream))
+        if rc not in (_abi.PSF_OK, _abi.PSF_ERR_NO_MEM):
+            _abi.check(rc, "psf_export")
+        out = np.zeros(n.value, dtype=_abi.CELL_DTYPE)
+        if n.value:
+            got = ctypes.c_size_t()
+            _abi.check(lib.psf_export(self._h, out.ctypes.data, n.value, ctypes.byref(got), _stream_handle(stream)),
+                       "psf_export")
+            out = out[:got.value]
+        return out
+
+    def stats(self, stream=None) -> dict:
+        st = _abi.Stats()
+        _abi.check(_abi.load().psf_get_stats(self._h, ctypes.byref(st), _stream_handle(stream)), "psf_get_stats")
+        return st.as_dict()
+
+    def close(self) -> None:
+        """Wait for the table's work, then release it."""
+        import torch
+
+        if getattr(self, "_h", None) is not None and self._h.value:
+            torch.cuda.synchronize(self.device)
+            _abi.load().psf_destroy(self._h)
+            self._h = ctypes.c_void_p()
+        self.mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

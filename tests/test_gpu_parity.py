@@ -1,0 +1,252 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Small workloads are compared in full every iteration (tables after insert and after
+update, CV outputs); the full-size 1280x720 and 1920x1080 workloads are compared in
+full for their first iterations, in the launch configuration the benchmark times
+(psf_step: insert, update, query on one stream).
+"""
+
+import numpy as np
+import pytest
+
+from helpers import random_vertices, stack, vertex
+from parity import check_after_insert, check_after_update, check_cv
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_for(oracle_mod, cfg):
+    return oracle_mod.Oracle(pos_bits=cfg.pos_bits_q, dir_bits=cfg.dir_bits_d, use_normal=bool(cfg.use_normal),
+                             frac_bits=cfg.frac_bits, blend_mode=cfg.blend_mode, cv_max_depth=cfg.cv_max_depth,
+                             alpha_min=float(np.float32(cfg.alpha_min)), beta=float(np.float32(cfg.beta)))
+
+
+def _run_and_compare(psf, oracle_mod, cfg, batches, P, D, *, check_insert=True, use_step=False):
+    """Drive a GPU table and the oracle through the same iterations; compare everything."""
+    import torch
+
+    table = psf.Table(cfg)
+    ora = _oracle_for(oracle_mod, cfg)
+    worst = {"L32": 0.0, "L16": 0.0, "cv": 0.0}
+    for v in batches:
+        dv = torch.from_numpy(v).cuda()
+        st = ora.insert(v)
+        if use_step:
+            out = table.step(dv, P, D)
+        else:
+            table.insert(dv)
+            if check_insert:
+                check_after_insert(table.export(), ora.export())
+            table.update()
+            out = table.query_cv(dv, P, D)
+        ora.update()
+        r32, r16 = check_after_update(table.export(), ora.export(), fp16=bool(cfg.cache_fp16))
+        worst["L32"] = max(worst["L32"], r32)
+        worst["L16"] = max(worst["L16"], r16 or 0.0)
+        ref = ora.query_cv(v, P, D)
+        worst["cv"] = max(worst["cv"], check_cv(out.cpu().numpy(), ref, v, ora.lookup(v), P, D, float(cfg.beta),
+                                                cfg.cv_max_depth, ora.export()["L"], fp16=bool(cfg.cache_fp16)))
+        stats = table.stats()
+        dropped, zero_w = ora.counters()
+        assert stats["dropped_vertices"] == dropped and stats["zero_weight_vertices"] == zero_w
+        assert stats["status"] == st or (stats["status"] & ~psf.STATUS_RANGE) == 0
+        assert stats["live_cells"] == len(ora)
+    table.close()
+    return worst
+
+
+def _workload_batches(name, iterations, seed_offset=0):
+    from synth.scene import iteration_vertices, make_scene, workload
+
+    w = workload(name)
+    scene = make_scene(w["seed"])
+    return w, [iteration_vertices(w, it + seed_offset, scene) for it in range(iterations)]
+
+
+def _cfg_for(psf, w, **over):
+    kw = dict(log2_capacity=w["log2_capacity"], pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],
+              alpha_min=w["alpha_min"], cache_fp16=w["cache_fp16"])
+    kw.update(over)
+    return psf.make_config(**kw)
+
+
+@pytest.mark.parametrize("fp16", [False, True])
+def test_64x64_depth3_all_iterations(psf_mod, oracle_mod, fp16):
+    w, batches = _workload_batches("64x64_d3", 8)
+    worst = _run_and_compare(psf_mod, oracle_mod, _cfg_for(psf_mod, w, cache_fp16=fp16), batches,
+                             w["width"] * w["height"], w["depth"])
+    print("worst relative errors", worst)
+
+
+@pytest.mark.parametrize("over", [dict(use_normal=False), dict(blend_mode=1), dict(cv_max_depth=1),
+                                  dict(beta=0.5), dict(frac_bits=16), dict(frac_bits=32), dict(dir_bits=5, pos_bits=6),
+                                  dict(dir_bits=0), dict(alpha_min=0.0)])
+def test_configuration_variants(psf_mod, oracle_mod, over):
+    w, batches = _workload_batches("64x64_d3", 3)
+    _run_and_compare(psf_mod, oracle_mod, _cfg_for(psf_mod, w, **over), batches, w["width"] * w["height"], w["depth"])
+
+
+def test_reset_and_multiple_inserts_per_iteration(psf_mod, oracle_mod):
+    import torch
+
+    w, batches = _workload_batches("64x64_d3", 4)
+    cfg = _cfg_for(psf_mod, w)
+    table = psf_mod.Table(cfg)
+    ora = _oracle_for(oracle_mod, cfg)
+    P, D = w["width"] * w["height"], w["depth"]
+    for it, v in enumerate(batches):
+        if it == 2:
+            table.reset()
+            ora.reset()
+        dv = torch.from_numpy(v).cuda()
+        cuts = [0, 1, 4097, 9000, len(v)]  # ragged pieces, one of a single vertex
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            table.insert(dv[a:b])
+        ora.insert(v)
+        check_after_insert(table.export(), ora.export())
+        table.update()
+        ora.update()
+        check_after_update(table.export(), ora.export())
+        out = table.query_cv(dv, P, D)
+        check_cv(out.cpu().numpy(), ora.query_cv(v, P, D), v, ora.lookup(v), P, D, 1.0, cfg.cv_max_depth,
+                 ora.export()["L"])
+    table.close()
+
+
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 255, 256, 257, 4103, 70001])
+def test_ragged_sizes_and_duplicates(psf_mod, oracle_mod, n):
+    rng = np.random.default_rng(n)
+    v = random_vertices(rng, n, q=3, cells_per_axis=4, zero_weight_fraction=0.02)
+    cfg = psf_mod.make_config(log2_capacity=14, pos_bits=3, dir_bits=2)
+    # P paths of depth D with P*D = n where possible, else D = 1
+    D = 1
+    for d in (4, 3, 2):
+        if n % d == 0:
+            D = d
+            break
+    _run_and_compare(psf_mod, oracle_mod, cfg, [v, v[::-1].copy()], n // D, D)
+
+
+def test_edge_cases(psf_mod, oracle_mod):
+    import torch
+
+    cfg = psf_mod.make_config(log2_capacity=10, pos_bits=4, dir_bits=2)
+    recs = [
+        vertex((0.0, 0.0, 0.0)), vertex((1.0, 1.0, 1.0)), vertex((0.5, 0.25, 0.75)),  # cell faces
+        vertex((-0.03125, 0.5, 0.5), n=(0, -1, 0), d=(0, 0, -1)),
+        vertex((0.3, 0.3, 0.3), d=(1.0, 0.0, 0.0)), vertex((0.3, 0.3, 0.3), d=(-1.0, 0.0, 0.0)),
+        vertex((0.3, 0.3, 0.3), d=(0.0, 1.0, 0.0)), vertex((0.3, 0.3, 0.3), d=(0.0, -1.0, 0.0)),
+        vertex((0.3, 0.3, 0.3), d=(0.0, 0.0, 1.0)), vertex((0.3, 0.3, 0.3), d=(0.0, 0.0, -1.0)),
+        vertex((0.3, 0.3, 0.3), d=(-0.0, -0.0, -1.0)), vertex((0.3, 0.3, 0.3), n=(1, 1, 0), d=(0.6, -0.8, 0.0)),
+        vertex((-2048.0, 0.0, 0.0)), vertex((2047.99, 0.0, 0.0)),  # extreme valid cells
+        vertex((0.5, 0.5, 0.5), L=(np.nan, 1.0, 1.0)), vertex((0.5, 0.5, 0.5), L=(1.0, np.inf, 1.0)),
+        vertex((0.5, 0.5, 0.5), w=2.0, L=(1.0, 1.0, 20000.0)), vertex((0.5, 0.5, 0.5), w=-0.5),
+        vertex((0.5, 0.5, 0.5), w=40000.0), vertex((4096.0, 0.5, 0.5)), vertex((np.nan, 0.5, 0.5)),
+        vertex((0.5, 0.5, 0.5), d=(0.0, 0.0, 0.0)), vertex((0.5, 0.5, 0.5), n=(np.inf, 0, 0)),
+        vertex((0.5, 0.5, 0.5), w=2.0 ** -30), vertex((0.5, 0.5, 0.5), w=0.0),
+        vertex((0.5, 0.5, 0.5), w=1.0, L=(32768.0, -32768.0, 0.0)),
+    ]
+    v = stack(recs)
+    P, D = len(recs), 1
+    table = psf_mod.Table(cfg)
+    ora = _oracle_for(oracle_mod, cfg)
+    # empty iteration and a query of an empty table
+    table.insert(torch.zeros((0, 16), dtype=torch.float32, device="cuda"))
+    out0 = table.query_cv(torch.from_numpy(v).cuda(), P, D)
+    assert np.array_equal(out0.cpu().numpy(), v[:, 12:15])
+    st_ref = ora.insert(v)
+    table.insert(torch.from_numpy(v).cuda())
+    check_after_insert(table.export(), ora.export())
+    table.update()
+    ora.update()
+    check_after_update(table.export(), ora.export())
+    stats = table.stats()
+    assert stats["status"] == st_ref == psf_mod.STATUS_RANGE
+    assert (stats["dropped_vertices"], stats["zero_weight_vertices"]) == ora.counters()
+    # depth-2 query over pairs to exercise the CV terms on the edge vertices
+    v2 = np.concatenate([v[:12], v[12:24]])
+    out = table.query_cv(torch.from_numpy(v2).cuda(), 12, 2)
+    check_cv(out.cpu().numpy(), ora.query_cv(v2, 12, 2), v2, ora.lookup(v2), 12, 2, 1.0, cfg.cv_max_depth,
+             ora.export()["L"])
+    # the status seen by update() is the sticky bit, copied back without a sync
+    table.insert(torch.from_numpy(v).cuda())
+    table.update()
+    torch.cuda.synchronize()
+    assert table.update() & psf_mod.STATUS_RANGE
+    table.close()
+
+
+def test_table_full_is_reported_and_bounded(psf_mod):
+    import torch
+
+    cfg = psf_mod.make_config(log2_capacity=4, pos_bits=4, dir_bits=2)
+    recs = [vertex(((i % 8) / 16.0 + 0.01, (i // 8) / 16.0 + 0.01, 0.5)) for i in range(40)]
+    table = psf_mod.Table(cfg)
+    table.insert(torch.from_numpy(stack(recs)).cuda())
+    table.update()
+    st = table.stats()
+    assert st["status"] & psf_mod.STATUS_TABLE_FULL
+    assert st["live_cells"] == 16 and st["dropped_vertices"] == 40 - 16
+    assert st["max_probe"] == 16
+    rec = table.export()
+    assert len(rec) == 16 and int(rec["c_old"].sum()) == 16 << 24
+    table.close()
+
+
+def test_deterministic_tables_and_outputs(psf_mod):
+    import torch
+
+    w, batches = _workload_batches("64x64_d3", 3)
+    cfg = _cfg_for(psf_mod, w, cache_fp16=True)
+    P, D = w["width"] * w["height"], w["depth"]
+    exports, outs = [], []
+    for rep in range(2):
+        table = psf_mod.Table(cfg)
+        o = []
+        for v in batches:
+            dv = torch.from_numpy(v if rep == 0 else v[np.r_[P * D - 1:-1:-1]].copy()).cuda()  # reversed order
+            table.insert(dv)
+            table.update()
+            o.append(table.query_cv(torch.from_numpy(v).cuda(), P, D).cpu().numpy())
+        exports.append(table.export().tobytes())
+        outs.append(np.concatenate(o).tobytes())
+        table.close()
+    assert exports[0] == exports[1]
+    assert outs[0] == outs[1]
+
+
+@pytest.mark.slow
+def test_1280x720_depth4_full_size(psf_mod, oracle_mod):
+    w, batches = _workload_batches("1280x720_d4", 3)
+    worst = _run_and_compare(psf_mod, oracle_mod, _cfg_for(psf_mod, w), batches, w["width"] * w["height"],
+                             w["depth"], use_step=True)
+    print("worst relative errors", worst)
+
+
+@pytest.mark.slow
+def test_1920x1080_depth5_full_size_fp32_and_fp16(psf_mod, oracle_mod):
+    """Both caches against one FP64 oracle run (the oracle has no cache precision)."""
+    import torch
+
+    w, batches = _workload_batches("1920x1080_d5", 2)
+    P, D = w["width"] * w["height"], w["depth"]
+    tables = {fp16: psf_mod.Table(_cfg_for(psf_mod, w, cache_fp16=fp16)) for fp16 in (False, True)}
+    ora = _oracle_for(oracle_mod, _cfg_for(psf_mod, w))
+    errs = {}
+    for v in batches:
+        dv = torch.from_numpy(v).cuda()
+        outs = {fp16: t.step(dv, P, D) for fp16, t in tables.items()}
+        ora.insert(v)
+        ora.update()
+        ref_rec = ora.export()
+        ref = ora.query_cv(v, P, D)
+        C = ora.lookup(v)
+        for fp16, t in tables.items():
+            r32, r16 = check_after_update(t.export(), ref_rec, fp16=fp16)
+            rc = check_cv(outs[fp16].cpu().numpy(), ref, v, C, P, D, 1.0, 0xFFFFFFFF, ref_rec["L"], fp16=fp16)
+            errs[fp16] = (r32, r16, rc)
+        del dv, outs
+    for t in tables.values():
+        assert t.stats()["status"] == 0
+        t.close()
+    print("worst error/bound ratios (fp32 L, fp16 L, cv):", errs)
