@@ -22,9 +22,7 @@ import math
 import multiprocessing as mp
 import os
 import statistics
-import subprocess
 import sys
-import tempfile
 import time
 
 import numpy as np
@@ -36,6 +34,7 @@ if ROOT not in sys.path:
 METRIC = "path vertices filtered/sec (insert+update+query)"
 UNIT = "vertices/s"
 DEFAULT_WORKLOAD = "1280x720_d4"
+POOL = 40  # distinct input batches kept resident; longer runs cycle through them
 KERNEL_SOURCES = ["paper_2005_07547_b300/csrc/psf.cu", "paper_2005_07547_b300/csrc/psf_device.cuh"]
 
 
@@ -110,59 +109,76 @@ def load_traffic(kernel: str) -> float | None:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """SM clocks and clock-event (throttle) reasons sampled through NVML every millisecond
+    by a background thread while the timed region runs (read-only queries)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.path = None
+    def __init__(self, cuda_index: int, period_s: float = 0.001):
+        self.cuda_index = cuda_index
+        self.period = period_s
+        self.samples = []
+        self.max_mhz = None
+        self.error = None
+        self._stop = None
+        self._thread = None
+
+    def _handle(self, nv):
+        try:
+            import torch
+
+            p = torch.cuda.get_device_properties(self.cuda_index)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+            return nv.nvmlDeviceGetHandleByPciBusId(bus)
+        except Exception:
+            return nv.nvmlDeviceGetHandleByIndex(self.cuda_index)
 
     def __enter__(self):
-        fd, self.path = tempfile.mkstemp(suffix=".csv")
-        os.close(fd)
+        import threading
+
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
-        except OSError:
-            self.proc = None
+            import pynvml as nv
+
+            nv.nvmlInit()
+            h = self._handle(nv)
+            self.max_mhz = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        except Exception as e:  # no NVML: report unsampled
+            self.error = repr(e)
+            return self
+        self._stop = threading.Event()
+
+        def loop():
+            while not self._stop.is_set():
+                try:
+                    self.samples.append((nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM),
+                                         nv.nvmlDeviceGetCurrentClocksEventReasons(h),
+                                         nv.nvmlDeviceGetPowerUsage(h) / 1000.0))
+                except Exception as e:
+                    self.error = repr(e)
+                    return
+                self._stop.wait(self.period)
+
+        self._thread = threading.Thread(target=loop, daemon=True)
+        self._thread.start()
         return self
 
     def __exit__(self, *exc):
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join(timeout=5)
 
     def summary(self) -> dict:
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        try:
-            with open(self.path) as f:
-                for line in f:
-                    parts = [p.strip() for p in line.split(",")]
-                    if len(parts) < 9:
-                        continue
-                    try:
-                        sm.append(float(parts[1]))
-                        mx.append(float(parts[2]))
-                    except ValueError:
-                        continue
-                    for name, val in zip(names, parts[5:9]):
-                        if val.lower() == "active":
-                            reasons.add(name)
-        finally:
-            os.unlink(self.path)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"], "error": self.error}
+        reasons = set()
+        for _, mask, _ in self.samples:
+            for bit, name in self.REASONS.items():
+                if mask & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(s[0] for s in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(self.samples),
+                "power_w_max": max(s[2] for s in self.samples), "source": "nvml, 1 ms"}
 
 
 # ---------------------------------------------------------------------------
@@ -264,7 +280,7 @@ def run_psf(args) -> None:
     P, D = w["width"] * w["height"], w["depth"]
     V = P * D
     off = rank_seed_offset(rank)
-    n_iter = args.warmup + args.steps
+    n_iter = min(args.warmup + args.steps, POOL)
     host = generate(args.workload, [off + i for i in range(n_iter)], os.cpu_count() or 1)
     cpu_sample = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -282,14 +298,15 @@ def run_psf(args) -> None:
     cfg = psf.make_config(log2_capacity=w["log2_capacity"], pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],
                           alpha_min=w["alpha_min"], cache_fp16=args.fp16 or w["cache_fp16"])
     table = psf.Table(cfg)
+    table.set_launch(insert_mode=args.insert_mode)
     dev = [torch.from_numpy(v).cuda() for v in host]
     out = torch.empty((V, 3), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     for k in range(args.warmup):
-        table.insert(dev[k])
+        table.insert(dev[k % n_iter])
         table.update()
-        table.query_cv(dev[k], P, D, out=out)
+        table.query_cv(dev[k % n_iter], P, D, out=out)
     torch.cuda.synchronize()
     before = table.stats()
 
@@ -301,7 +318,7 @@ def run_psf(args) -> None:
     with ClockSampler(local) as clocks:
         start.record(stream)
         for k in range(args.steps):
-            v = dev[args.warmup + k]
+            v = dev[(args.warmup + k) % n_iter]
             e = ev[k]
             e[0].record(stream)
             table.insert(v)
@@ -362,7 +379,9 @@ def run_psf(args) -> None:
         "config": {"workload": w["name"], "paths": P, "depth": D, "vertices_per_step": V,
                    "log2_capacity": w["log2_capacity"], "cache": "fp16" if fp16 else "fp32",
                    "touched_cells_per_step": touched, "live_cells": after["live_cells"],
-                   "l2": "inputs larger than L2: a fresh 236 MB vertex batch every step",
+                   "l2": f"inputs larger than L2: {n_iter} distinct {V * 64 / 1e6:.0f} MB vertex batches, "
+                         "a different one every step",
+                   "insert_mode": args.insert_mode,
                    "parallelism": f"sessions x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "mean": float(np.mean(step_ms))},
@@ -425,13 +444,14 @@ def run_e2e(psf, table, host: list[np.ndarray], P: int, D: int, steps: int) -> d
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--impl", default="psf", choices=["psf", "reference"])
     ap.add_argument("--fp16", action="store_true", help="FP16 copy of the approximant for the query")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--insert-mode", type=int, default=0, help="0: warp aggregation of equal keys; 1: none")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps are required")

@@ -162,6 +162,20 @@ int psf_get_stats(psf_table* t, psf_stats* out, void* stream);
  * have completed (synchronise its stream first), as for freeing d_mem.  NULL is a no-op. */
 int psf_destroy(psf_table* t);
 
+/* Launch knobs of a table's kernels (the autotuner's search space).  Results do not
+ * depend on them: the integer sums are order-independent.  Zero fields mean "default". */
+typedef struct {
+    uint32_t insert_mode;          /* 0: lanes of a warp holding the same key are merged (match_any)
+                                      and one leader probes and adds; 1: every vertex adds on its own */
+    uint32_t insert_blocks_per_sm; /* cap on resident 256-thread blocks per SM (0 = occupancy limit) */
+    uint32_t update_blocks_per_sm;
+    uint32_t query_blocks_per_sm;
+} psf_launch_config;
+
+/* Set / read the launch knobs of a table (host-side only; affects later calls). */
+int psf_set_launch_config(psf_table* t, const psf_launch_config* cfg);
+int psf_get_launch_config(const psf_table* t, psf_launch_config* out);
+
 /* Text of the last CUDA error seen by this thread's calls (empty if none). */
 const char* psf_last_cuda_error(void);
 

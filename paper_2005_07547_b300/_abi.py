@@ -73,6 +73,17 @@ class Stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class LaunchConfig(ctypes.Structure):
+    """psf_launch_config."""
+
+    _fields_ = [
+        ("insert_mode", ctypes.c_uint32),
+        ("insert_blocks_per_sm", ctypes.c_uint32),
+        ("update_blocks_per_sm", ctypes.c_uint32),
+        ("query_blocks_per_sm", ctypes.c_uint32),
+    ]
+
+
 # psf_cell_record as a numpy structured dtype (72 bytes: 68 of fields, padded to 8-byte alignment)
 CELL_DTYPE = np.dtype([("key", "<u8"), ("sum", "<i8", (3,)), ("c_new", "<i8"), ("c_old", "<i8"),
                        ("L", "<f4", (3,)), ("L_fp16", "<u2", (3,)), ("pad", "<u2")], align=True)
@@ -93,6 +104,8 @@ SIGNATURES = {
     "psf_export": (_i, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _vp]),
     "psf_get_stats": (_i, [_vp, ctypes.POINTER(Stats), _vp]),
     "psf_destroy": (_i, [_vp]),
+    "psf_set_launch_config": (_i, [_vp, ctypes.POINTER(LaunchConfig)]),
+    "psf_get_launch_config": (_i, [_vp, ctypes.POINTER(LaunchConfig)]),
 }
 
 _lib = None

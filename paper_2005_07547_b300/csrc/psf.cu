@@ -22,8 +22,8 @@
 #include "psf.h"
 #include "psf_device.cuh"
 
-using psf::Acc;
 using psf::DevHeader;
+using psf::Slot;
 using psf::TableView;
 
 namespace {
@@ -42,9 +42,10 @@ struct psf_table {
     unsigned* h_status;  // host-mapped pinned word written by k_update
     int device;
     int sms;
-    int insert_blocks_per_sm;
+    int insert_blocks_per_sm;  // occupancy limits of the kernels
     int update_blocks_per_sm;
     int query_blocks_per_sm;
+    psf_launch_config launch;  // tuning knobs (psf_set_launch_config)
 };
 
 namespace {
@@ -56,7 +57,7 @@ bool cuda_ok(cudaError_t e, const char* what) {
 }
 
 struct Layout {
-    size_t hdr, keys, acc, lst, cold, mirror, dirty, total;
+    size_t hdr, keys, slots, mirror, dirty, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -79,12 +80,8 @@ Layout layout_of(const psf_config* c) {
     off = align256(off + sizeof(DevHeader));
     L.keys = off;
     off = align256(off + cap * sizeof(unsigned long long));
-    L.acc = off;
-    off = align256(off + cap * sizeof(Acc));
-    L.lst = off;
-    off = align256(off + cap * sizeof(float4));
-    L.cold = off;
-    off = align256(off + cap * sizeof(long long));
+    L.slots = off;
+    off = align256(off + cap * sizeof(Slot));
     L.mirror = off;
     if (c->cache_fp16) off = align256(off + cap * sizeof(uint2));
     L.dirty = off;
@@ -93,7 +90,8 @@ Layout layout_of(const psf_config* c) {
     return L;
 }
 
-int grid_for(const psf_table* t, int per_sm, unsigned long long work_items) {
+int grid_for(const psf_table* t, int per_sm, unsigned long long work_items, uint32_t limit = 0) {
+    if (limit && static_cast<int>(limit) < per_sm) per_sm = static_cast<int>(limit);
     const unsigned long long need = (work_items + kThreads - 1) / kThreads;
     const unsigned long long full = static_cast<unsigned long long>(t->sms) * static_cast<unsigned long long>(per_sm);
     return static_cast<int>(std::max<unsigned long long>(1, std::min(need, full)));
@@ -105,6 +103,7 @@ int grid_for(const psf_table* t, int per_sm, unsigned long long work_items) {
 // Kernels
 // ---------------------------------------------------------------------------
 
+template <int kMode>
 __global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* __restrict__ v, unsigned long long n) {
     __shared__ unsigned s_max_probe;
     if (threadIdx.x == 0) s_max_probe = 0;
@@ -116,13 +115,13 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* 
         const bool valid = i < n;
         float4 v0 = make_float4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
         if (valid) {
-            const float4* r = v + 4 * i;
-            v0 = __ldg(r);
-            v1 = __ldg(r + 1);
-            v2 = __ldg(r + 2);
-            v3 = __ldg(r + 3);
+            const float4* r = v + 4 * i;  // streamed once: evict-first
+            v0 = __ldcs(r);
+            v1 = __ldcs(r + 1);
+            v2 = __ldcs(r + 2);
+            v3 = __ldcs(r + 3);
         }
-        psf::insert_warp(t, valid, v0, v1, v2, v3, &max_len);
+        psf::insert_warp<kMode>(t, valid, v0, v1, v2, v3, &max_len);
     }
     if (max_len) atomicMax(&s_max_probe, max_len);
     __syncthreads();
@@ -157,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_query(TableView t, const float4* _
         for (int j = static_cast<int>(D) - 1; j >= 0; --j) {
             const unsigned long long i = static_cast<unsigned long long>(j) * P + p;
             const float4* r = v + 4 * i;
-            const float4 v0 = __ldg(r), v1 = __ldg(r + 1), v2 = __ldg(r + 2), v3 = __ldg(r + 3);
+            const float4 v0 = __ldcs(r), v1 = __ldcs(r + 1), v2 = __ldcs(r + 2), v3 = __ldcs(r + 3);
             const float3 c = psf::cell_value(t, v0, v1, v2);
             float o0 = v3.x, o1 = v3.y, o2 = v3.z;
             if (j + 1 < static_cast<int>(D) && static_cast<unsigned>(j) < t.cv_max_depth) {
@@ -191,13 +190,13 @@ __global__ void __launch_bounds__(kThreads) k_export(TableView t, unsigned long 
         if (!live) continue;
         psf_cell_record r;
         r.key = key;
-        const Acc a = t.acc[s];
+        const Slot& a = t.slots[s];
         r.sum[0] = a.s[0];
         r.sum[1] = a.s[1];
         r.sum[2] = a.s[2];
         r.c_new = a.c;
-        r.c_old = t.cold[s];
-        const float4 L = t.lst[s];
+        r.c_old = a.c_old;
+        const float4 L = a.L;
         r.L[0] = L.x;
         r.L[1] = L.y;
         r.L[2] = L.z;
@@ -226,6 +225,14 @@ __global__ void __launch_bounds__(kThreads) k_count_live(TableView t, unsigned l
     if (mine) atomicAdd(&s_count, mine);
     __syncthreads();
     if (threadIdx.x == 0 && s_count) atomicAdd(count, s_count);
+}
+
+// Global counter reset: c_old := 0 in every slot (the approximant is kept).
+__global__ void __launch_bounds__(kThreads) k_reset(TableView t) {
+    const unsigned long long cap = 1ull << t.log2cap;
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+    for (unsigned long long s = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; s < cap; s += stride)
+        t.slots[s].c_old = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -258,7 +265,8 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     t->bytes = bytes;
     if (!cuda_ok(cudaGetDevice(&t->device), "cudaGetDevice") ||
         !cuda_ok(cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device), "cudaDeviceGetAttribute") ||
-        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->insert_blocks_per_sm, k_insert, kThreads, 0), "occupancy") ||
+        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->insert_blocks_per_sm, k_insert<psf::kAggWarp>, kThreads, 0),
+                 "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->update_blocks_per_sm, k_update, kThreads, 0), "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->query_blocks_per_sm, k_query, kThreads, 0), "occupancy") ||
         !cuda_ok(cudaHostAlloc(reinterpret_cast<void**>(&t->h_status), sizeof(unsigned), cudaHostAllocMapped),
@@ -267,13 +275,12 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
         return PSF_ERR_CUDA;
     }
     *t->h_status = 0;
+    t->launch = psf_launch_config{0u, 0u, 0u, 0u};
     char* base = static_cast<char*>(d_mem);
     TableView& v = t->view;
     v.hdr = reinterpret_cast<DevHeader*>(base + L.hdr);
     v.keys = reinterpret_cast<unsigned long long*>(base + L.keys);
-    v.acc = reinterpret_cast<Acc*>(base + L.acc);
-    v.lst = reinterpret_cast<float4*>(base + L.lst);
-    v.cold = reinterpret_cast<long long*>(base + L.cold);
+    v.slots = reinterpret_cast<Slot*>(base + L.slots);
     v.mirror = cfg->cache_fp16 ? reinterpret_cast<uint2*>(base + L.mirror) : nullptr;
     v.dirty = reinterpret_cast<unsigned*>(base + L.dirty);
     unsigned* dev_status = nullptr;
@@ -310,15 +317,20 @@ int psf_insert(psf_table* t, const float* d_vertices, uint64_t n, void* stream) 
     if (!t) return PSF_ERR_INVALID_ARG;
     if (n == 0) return PSF_OK;
     if (!d_vertices || (reinterpret_cast<uintptr_t>(d_vertices) & 15u)) return PSF_ERR_INVALID_ARG;
-    const int grid = grid_for(t, t->insert_blocks_per_sm, n);
-    k_insert<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view, reinterpret_cast<const float4*>(d_vertices), n);
+    const int grid = grid_for(t, t->insert_blocks_per_sm, n, t->launch.insert_blocks_per_sm);
+    const float4* v = reinterpret_cast<const float4*>(d_vertices);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (t->launch.insert_mode == 1)
+        k_insert<psf::kAggNone><<<grid, kThreads, 0, st>>>(t->view, v, n);
+    else
+        k_insert<psf::kAggWarp><<<grid, kThreads, 0, st>>>(t->view, v, n);
     return cuda_ok(cudaGetLastError(), "k_insert") ? PSF_OK : PSF_ERR_CUDA;
 }
 
 int psf_update(psf_table* t, void* stream) {
     if (!t) return PSF_ERR_INVALID_ARG;
     const unsigned long long nwords = ((1ull << t->cfg.log2_capacity) + 31ull) >> 5;
-    const int grid = grid_for(t, t->update_blocks_per_sm, nwords);  // one warp per 32 words
+    const int grid = grid_for(t, t->update_blocks_per_sm, nwords, t->launch.update_blocks_per_sm);  // a warp per 32 words
     k_update<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view);
     if (!cuda_ok(cudaGetLastError(), "k_update")) return PSF_ERR_CUDA;
     return static_cast<int>(*reinterpret_cast<volatile unsigned*>(t->h_status) & 0x7fffffffu);
@@ -330,7 +342,7 @@ int psf_query_cv(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, 
     if (!d_vertices || !d_out_rgb || (reinterpret_cast<uintptr_t>(d_vertices) & 15u) ||
         (reinterpret_cast<uintptr_t>(d_out_rgb) & 3u))
         return PSF_ERR_INVALID_ARG;
-    const int grid = grid_for(t, t->query_blocks_per_sm, P);
+    const int grid = grid_for(t, t->query_blocks_per_sm, P, t->launch.query_blocks_per_sm);
     k_query<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view, reinterpret_cast<const float4*>(d_vertices), P,
                                                                       D, d_out_rgb);
     return cuda_ok(cudaGetLastError(), "k_query") ? PSF_OK : PSF_ERR_CUDA;
@@ -346,11 +358,21 @@ int psf_step(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, floa
 
 int psf_reset(psf_table* t, void* stream) {
     if (!t) return PSF_ERR_INVALID_ARG;
-    const size_t cap = size_t{1} << t->cfg.log2_capacity;
-    return cuda_ok(cudaMemsetAsync(t->view.cold, 0, cap * sizeof(long long), static_cast<cudaStream_t>(stream)),
-                   "cudaMemsetAsync")
-               ? PSF_OK
-               : PSF_ERR_CUDA;
+    const unsigned long long cap = 1ull << t->cfg.log2_capacity;
+    k_reset<<<grid_for(t, 4, cap), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view);
+    return cuda_ok(cudaGetLastError(), "k_reset") ? PSF_OK : PSF_ERR_CUDA;
+}
+
+int psf_set_launch_config(psf_table* t, const psf_launch_config* c) {
+    if (!t || !c || c->insert_mode > 1) return PSF_ERR_INVALID_ARG;
+    t->launch = *c;
+    return PSF_OK;
+}
+
+int psf_get_launch_config(const psf_table* t, psf_launch_config* out) {
+    if (!t || !out) return PSF_ERR_INVALID_ARG;
+    *out = t->launch;
+    return PSF_OK;
 }
 
 int psf_export(psf_table* t, psf_cell_record* h_out, size_t cap_out, size_t* n_out, void* stream) {

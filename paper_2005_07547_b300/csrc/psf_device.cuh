@@ -3,14 +3,14 @@
 // Table memory (one contiguous caller-owned allocation, every array 256-byte aligned):
 //   DevHeader                       status word and counters
 //   keys   u64[cap]                 packed cell key or kEmpty (open addressing, linear probe)
-//   acc    Acc[cap]   (32 B)        this iteration's fixed-point sums and counter c_new
-//   lst    float4[cap](16 B)        the FP32 approximant (r, g, b, 0)
-//   cold   i64[cap]                 cumulative counter c_old
-//   mirror uint2[cap] (8 B)         FP16 copy of the approximant (only with cache_fp16)
+//   slots  Slot[cap]  (64 B)        sums + c_new (bytes 0-31), approximant L~ (32-47),
+//                                   c_old (48-55): one aligned 64-byte block per cell
+//   mirror uint2[cap] (8 B)         FP16 copy of L~ (only with cache_fp16)
 //   dirty  u32[cap/32]              one bit per slot: touched this iteration
-// The split keeps every per-slot access inside one 32-byte sector: inserts touch
-// keys + acc, the update touches acc + lst + cold (+ mirror), queries touch keys +
-// lst (or mirror).
+// Inserts touch keys + the first 32-byte sector of a slot (atomics); the blend reads and
+// writes exactly one 64-byte block per touched cell, the DRAM access granularity, so
+// scattered cells cost no partial bursts; queries read keys + the second sector of the
+// slot (FP32) or the compact 8-byte FP16 copy.
 
 #pragma once
 
@@ -39,17 +39,23 @@ struct DevHeader {
 };
 static_assert(sizeof(DevHeader) == 256, "header is one 256-byte block");
 
-struct alignas(32) Acc {
-    long long s[3];
-    long long c;
+struct alignas(64) Slot {
+    long long s[3];  // this iteration's sum of round(w L_c 2^F)
+    long long c;     // this iteration's counter c_new = sum of round(w 2^F)
+    float4 L;        // the approximant (r, g, b, unused)
+    long long c_old; // cumulative counter of blended iterations
+    long long spare;
 };
+static_assert(sizeof(Slot) == 64, "one slot is one 64-byte block");
+
+// Insert aggregation modes (a launch-time choice, results are identical)
+constexpr int kAggWarp = 0;  // lanes with equal keys merged (match_any), one probe per key per warp
+constexpr int kAggNone = 1;  // every vertex probes and adds on its own
 
 struct TableView {
     DevHeader* hdr;
     unsigned long long* keys;
-    Acc* acc;
-    float4* lst;
-    long long* cold;
+    Slot* slots;
     uint2* mirror;  // nullptr unless cache_fp16
     unsigned* dirty;
     unsigned* h_status;  // host-mapped copy of the status word (may be nullptr)
@@ -199,17 +205,6 @@ __device__ __forceinline__ long long probe_find(const TableView& t, unsigned lon
     return -1;
 }
 
-// Sum a 64-bit value over the lanes of `group` exactly: split into a 24-bit unsigned low
-// part and a signed high part so that both 32-bit warp reductions cannot overflow
-// (|v| < 2^48, at most 32 lanes).
-__device__ __forceinline__ long long group_sum64(unsigned group, long long v) {
-    const unsigned lo = static_cast<unsigned>(v & 0xFFFFFFll);
-    const int hi = static_cast<int>(v >> 24);
-    const unsigned slo = __reduce_add_sync(group, lo);
-    const int shi = __reduce_add_sync(group, hi);
-    return static_cast<long long>(shi) * (1ll << 24) + static_cast<long long>(slo);
-}
-
 // Leader of a group of lanes holding the same key: probe once, add the group's sums.
 __device__ __forceinline__ void scatter_group(const TableView& t, unsigned long long key, unsigned members,
                                               const long long sums[4], unsigned* max_len) {
@@ -221,7 +216,7 @@ __device__ __forceinline__ void scatter_group(const TableView& t, unsigned long 
         atomicAdd(&t.hdr->dropped, static_cast<unsigned long long>(__popc(members)));
         return;
     }
-    Acc* a = t.acc + slot;
+    Slot* a = t.slots + slot;
     atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[0]), static_cast<unsigned long long>(sums[0]));
     atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[1]), static_cast<unsigned long long>(sums[1]));
     atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[2]), static_cast<unsigned long long>(sums[2]));
@@ -231,8 +226,17 @@ __device__ __forceinline__ void scatter_group(const TableView& t, unsigned long 
         atomicOr(t.dirty + (slot >> 5), 1u << (slot & 31));
 }
 
-// One warp's worth of vertices (one per lane, `valid` lanes only): classify, aggregate
-// lanes with equal keys (match_any), let one leader per key probe and add.
+__device__ __forceinline__ long long shfl64(long long v, int src) {
+    return static_cast<long long>(__shfl_sync(kFull, static_cast<unsigned long long>(v), src));
+}
+
+// One warp's worth of vertices (one per lane, `valid` lanes only): classify, then add each
+// accepted vertex to its cell.  With kAggWarp, lanes holding the same key are found with
+// match_any; the lowest lane of each group (its leader) collects the others' sums through
+// a warp-uniform shuffle loop that visits only the donor lanes, then probes once and adds.
+// A warp whose keys are all distinct (the common case after the first bounce) skips the
+// loop.  Integer sums are exact, so every mode gives bit-identical tables.
+template <int kMode>
 __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, const float4& v0, const float4& v1,
                                             const float4& v2, const float4& v3, unsigned* max_len) {
     const unsigned lane = threadIdx.x & 31u;
@@ -255,13 +259,31 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
         }
         if (zero_w) atomicAdd(&t.hdr->zero_weight, static_cast<unsigned long long>(__popc(zero_w)));
     }
-    if (cls == 1) {
-        const unsigned group = __match_any_sync(accepted, key);
-        long long red[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) red[k] = group_sum64(group, sums[k]);
-        if (lane == static_cast<unsigned>(__ffs(group) - 1)) scatter_group(t, key, group, red, max_len);
+    if (kMode == kAggNone) {
+        if (cls == 1) scatter_group(t, key, 1u << lane, sums, max_len);
+        return;
     }
+    unsigned group = 0;
+    if (cls == 1) group = __match_any_sync(accepted, key);
+    const bool donor = cls == 1 && (group & ((1u << lane) - 1u)) != 0u;
+    unsigned donors = __ballot_sync(kFull, donor);
+    if (donors) {
+        const int my_leader = cls == 1 ? __ffs(group) - 1 : 0;
+        while (donors) {  // the same iterations in every lane
+            const int src = __ffs(donors) - 1;
+            donors &= donors - 1u;
+            const int dst = __shfl_sync(kFull, my_leader, src);
+            const long long a0 = shfl64(sums[0], src), a1 = shfl64(sums[1], src);
+            const long long a2 = shfl64(sums[2], src), a3 = shfl64(sums[3], src);
+            if (static_cast<int>(lane) == dst) {
+                sums[0] += a0;
+                sums[1] += a1;
+                sums[2] += a2;
+                sums[3] += a3;
+            }
+        }
+    }
+    if (cls == 1 && !donor) scatter_group(t, key, group, sums, max_len);
 }
 
 // ---------------------------------------------------------------------------
@@ -279,31 +301,27 @@ __device__ __forceinline__ uint2 pack_half4(float a, float b, float c) {
 }
 
 __device__ __forceinline__ void blend_slot(const TableView& t, unsigned long long s) {
-    const longlong2* ap = reinterpret_cast<const longlong2*>(t.acc + s);
-    const longlong2 a01 = __ldcg(ap);
-    const longlong2 a23 = __ldcg(ap + 1);
+    longlong2* p = reinterpret_cast<longlong2*>(t.slots + s);
+    const longlong2 a01 = __ldcg(p);      // sum_r, sum_g
+    const longlong2 a23 = __ldcg(p + 1);  // sum_b, c_new
+    float4 L = __ldcg(reinterpret_cast<const float4*>(p + 2));
+    const longlong2 co2 = __ldcg(p + 3);  // c_old, spare
     const long long cn = a23.y;
-    longlong2* wp = reinterpret_cast<longlong2*>(t.acc + s);
     const longlong2 z = make_longlong2(0, 0);
-    if (cn <= 0) {  // not reachable for accepted vertices; keep the cell unchanged
-        __stcg(wp, z);
-        __stcg(wp + 1, z);
-        return;
-    }
-    const long long co = t.cold[s];
+    __stcg(p, z);
+    __stcg(p + 1, z);
+    if (cn <= 0) return;  // not reachable for accepted vertices; keep the cell unchanged
+    const long long co = co2.x;
     const long long ctot = co > (0x7fffffffffffffffll - cn) ? 0x7fffffffffffffffll : co + cn;
     const float fcn = __ll2float_rn(cn);
     float alpha = t.alpha_min;
     if (t.blend_mode == 0) alpha = fmaxf(sqrtf(__fdiv_rn(fcn, __ll2float_rn(ctot))), t.alpha_min);
     const float keep = 1.0f - alpha;
-    float4 L = t.lst[s];
     L.x = fmaf(alpha, __fdiv_rn(__ll2float_rn(a01.x), fcn), keep * L.x);
     L.y = fmaf(alpha, __fdiv_rn(__ll2float_rn(a01.y), fcn), keep * L.y);
     L.z = fmaf(alpha, __fdiv_rn(__ll2float_rn(a23.x), fcn), keep * L.z);
-    t.lst[s] = L;
-    t.cold[s] = ctot;
-    __stcg(wp, z);
-    __stcg(wp + 1, z);
+    __stcg(reinterpret_cast<float4*>(p + 2), L);
+    __stcg(p + 3, make_longlong2(ctot, co2.y));
     if (t.mirror) t.mirror[s] = pack_half4(L.x, L.y, L.z);
 }
 
@@ -371,7 +389,7 @@ __device__ __forceinline__ float3 cell_value(const TableView& t, const float4& v
         c.y = __half2float(__ushort_as_half(static_cast<unsigned short>(h.x >> 16)));
         c.z = __half2float(__ushort_as_half(static_cast<unsigned short>(h.y & 0xffffu)));
     } else {
-        const float4 L = __ldcg(t.lst + s);
+        const float4 L = __ldcg(&t.slots[s].L);
         c = make_float3(L.x, L.y, L.z);
     }
     return c;

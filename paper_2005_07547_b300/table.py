@@ -106,6 +106,16 @@ class Table:
         _abi.check(_abi.load().psf_get_stats(self._h, ctypes.byref(st), _stream_handle(stream)), "psf_get_stats")
         return st.as_dict()
 
+    def set_launch(self, insert_mode: int = 0, insert_blocks_per_sm: int = 0, update_blocks_per_sm: int = 0,
+                   query_blocks_per_sm: int = 0) -> None:
+        lc = _abi.LaunchConfig(insert_mode, insert_blocks_per_sm, update_blocks_per_sm, query_blocks_per_sm)
+        _abi.check(_abi.load().psf_set_launch_config(self._h, ctypes.byref(lc)), "psf_set_launch_config")
+
+    def get_launch(self) -> dict:
+        lc = _abi.LaunchConfig()
+        _abi.check(_abi.load().psf_get_launch_config(self._h, ctypes.byref(lc)), "psf_get_launch_config")
+        return {name: getattr(lc, name) for name, _ in lc._fields_}
+
     def close(self) -> None:
         """Wait for the table's work, then release it."""
         import torch

@@ -67,10 +67,13 @@ def check_cv(out_gpu, out_ref, verts, C_ref, P, D, beta, cv_max_depth, ref_L_all
     fl = _floor(ref_L_all)
     bound = tol * (np.abs(L) + has_cv * beta * (np.abs(t) * np.abs(C_next.reshape(-1, 3)) + np.abs(C_ref)
                                                + (1.0 + np.abs(t)) * fl))
+    # non-finite inputs propagate identically on both sides
+    assert np.array_equal(np.isnan(out_gpu), np.isnan(out_ref))
     err = np.abs(out_gpu - out_ref)
+    err[np.isnan(out_ref)] = 0.0
     bad = err > bound
     assert not np.any(bad), (np.argwhere(bad)[:5], out_gpu[bad][:5], out_ref[bad][:5])
     # vertices without a control variate are copied exactly
     no_cv = ~has_cv[:, 0]
-    assert np.array_equal(out_gpu[no_cv], L[no_cv].astype(np.float32).astype(np.float64))
+    assert np.array_equal(out_gpu[no_cv], L[no_cv].astype(np.float32).astype(np.float64), equal_nan=True)
     return float(np.max(err / np.maximum(bound, 1e-300))) if err.size else 0.0

@@ -80,8 +80,8 @@ def test_table_bytes_and_config_validation(lib):
 
     good = _abi.make_config(log2_capacity=16)
     n16 = lib.psf_table_bytes(ctypes.byref(good))
-    # header + keys 8 + acc 32 + approximant 16 + c_old 8 bytes per slot + dirty bits
-    assert n16 >= (1 << 16) * (8 + 32 + 16 + 8) + (1 << 16) // 8
+    # header + 8-byte key + 64-byte slot record per slot + dirty bits
+    assert n16 >= (1 << 16) * (8 + 64) + (1 << 16) // 8
     assert n16 % 256 == 0
     fp16 = _abi.make_config(log2_capacity=16, cache_fp16=True)
     assert lib.psf_table_bytes(ctypes.byref(fp16)) == n16 + (1 << 16) * 8
