@@ -108,6 +108,58 @@ def load_traffic(kernel: str) -> float | None:
     return float(k["bytes_per_launch"]) if k else None
 
 
+class _Nvml:
+    """Read-only NVML queries through the driver's libnvidia-ml (ctypes)."""
+
+    CLOCK_SM = 1
+
+    def __init__(self):
+        import ctypes
+
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self._reasons = fn or self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def handle(self, cuda_index: int):
+        ct = self.ct
+        h = ct.c_void_p()
+        try:
+            import torch
+
+            p = torch.cuda.get_device_properties(cuda_index)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+            if self.lib.nvmlDeviceGetHandleByPciBusId_v2(ct.c_char_p(bus), ct.byref(h)) == 0:
+                return h
+        except Exception:
+            pass
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ct.c_uint(cuda_index), ct.byref(h)) != 0:
+            raise RuntimeError("no NVML handle")
+        return h
+
+    def sm_mhz(self, h) -> int:
+        v = self.ct.c_uint()
+        self.lib.nvmlDeviceGetClockInfo(h, self.CLOCK_SM, self.ct.byref(v))
+        return int(v.value)
+
+    def max_sm_mhz(self, h) -> int:
+        v = self.ct.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(h, self.CLOCK_SM, self.ct.byref(v))
+        return int(v.value)
+
+    def reasons(self, h) -> int:
+        v = self.ct.c_ulonglong()
+        self._reasons(h, self.ct.byref(v))
+        return int(v.value)
+
+    def power_w(self, h) -> float:
+        v = self.ct.c_uint()
+        self.lib.nvmlDeviceGetPowerUsage(h, self.ct.byref(v))
+        return v.value / 1000.0
+
+
 class ClockSampler:
     """SM clocks and clock-event (throttle) reasons sampled through NVML every millisecond
     by a background thread while the timed region runs (read-only queries)."""
@@ -124,25 +176,13 @@ class ClockSampler:
         self._stop = None
         self._thread = None
 
-    def _handle(self, nv):
-        try:
-            import torch
-
-            p = torch.cuda.get_device_properties(self.cuda_index)
-            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
-            return nv.nvmlDeviceGetHandleByPciBusId(bus)
-        except Exception:
-            return nv.nvmlDeviceGetHandleByIndex(self.cuda_index)
-
     def __enter__(self):
         import threading
 
         try:
-            import pynvml as nv
-
-            nv.nvmlInit()
-            h = self._handle(nv)
-            self.max_mhz = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+            nv = _Nvml()
+            h = nv.handle(self.cuda_index)
+            self.max_mhz = nv.max_sm_mhz(h)
         except Exception as e:  # no NVML: report unsampled
             self.error = repr(e)
             return self
@@ -151,9 +191,7 @@ class ClockSampler:
         def loop():
             while not self._stop.is_set():
                 try:
-                    self.samples.append((nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM),
-                                         nv.nvmlDeviceGetCurrentClocksEventReasons(h),
-                                         nv.nvmlDeviceGetPowerUsage(h) / 1000.0))
+                    self.samples.append((nv.sm_mhz(h), nv.reasons(h), nv.power_w(h)))
                 except Exception as e:
                     self.error = repr(e)
                     return
@@ -178,7 +216,7 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(s[0] for s in self.samples), "sm_max_mhz": self.max_mhz,
                 "reasons": sorted(reasons), "samples": len(self.samples),
-                "power_w_max": max(s[2] for s in self.samples), "source": "nvml, 1 ms"}
+                "power_w_max": max(s[2] for s in self.samples), "source": "NVML (libnvidia-ml), 1 ms"}
 
 
 # ---------------------------------------------------------------------------
@@ -441,6 +479,223 @@ def run_e2e(psf, table, host: list[np.ndarray], P: int, D: int, steps: int) -> d
             "note": "pinned host buffers; H2D of step k+1 overlapped with step k on a second stream"}
 
 
+def _gen_session(args):
+    s, iteration = args
+    from synth.scene import iteration_vertices
+
+    return iteration_vertices(s, iteration)
+
+
+def run_sessions(args) -> None:
+    """64 uneven render sessions: one fused persistent launch per iteration (graph-replayed)
+    against the plain per-session loop of psf_step calls, eager and graph-captured."""
+    rank, world, local = dist_env()
+    from synth.scene import session_workloads
+
+    sessions = session_workloads(args.sessions, first_session_seed=4000 + 1000 * rank)
+    pool = max(1, min(args.pool, args.warmup + args.steps))
+    jobs = [(s, it) for it in range(pool) for s in sessions]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(os.cpu_count() or 1, 32)) as p:
+        flat = p.map(_gen_session, jobs, chunksize=1)
+    host = [[flat[it * len(sessions) + k] for it in range(pool)] for k in range(len(sessions))]
+
+    import torch
+
+    import paper_2005_07547_b300 as psf
+    from paper_2005_07547_b300 import autotune
+
+    torch.cuda.set_device(local)
+    V = sum(s["width"] * s["height"] * s["depth"] for s in sessions)
+    dev = [[torch.from_numpy(v).cuda() for v in host[k]] for k in range(len(sessions))]
+    del host, flat
+
+    def cfg_of(s):
+        return psf.make_config(log2_capacity=s["log2_capacity"], pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
+                               alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"])
+
+    outs = [torch.empty((d[0].shape[0], 3), device="cuda") for d in dev]
+
+    def entries(tables, it):
+        return [(tables[k], dev[k][it % pool], outs[k], s["width"] * s["height"], s["depth"])
+                for k, s in enumerate(sessions)]
+
+    tuned = autotune.tune_batch(lambda: entries([psf.Table(cfg_of(s)) for s in sessions], 0), len(sessions))
+    knobs = tuned["best"]
+    tables = [psf.Table(cfg_of(s)) for s in sessions]
+    batches = [psf.Batch(len(sessions), **knobs) for _ in range(pool)]
+    for it, b in enumerate(batches):
+        b.set(entries(tables, it))
+    torch.cuda.synchronize()
+    graphs = []
+    for b in batches:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            b.launch()
+        graphs.append(g)
+
+    def timed(step_fn, n_warm, n_steps):
+        for k in range(n_warm):
+            step_fn(k)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps + 1)]
+        ev[0].record()
+        for k in range(n_steps):
+            step_fn(n_warm + k)
+            ev[k + 1].record()
+        torch.cuda.synchronize()
+        per = [ev[k].elapsed_time(ev[k + 1]) for k in range(n_steps)]
+        return ev[0].elapsed_time(ev[-1]), per
+
+    with ClockSampler(local) as clocks:
+        t_batch, per_batch = timed(lambda k: graphs[k % pool].replay(), args.warmup, args.steps)
+    status = max(b.status() for b in batches)
+
+    plain_tables = [psf.Table(cfg_of(s)) for s in sessions]
+
+    def plain(k):
+        for i, s in enumerate(sessions):
+            plain_tables[i].step(dev[i][k % pool], s["width"] * s["height"], s["depth"], out=outs[i])
+
+    t_plain, per_plain = timed(plain, args.warmup, args.steps)
+    graph_tables = [psf.Table(cfg_of(s)) for s in sessions]
+    plain_graphs = []
+    for it in range(pool):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for i, s in enumerate(sessions):
+                graph_tables[i].step(dev[i][it], s["width"] * s["height"], s["depth"], out=outs[i])
+        plain_graphs.append(g)
+    t_pgraph, per_pgraph = timed(lambda k: plain_graphs[k % pool].replay(), args.warmup, args.steps)
+    # the batched tables equal the plain ones bit for bit (same iterations, order-free sums)
+    same = all(tables[i].export().tobytes() == plain_tables[i].export().tobytes() for i in range(len(sessions)))
+
+    def rate(ms):
+        return V * args.steps / (ms / 1e3)
+
+    line = {
+        "metric": METRIC + ", 64 batched sessions", "value": rate(t_batch), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 fixed point", "data": "synthetic",
+        "config": {"workload": f"{len(sessions)} sessions, width log-uniform 128..1280, 16:9, depth U{{2..6}}",
+                   "vertices_per_step": V, "pool": pool, "fp16_cache": True, "batch_knobs": knobs,
+                   "l2": f"inputs larger than L2: {pool} distinct iterations of {V * 64 / 1e9:.1f} GB"},
+        "latency_ms": {"p50": float(np.percentile(per_batch, 50)), "p99": float(np.percentile(per_batch, 99))},
+        "plain_loop": {"value": rate(t_plain), "ms_per_step": t_plain / args.steps, "launches_per_step": 3 * len(sessions),
+                       "p50": float(np.percentile(per_plain, 50)), "p99": float(np.percentile(per_plain, 99))},
+        "plain_graph": {"value": rate(t_pgraph), "ms_per_step": t_pgraph / args.steps,
+                        "p50": float(np.percentile(per_pgraph, 50)), "p99": float(np.percentile(per_pgraph, 99))},
+        "speedup_vs_plain_loop": t_plain / t_batch, "speedup_vs_plain_graph": t_pgraph / t_batch,
+        "identical_to_plain": same, "status": status, "autotune": tuned["all"],
+        "gpu_launches": args.steps, "clocks": clocks.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+class TemplateSource:
+    """Vertex streams for served requests: each request is mapped to the pre-generated
+    template with its depth and the nearest width (log scale); iteration k of a session
+    reads template iteration k mod n_iter.  Templates are resident on the device."""
+
+    def __init__(self, templates: dict):
+        # templates: {(width, depth): [tensor per iteration]}
+        self.templates = templates
+        self.widths = {}
+        for (w, d) in templates:
+            self.widths.setdefault(d, []).append(w)
+
+    def fit(self, req: dict) -> dict:
+        """The request resized to its template (the sizes the server will run)."""
+        import math
+
+        ws = self.widths[req["depth"]]
+        w = min(ws, key=lambda x: abs(math.log(x) - math.log(req["width"])))
+        h = int(round(9 * w / 16))
+        r = dict(req)
+        r["width"], r["height"] = w, h
+        v = w * h * req["depth"]
+        r["log2_capacity"] = int(math.ceil(math.log2(v))) + 1
+        from synth.scene import config4_q_bits
+
+        r["pos_bits"] = config4_q_bits(r["log2_capacity"], r["dir_bits"])
+        r["vertices"] = v
+        return r
+
+    def __call__(self, req: dict, iteration: int):
+        its = self.templates[(req["width"], req["depth"])]
+        return its[iteration % len(its)]
+
+
+def _gen_template(args):
+    w, d, it = args
+    from synth.scene import iteration_vertices
+
+    h = int(round(9 * w / 16))
+    wl = dict(width=w, height=h, depth=d, seed=7000 + 10 * w + d, radiance="glossy", camera_step=0.0,
+              camera_x0=0.5)
+    return iteration_vertices(wl, it)
+
+
+TEMPLATE_WIDTHS = (128, 181, 256, 362, 512, 724, 1024, 1280)
+
+
+def make_templates(depths=(2, 3, 4, 5, 6), widths=TEMPLATE_WIDTHS, iterations=2) -> dict:
+    """Real path-vertex streams for a grid of (width, depth), generated on the host."""
+    import torch
+
+    jobs = [(w, d, it) for w in widths for d in depths for it in range(iterations)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(os.cpu_count() or 1, 32)) as p:
+        res = p.map(_gen_template, jobs, chunksize=1)
+    out = {}
+    for (w, d, it), v in zip(jobs, res):
+        out.setdefault((w, d), []).append(torch.from_numpy(v).cuda())
+    return out
+
+
+def run_serving(args) -> None:
+    """Poisson arrivals at --rate per second for --duration seconds, 60 GB table budget:
+    the continuous-batching server against the plain per-session loop on the same trace."""
+    from synth.scene import serving_arrivals
+
+    import torch
+
+    import paper_2005_07547_b300 as psf
+    from paper_2005_07547_b300.serve import Server
+
+    rank, world, local = dist_env()
+    reqs = serving_arrivals(args.rate, args.duration, seed=5 + rank)
+    templates = make_templates()
+    torch.cuda.set_device(local)
+    psf.load()
+    src = TemplateSource(templates)
+    reqs = [src.fit(r) for r in reqs]
+    reports = {}
+    for mode in ("batched", "plain"):
+        srv = Server(src, budget_bytes=args.budget_gb * 1e9, mode=mode)
+        with ClockSampler(local) as clocks:
+            rep = srv.run(reqs, args.duration)
+        rep["clocks"] = clocks.summary()
+        srv.close()
+        torch.cuda.synchronize()
+        reports[mode] = rep
+    b, p = reports["batched"], reports["plain"]
+    line = {
+        "metric": METRIC + ", served sessions", "value": b["vertices_per_s"] * world, "unit": UNIT, "n_gpus": world,
+        "steps": b["ticks"], "warmup": 0, "ms_per_step": 1e3 * b["wall_s"] / max(1, b["ticks"]),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 fixed point",
+        "data": "synthetic",
+        "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.duration} s, sessions of 16..128 iterations, "
+                               "width log-uniform 128..1280 mapped to the nearest template, depth U{2..6}",
+                   "requests": len(reqs), "budget_gb": args.budget_gb, "templates": len(templates)},
+        "batched": b, "plain": p,
+        "throughput_ratio_batched_over_plain": b["vertices_per_s"] / p["vertices_per_s"] if p["vertices_per_s"] else None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,11 +707,20 @@ def main(argv=None) -> None:
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--insert-mode", type=int, default=0, help="0: warp aggregation of equal keys; 1: none")
+    ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
+    ap.add_argument("--pool", type=int, default=4, help="distinct resident iterations per session (batched)")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
+    ap.add_argument("--budget-gb", type=float, default=60.0, help="serving: device memory for tables")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps are required")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "sessions":
+        run_sessions(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_psf(args)
 

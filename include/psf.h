@@ -176,6 +176,59 @@ typedef struct {
 int psf_set_launch_config(psf_table* t, const psf_launch_config* cfg);
 int psf_get_launch_config(const psf_table* t, psf_launch_config* out);
 
+/* ------------------------------------------------------------------------------------
+ * Batched iterations: one persistent fused kernel per iteration across many tables.
+ *
+ * A psf_batch holds device-resident descriptors of up to max_items (table, vertices,
+ * output, P, D) items and the words of a grid barrier.  psf_batch_launch runs ONE
+ * cooperative kernel (all blocks co-resident) that inserts every item's vertices,
+ * waits at a grid barrier, blends every item's touched cells, waits again and answers
+ * every item's control-variate query -- the same results, bit for bit, as psf_step on
+ * each table alone.  The launch reads only the device descriptors, so it can be
+ * captured once in a CUDA graph and replayed while psf_batch_set changes what the
+ * descriptors point at (sessions joining and leaving).  Each barrier wait is bounded
+ * (barrier_timeout_us); a wait that runs out sets PSF_STATUS_TIMEOUT in the batch and in
+ * every item's table, and that iteration's results are undefined.
+ * ------------------------------------------------------------------------------------ */
+
+typedef struct {
+    psf_table* table;
+    const float* d_vertices; /* D*P records, depth-major, 16-byte aligned */
+    float* d_out_rgb;        /* D*P*3 float32 */
+    uint32_t P;
+    uint32_t D;
+} psf_batch_item;
+
+typedef struct {
+    uint32_t insert_mode;         /* as psf_launch_config.insert_mode */
+    uint32_t blocks_per_sm;       /* resident 256-thread blocks per SM (0 = occupancy limit) */
+    uint32_t barrier_timeout_us;  /* bound on each grid-barrier wait (0 = 2,000,000) */
+    uint32_t test_phantom_blocks; /* testing only: each barrier also waits for this many blocks that
+                                     do not exist, so every wait runs out (0 in normal use) */
+} psf_batch_config;
+
+typedef struct psf_batch psf_batch;
+
+/* Allocate a batch for up to max_items (1..PSF_MAX_BATCH) items: device descriptors and
+ * barrier words (cudaMalloc) and a pinned host staging buffer.  cfg may be NULL. */
+int psf_batch_create(uint32_t max_items, const psf_batch_config* cfg, psf_batch** out);
+
+/* Enqueue on `stream` the copy of n item descriptors (n <= max_items; n = 0 allowed).
+ * Every item's table must have been created on the current device and outlive its use. */
+int psf_batch_set(psf_batch* b, const psf_batch_item* items, uint32_t n, void* stream);
+
+/* Enqueue one fused iteration over the items last set (capturable in a CUDA graph). */
+int psf_batch_launch(psf_batch* b, void* stream);
+
+/* psf_batch_set followed by psf_batch_launch. */
+int psf_batch_step(psf_batch* b, const psf_batch_item* items, uint32_t n, void* stream);
+
+/* Sticky status of the batch (PSF_STATUS_TIMEOUT); synchronises `stream`. */
+int psf_batch_status(psf_batch* b, uint32_t* status, void* stream);
+
+/* Release the batch (its work must have completed).  NULL is a no-op. */
+int psf_batch_destroy(psf_batch* b);
+
 /* Text of the last CUDA error seen by this thread's calls (empty if none). */
 const char* psf_last_cuda_error(void);
 

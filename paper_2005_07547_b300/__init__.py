@@ -21,4 +21,5 @@ from ._abi import (  # noqa: F401
     load,
     make_config,
 )
+from .batch import Batch  # noqa: F401
 from .table import Table  # noqa: F401

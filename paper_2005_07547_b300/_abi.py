@@ -84,6 +84,29 @@ class LaunchConfig(ctypes.Structure):
     ]
 
 
+class BatchItem(ctypes.Structure):
+    """psf_batch_item."""
+
+    _fields_ = [
+        ("table", ctypes.c_void_p),
+        ("d_vertices", ctypes.c_void_p),
+        ("d_out_rgb", ctypes.c_void_p),
+        ("P", ctypes.c_uint32),
+        ("D", ctypes.c_uint32),
+    ]
+
+
+class BatchConfig(ctypes.Structure):
+    """psf_batch_config."""
+
+    _fields_ = [
+        ("insert_mode", ctypes.c_uint32),
+        ("blocks_per_sm", ctypes.c_uint32),
+        ("barrier_timeout_us", ctypes.c_uint32),
+        ("test_phantom_blocks", ctypes.c_uint32),
+    ]
+
+
 # psf_cell_record as a numpy structured dtype (72 bytes: 68 of fields, padded to 8-byte alignment)
 CELL_DTYPE = np.dtype([("key", "<u8"), ("sum", "<i8", (3,)), ("c_new", "<i8"), ("c_old", "<i8"),
                        ("L", "<f4", (3,)), ("L_fp16", "<u2", (3,)), ("pad", "<u2")], align=True)
@@ -105,6 +128,12 @@ SIGNATURES = {
     "psf_get_stats": (_i, [_vp, ctypes.POINTER(Stats), _vp]),
     "psf_destroy": (_i, [_vp]),
     "psf_set_launch_config": (_i, [_vp, ctypes.POINTER(LaunchConfig)]),
+    "psf_batch_create": (_i, [_u32, ctypes.POINTER(BatchConfig), ctypes.POINTER(_vp)]),
+    "psf_batch_set": (_i, [_vp, ctypes.POINTER(BatchItem), _u32, _vp]),
+    "psf_batch_launch": (_i, [_vp, _vp]),
+    "psf_batch_step": (_i, [_vp, ctypes.POINTER(BatchItem), _u32, _vp]),
+    "psf_batch_status": (_i, [_vp, ctypes.POINTER(_u32), _vp]),
+    "psf_batch_destroy": (_i, [_vp]),
     "psf_get_launch_config": (_i, [_vp, ctypes.POINTER(LaunchConfig)]),
 }
 

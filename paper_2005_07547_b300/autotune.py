@@ -1,0 +1,118 @@
+"""Autotuner for the launch knobs and the table load factor.
+
+Every knob changes only the order of the integer additions (or the table's slot
+layout), never a result, so candidates are timed on scratch tables fed the caller's
+own device-resident vertex batches and the fastest is returned.  Timing uses CUDA
+events on the current stream after warm-up iterations.
+
+  tune_table(cfg, batches, P, D)   -> insert mode and per-kernel grid caps for psf_step
+  tune_capacity(cfg, batches, P, D)-> log2 capacity (load factor) for a session size
+  tune_batch(entries_fn)           -> insert mode and blocks/SM for the batched kernel
+"""
+
+from __future__ import annotations
+
+import ctypes
+import itertools
+import math
+
+from . import _abi
+from .batch import Batch
+from .table import Table
+
+TABLE_SPACE = {
+    "insert_mode": (0, 1),
+    "insert_blocks_per_sm": (0, 4, 2),
+    "query_blocks_per_sm": (0, 4),
+    "update_blocks_per_sm": (0, 2),
+}
+BATCH_SPACE = {"insert_mode": (0, 1), "blocks_per_sm": (0, 3, 2)}
+
+
+def _time_ms(fn, iters: int) -> float:
+    import torch
+
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record()
+    for k in range(iters):
+        fn(k)
+    end.record()
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / iters
+
+
+def _clone_config(cfg: _abi.Config, **over) -> _abi.Config:
+    c = _abi.Config()
+    ctypes.memmove(ctypes.byref(c), ctypes.byref(cfg), ctypes.sizeof(cfg))
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c
+
+
+def tune_table(cfg: _abi.Config, batches, P: int, D: int, space: dict | None = None, warmup: int = 2,
+               iters: int = 4) -> dict:
+    """Fastest psf_step launch knobs for this configuration and input (list of (P*D, 16) tensors)."""
+    import torch
+
+    space = space or TABLE_SPACE
+    out = torch.empty((P * D, 3), dtype=torch.float32, device=batches[0].device)
+    results = []
+    keys = list(space)
+    for values in itertools.product(*(space[k] for k in keys)):
+        knobs = dict(zip(keys, values))
+        t = Table(cfg)
+        t.set_launch(**knobs)
+        for k in range(warmup):
+            t.step(batches[k % len(batches)], P, D, out=out)
+        ms = _time_ms(lambda k: t.step(batches[(warmup + k) % len(batches)], P, D, out=out), iters)
+        t.close()
+        results.append((ms, knobs))
+    results.sort(key=lambda r: r[0])
+    return {"best": results[0][1], "best_ms": results[0][0], "all": [{"ms": ms, **k} for ms, k in results]}
+
+
+def tune_capacity(cfg: _abi.Config, batches, P: int, D: int, extra_bits=(1, 2), warmup: int = 2,
+                  iters: int = 4) -> dict:
+    """Load factor: capacity 2^(ceil(log2 V) + e) for each e, timed; returns the fastest
+    and its table bytes (more slots cost memory, fewer cost longer probes)."""
+    import torch
+
+    V = P * D
+    out = torch.empty((V, 3), dtype=torch.float32, device=batches[0].device)
+    res = []
+    for e in extra_bits:
+        log2cap = max(4, int(math.ceil(math.log2(max(V, 2)))) + e)
+        c = _clone_config(cfg, log2_capacity=log2cap)
+        t = Table(c)
+        for k in range(warmup):
+            t.step(batches[k % len(batches)], P, D, out=out)
+        ms = _time_ms(lambda k: t.step(batches[(warmup + k) % len(batches)], P, D, out=out), iters)
+        res.append({"log2_capacity": log2cap, "ms": ms, "table_bytes": t.nbytes, "max_probe": t.stats()["max_probe"]})
+        t.close()
+    best = min(res, key=lambda r: r["ms"])
+    return {"best": best["log2_capacity"], "all": res}
+
+
+def tune_batch(make_entries, n_items: int, space: dict | None = None, warmup: int = 2, iters: int = 3) -> dict:
+    """Fastest batched-kernel knobs.  make_entries() must return fresh (table, vertices, out, P, D)
+    entries (scratch tables) for each candidate."""
+    space = space or BATCH_SPACE
+    keys = list(space)
+    results = []
+    for values in itertools.product(*(space[k] for k in keys)):
+        knobs = dict(zip(keys, values))
+        entries = make_entries()
+        b = Batch(n_items, **knobs)
+        b.set(entries)
+        for _ in range(warmup):
+            b.launch()
+        ms = _time_ms(lambda k: b.launch(), iters)
+        if b.status() != 0:
+            ms = float("inf")
+        b.close()
+        for e in entries:
+            e[0].close()
+        results.append((ms, knobs))
+    results.sort(key=lambda r: r[0])
+    return {"best": results[0][1], "best_ms": results[0][0], "all": [{"ms": ms, **k} for ms, k in results]}

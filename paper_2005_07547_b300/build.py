@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libpsf.so")
-SOURCES = ["psf.cu"]
-DEPS = SOURCES + ["psf_device.cuh"]
+SOURCES = ["psf.cu", "psf_batch.cu"]
+DEPS = SOURCES + ["psf_device.cuh", "psf_table.h"]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

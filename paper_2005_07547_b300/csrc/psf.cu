@@ -21,40 +21,25 @@
 
 #include "psf.h"
 #include "psf_device.cuh"
+#include "psf_table.h"
 
 using psf::DevHeader;
 using psf::Slot;
 using psf::TableView;
 
-namespace {
+thread_local std::string psf_g_last_error;
 
-thread_local std::string g_last_error;
+using psf::kThreads;
 
-constexpr int kThreads = 256;
-
-}  // namespace
-
-struct psf_table {
-    psf_config cfg;
-    TableView view;
-    void* mem;
-    size_t bytes;
-    unsigned* h_status;  // host-mapped pinned word written by k_update
-    int device;
-    int sms;
-    int insert_blocks_per_sm;  // occupancy limits of the kernels
-    int update_blocks_per_sm;
-    int query_blocks_per_sm;
-    psf_launch_config launch;  // tuning knobs (psf_set_launch_config)
-};
-
-namespace {
-
-bool cuda_ok(cudaError_t e, const char* what) {
+bool psf_cuda_ok(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return true;
-    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    psf_g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
     return false;
 }
+
+namespace {
+
+bool cuda_ok(cudaError_t e, const char* what) { return psf_cuda_ok(e, what); }
 
 struct Layout {
     size_t hdr, keys, slots, mirror, dirty, total;
@@ -110,18 +95,31 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* 
     __syncthreads();
     unsigned max_len = 0;
     const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
-    for (unsigned long long base = static_cast<unsigned long long>(blockIdx.x) * blockDim.x; base < n; base += stride) {
-        const unsigned long long i = base + threadIdx.x;
-        const bool valid = i < n;
-        float4 v0 = make_float4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
-        if (valid) {
-            const float4* r = v + 4 * i;  // streamed once: evict-first
-            v0 = __ldcs(r);
-            v1 = __ldcs(r + 1);
-            v2 = __ldcs(r + 2);
-            v3 = __ldcs(r + 3);
+    // the next tile's records are loaded while the current tile probes and adds
+    unsigned long long base = static_cast<unsigned long long>(blockIdx.x) * blockDim.x;
+    float4 v0 = make_float4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
+    if (base + threadIdx.x < n) {
+        const float4* r = v + 4 * (base + threadIdx.x);  // streamed once: evict-first
+        v0 = __ldcs(r);
+        v1 = __ldcs(r + 1);
+        v2 = __ldcs(r + 2);
+        v3 = __ldcs(r + 3);
+    }
+    for (; base < n; base += stride) {
+        const unsigned long long nx = base + stride + threadIdx.x;
+        float4 n0 = make_float4(0, 0, 0, 0), n1 = n0, n2 = n0, n3 = n0;
+        if (nx < n) {
+            const float4* r = v + 4 * nx;
+            n0 = __ldcs(r);
+            n1 = __ldcs(r + 1);
+            n2 = __ldcs(r + 2);
+            n3 = __ldcs(r + 3);
         }
-        psf::insert_warp<kMode>(t, valid, v0, v1, v2, v3, &max_len);
+        psf::insert_warp<kMode>(t, base + threadIdx.x < n, v0, v1, v2, v3, &max_len);
+        v0 = n0;
+        v1 = n1;
+        v2 = n2;
+        v3 = n3;
     }
     if (max_len) atomicMax(&s_max_probe, max_len);
     __syncthreads();
@@ -151,26 +149,8 @@ __global__ void __launch_bounds__(kThreads) k_query(TableView t, const float4* _
                                                     float* __restrict__ out) {
     const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
     for (unsigned long long p = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < P;
-         p += stride) {
-        float3 c_next = make_float3(0.0f, 0.0f, 0.0f);
-        for (int j = static_cast<int>(D) - 1; j >= 0; --j) {
-            const unsigned long long i = static_cast<unsigned long long>(j) * P + p;
-            const float4* r = v + 4 * i;
-            const float4 v0 = __ldcs(r), v1 = __ldcs(r + 1), v2 = __ldcs(r + 2), v3 = __ldcs(r + 3);
-            const float3 c = psf::cell_value(t, v0, v1, v2);
-            float o0 = v3.x, o1 = v3.y, o2 = v3.z;
-            if (j + 1 < static_cast<int>(D) && static_cast<unsigned>(j) < t.cv_max_depth) {
-                o0 = psf::cv_combine(v3.x, v1.w, c_next.x, c.x, t.beta);
-                o1 = psf::cv_combine(v3.y, v2.w, c_next.y, c.y, t.beta);
-                o2 = psf::cv_combine(v3.z, v3.w, c_next.z, c.z, t.beta);
-            }
-            float* o = out + 3 * i;
-            o[0] = o0;
-            o[1] = o1;
-            o[2] = o2;
-            c_next = c;
-        }
-    }
+         p += stride)
+        psf::query_path(t, v, P, D, p, out);
 }
 
 __global__ void __launch_bounds__(kThreads) k_export(TableView t, unsigned long long s0, unsigned long long s1,
@@ -243,7 +223,7 @@ extern "C" {
 
 int psf_abi_version(void) { return PSF_ABI_VERSION; }
 
-const char* psf_last_cuda_error(void) { return g_last_error.c_str(); }
+const char* psf_last_cuda_error(void) { return psf_g_last_error.c_str(); }
 
 size_t psf_table_bytes(const psf_config* cfg) {
     if (!config_valid(cfg)) return 0;

@@ -1,0 +1,336 @@
+// psf_batch.cu -- one persistent fused insert + update + query kernel per iteration
+// across many tables (render sessions of different sizes and depths).
+//
+// Work is cut into warp units: 32 vertices of one table (insert), 32 dirty-bitmap
+// words = 1024 slots of one table (update), 32 paths of one table (query).  Per phase,
+// each warp walks the global unit range with a stride of the whole grid and finds its
+// table by binary search over the per-table prefix sums (kept in shared memory).  The
+// phases are separated by a grid barrier; the kernel is launched cooperatively so every
+// block is resident, and each wait is bounded by a timeout.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "psf.h"
+#include "psf_device.cuh"
+#include "psf_table.h"
+
+namespace {
+
+using psf::kThreads;
+using psf::TableView;
+
+struct BatchItemDev {
+    TableView t;
+    const float4* v;
+    float* out;
+    unsigned P;
+    unsigned D;
+    unsigned long long nverts;
+};
+
+struct BatchCtl {  // barrier words and sticky status (not overwritten by psf_batch_set)
+    unsigned barrier_count;
+    unsigned barrier_gen;
+    unsigned status;
+    unsigned pad[61];
+};
+static_assert(sizeof(BatchCtl) == 256, "control block is 256 bytes");
+
+struct BatchHdr {  // written by psf_batch_set
+    unsigned n;
+    unsigned phantom;
+    unsigned long long timeout_ns;
+    unsigned long long units[3];  // warp units per phase
+    unsigned long long pad[27];
+};
+static_assert(sizeof(BatchHdr) == 256, "batch header is 256 bytes");
+
+constexpr unsigned kMaxItems = PSF_MAX_BATCH;
+constexpr size_t kBeginBytes = 3 * (kMaxItems + 1) * sizeof(unsigned long long);
+
+size_t batch_bytes(uint32_t max_items) {
+    return sizeof(BatchCtl) + sizeof(BatchHdr) + kBeginBytes + static_cast<size_t>(max_items) * sizeof(BatchItemDev);
+}
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a co-resident grid.  The wait is bounded: on timeout the block
+// records PSF_STATUS_TIMEOUT (batch and every table) and the kernel leaves.
+__device__ bool grid_barrier(BatchCtl* ctl, const BatchHdr* h, const BatchItemDev* __restrict__ items) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* gen_p = &ctl->barrier_gen;
+        const unsigned gen = *gen_p;
+        __threadfence();
+        const unsigned expected = gridDim.x + h->phantom;
+        const unsigned arrived = atomicAdd(&ctl->barrier_count, 1u) + 1u;
+        if (arrived == expected) {
+            atomicExch(&ctl->barrier_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->barrier_gen, 1u);
+        } else {
+            const unsigned long long t0 = global_timer_ns();
+            while (*gen_p == gen) {
+                if (global_timer_ns() - t0 > h->timeout_ns) {
+                    ok = 0;
+                    atomicOr(&ctl->status, psf::kStatusTimeout);
+                    for (unsigned i = 0; i < h->n; ++i) atomicOr(&items[i].t.hdr->status, psf::kStatusTimeout);
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void load_begin(unsigned long long* s_begin, const unsigned long long* begin, unsigned n) {
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i <= n; i += blockDim.x) s_begin[i] = begin[i];
+    __syncthreads();
+}
+
+// Table owning warp unit u: the last i with begin[i] <= u (tables without units are skipped).
+__device__ __forceinline__ unsigned find_item(const unsigned long long* s_begin, unsigned n, unsigned long long u) {
+    unsigned lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (s_begin[mid] <= u)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+template <int kMode>
+__global__ void __launch_bounds__(kThreads)
+    k_batch(BatchCtl* ctl, const BatchHdr* __restrict__ h, const unsigned long long* __restrict__ begin,
+            const BatchItemDev* __restrict__ items) {
+    __shared__ unsigned long long s_begin[kMaxItems + 1];
+    const unsigned n = h->n;
+    if (n == 0) return;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long warp = (static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = (static_cast<unsigned long long>(gridDim.x) * blockDim.x) >> 5;
+
+    // phase 1: scatter every table's vertices
+    load_begin(s_begin, begin, n);
+    for (unsigned long long u = warp; u < h->units[0]; u += nwarps) {
+        const unsigned it = find_item(s_begin, n, u);
+        const BatchItemDev& b = items[it];
+        const unsigned long long i = (u - s_begin[it]) * 32ull + lane;
+        const bool valid = i < b.nverts;
+        float4 v0 = make_float4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
+        if (valid) {
+            const float4* r = b.v + 4 * i;
+            v0 = __ldcs(r);
+            v1 = __ldcs(r + 1);
+            v2 = __ldcs(r + 2);
+            v3 = __ldcs(r + 3);
+        }
+        unsigned len = 0;
+        psf::insert_warp<kMode>(b.t, valid, v0, v1, v2, v3, &len);
+        if (len > 16u) atomicMax(&b.t.hdr->max_probe, len);  // only long probes are recorded here
+    }
+    if (!grid_barrier(ctl, h, items)) return;
+
+    // phase 2: blend every table's touched cells
+    load_begin(s_begin, begin + (kMaxItems + 1), n);
+    for (unsigned long long u = warp; u < h->units[1]; u += nwarps) {
+        const unsigned it = find_item(s_begin, n, u);
+        const BatchItemDev& b = items[it];
+        const unsigned long long w0 = (u - s_begin[it]) * 32ull;
+        const unsigned long long nwords = ((1ull << b.t.log2cap) + 31ull) >> 5;
+        if (w0 == 0 && lane == 0) {
+            if (b.t.h_status) *reinterpret_cast<volatile unsigned*>(b.t.h_status) = b.t.hdr->status;
+            b.t.hdr->iterations += 1;
+        }
+        const unsigned total = psf::update_words(b.t, w0, nwords);
+        if (lane == 0 && total) atomicAdd(&b.t.hdr->touched, static_cast<unsigned long long>(total));
+    }
+    if (!grid_barrier(ctl, h, items)) return;
+
+    // phase 3: every table's control-variate query
+    load_begin(s_begin, begin + 2 * (kMaxItems + 1), n);
+    for (unsigned long long u = warp; u < h->units[2]; u += nwarps) {
+        const unsigned it = find_item(s_begin, n, u);
+        const BatchItemDev& b = items[it];
+        const unsigned long long p = (u - s_begin[it]) * 32ull + lane;
+        if (p < b.P) psf::query_path(b.t, b.v, b.P, b.D, p, b.out);
+    }
+}
+
+}  // namespace
+
+struct psf_batch {
+    uint32_t max_items;
+    psf_batch_config cfg;
+    char* d_buf;
+    char* h_stage;
+    cudaEvent_t staged;
+    bool pending;
+    int device;
+    int sms;
+    int per_sm[2];
+};
+
+extern "C" {
+
+int psf_batch_create(uint32_t max_items, const psf_batch_config* cfg, psf_batch** out) {
+    if (!out || max_items == 0 || max_items > kMaxItems) return PSF_ERR_INVALID_ARG;
+    *out = nullptr;
+    psf_batch* b = new (std::nothrow) psf_batch();
+    if (!b) return PSF_ERR_NO_MEM;
+    b->max_items = max_items;
+    b->cfg = cfg ? *cfg : psf_batch_config{0u, 0u, 0u, 0u};
+    if (b->cfg.insert_mode > 1) {
+        delete b;
+        return PSF_ERR_INVALID_ARG;
+    }
+    const size_t bytes = batch_bytes(max_items);
+    bool ok = psf_cuda_ok(cudaGetDevice(&b->device), "cudaGetDevice") &&
+              psf_cuda_ok(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device), "attribute") &&
+              psf_cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm[0], k_batch<psf::kAggWarp>, kThreads, 0),
+                          "occupancy") &&
+              psf_cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm[1], k_batch<psf::kAggNone>, kThreads, 0),
+                          "occupancy");
+    if (ok) ok = psf_cuda_ok(cudaMalloc(reinterpret_cast<void**>(&b->d_buf), bytes), "cudaMalloc");
+    if (ok) {
+        ok = psf_cuda_ok(cudaHostAlloc(reinterpret_cast<void**>(&b->h_stage), bytes, cudaHostAllocDefault), "cudaHostAlloc");
+        if (!ok) cudaFree(b->d_buf);
+    }
+    if (ok) {
+        ok = psf_cuda_ok(cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming), "cudaEventCreate");
+        if (!ok) {
+            cudaFree(b->d_buf);
+            cudaFreeHost(b->h_stage);
+        }
+    }
+    if (ok) {
+        std::memset(b->h_stage, 0, bytes);
+        ok = psf_cuda_ok(cudaMemset(b->d_buf, 0, bytes), "cudaMemset");
+        if (!ok) {
+            cudaFree(b->d_buf);
+            cudaFreeHost(b->h_stage);
+            cudaEventDestroy(b->staged);
+        }
+    }
+    if (!ok) {
+        delete b;
+        return PSF_ERR_CUDA;
+    }
+    *out = b;
+    return PSF_OK;
+}
+
+int psf_batch_set(psf_batch* b, const psf_batch_item* items, uint32_t n, void* stream) {
+    if (!b || n > b->max_items || (n && !items)) return PSF_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < n; ++i) {
+        const psf_batch_item& it = items[i];
+        if (!it.table) return PSF_ERR_INVALID_ARG;
+        const unsigned long long nv = static_cast<unsigned long long>(it.P) * it.D;
+        if (nv && (!it.d_vertices || !it.d_out_rgb || (reinterpret_cast<uintptr_t>(it.d_vertices) & 15u) ||
+                   (reinterpret_cast<uintptr_t>(it.d_out_rgb) & 3u)))
+            return PSF_ERR_INVALID_ARG;
+    }
+    // the staging buffer may still feed the previous copy
+    if (b->pending && !psf_cuda_ok(cudaEventSynchronize(b->staged), "cudaEventSynchronize")) return PSF_ERR_CUDA;
+    BatchHdr* h = reinterpret_cast<BatchHdr*>(b->h_stage + sizeof(BatchCtl));
+    unsigned long long* begin = reinterpret_cast<unsigned long long*>(b->h_stage + sizeof(BatchCtl) + sizeof(BatchHdr));
+    BatchItemDev* dev = reinterpret_cast<BatchItemDev*>(b->h_stage + sizeof(BatchCtl) + sizeof(BatchHdr) + kBeginBytes);
+    h->n = n;
+    h->phantom = b->cfg.test_phantom_blocks;
+    h->timeout_ns = 1000ull * (b->cfg.barrier_timeout_us ? b->cfg.barrier_timeout_us : 2000000u);
+    unsigned long long acc[3] = {0, 0, 0};
+    for (uint32_t i = 0; i < n; ++i) {
+        const psf_batch_item& it = items[i];
+        BatchItemDev& d = dev[i];
+        d.t = it.table->view;
+        d.v = reinterpret_cast<const float4*>(it.d_vertices);
+        d.out = it.d_out_rgb;
+        d.P = it.P;
+        d.D = it.D;
+        d.nverts = static_cast<unsigned long long>(it.P) * it.D;
+        const unsigned long long nwords = ((1ull << it.table->cfg.log2_capacity) + 31ull) >> 5;
+        const unsigned long long units[3] = {(d.nverts + 31) / 32, (nwords + 31) / 32, (static_cast<unsigned long long>(it.P) + 31) / 32};
+        for (int ph = 0; ph < 3; ++ph) {
+            begin[ph * (kMaxItems + 1) + i] = acc[ph];
+            acc[ph] += units[ph];
+        }
+    }
+    for (int ph = 0; ph < 3; ++ph) {
+        begin[ph * (kMaxItems + 1) + n] = acc[ph];
+        h->units[ph] = acc[ph];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t off = sizeof(BatchCtl);
+    const size_t len = sizeof(BatchHdr) + kBeginBytes + static_cast<size_t>(n) * sizeof(BatchItemDev);
+    if (!psf_cuda_ok(cudaMemcpyAsync(b->d_buf + off, b->h_stage + off, len, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync") ||
+        !psf_cuda_ok(cudaEventRecord(b->staged, st), "cudaEventRecord"))
+        return PSF_ERR_CUDA;
+    b->pending = true;
+    return PSF_OK;
+}
+
+int psf_batch_launch(psf_batch* b, void* stream) {
+    if (!b) return PSF_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int mode = b->cfg.insert_mode == 1 ? 1 : 0;
+    int per_sm = b->per_sm[mode];
+    if (b->cfg.blocks_per_sm && static_cast<int>(b->cfg.blocks_per_sm) < per_sm) per_sm = static_cast<int>(b->cfg.blocks_per_sm);
+    if (per_sm < 1) return PSF_ERR_INVALID_ARG;
+    // a fresh barrier for every launch (a timed-out launch leaves its count behind)
+    if (!psf_cuda_ok(cudaMemsetAsync(b->d_buf, 0, 2 * sizeof(unsigned), st), "cudaMemsetAsync")) return PSF_ERR_CUDA;
+    BatchCtl* ctl = reinterpret_cast<BatchCtl*>(b->d_buf);
+    const BatchHdr* h = reinterpret_cast<const BatchHdr*>(b->d_buf + sizeof(BatchCtl));
+    const unsigned long long* begin = reinterpret_cast<const unsigned long long*>(b->d_buf + sizeof(BatchCtl) + sizeof(BatchHdr));
+    const BatchItemDev* items =
+        reinterpret_cast<const BatchItemDev*>(b->d_buf + sizeof(BatchCtl) + sizeof(BatchHdr) + kBeginBytes);
+    void* args[] = {&ctl, &h, &begin, &items};
+    const dim3 grid(static_cast<unsigned>(b->sms * per_sm)), block(kThreads);
+    const void* fn = mode == 1 ? reinterpret_cast<const void*>(k_batch<psf::kAggNone>)
+                               : reinterpret_cast<const void*>(k_batch<psf::kAggWarp>);
+    return psf_cuda_ok(cudaLaunchCooperativeKernel(fn, grid, block, args, 0, st), "k_batch") ? PSF_OK : PSF_ERR_CUDA;
+}
+
+int psf_batch_step(psf_batch* b, const psf_batch_item* items, uint32_t n, void* stream) {
+    const int rc = psf_batch_set(b, items, n, stream);
+    return rc != PSF_OK ? rc : psf_batch_launch(b, stream);
+}
+
+int psf_batch_status(psf_batch* b, uint32_t* status, void* stream) {
+    if (!b || !status) return PSF_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned s = 0;
+    if (!psf_cuda_ok(cudaMemcpyAsync(&s, b->d_buf + offsetof(BatchCtl, status), sizeof(s), cudaMemcpyDeviceToHost, st),
+                     "cudaMemcpyAsync") ||
+        !psf_cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize"))
+        return PSF_ERR_CUDA;
+    *status = s;
+    return PSF_OK;
+}
+
+int psf_batch_destroy(psf_batch* b) {
+    if (!b) return PSF_OK;
+    cudaEventDestroy(b->staged);
+    cudaFreeHost(b->h_stage);
+    cudaFree(b->d_buf);
+    delete b;
+    return PSF_OK;
+}
+
+}  // extern "C"

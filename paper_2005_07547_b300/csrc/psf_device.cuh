@@ -20,6 +20,7 @@
 namespace psf {
 
 constexpr unsigned long long kEmpty = ~0ull;  // bit 63 set: never a valid key
+constexpr int kThreads = 256;                 // threads per block of every kernel
 constexpr unsigned kFull = 0xffffffffu;
 
 constexpr unsigned kStatusTableFull = 1u;
@@ -300,29 +301,45 @@ __device__ __forceinline__ uint2 pack_half4(float a, float b, float c) {
     return r;
 }
 
-__device__ __forceinline__ void blend_slot(const TableView& t, unsigned long long s) {
+struct SlotData {
+    longlong2 a01;  // sum_r, sum_g
+    longlong2 a23;  // sum_b, c_new
+    float4 L;
+    longlong2 co;   // c_old, spare
+};
+
+__device__ __forceinline__ SlotData load_slot(const TableView& t, unsigned long long s) {
+    const longlong2* p = reinterpret_cast<const longlong2*>(t.slots + s);
+    SlotData d;
+    d.a01 = __ldcg(p);
+    d.a23 = __ldcg(p + 1);
+    d.L = __ldcg(reinterpret_cast<const float4*>(p + 2));
+    d.co = __ldcg(p + 3);
+    return d;
+}
+
+// The blend of one loaded slot, then its stores: every store follows the loads it
+// overwrites, so no store waits on an outstanding load of the same bytes.
+__device__ __forceinline__ void blend_store(const TableView& t, unsigned long long s, SlotData d) {
     longlong2* p = reinterpret_cast<longlong2*>(t.slots + s);
-    const longlong2 a01 = __ldcg(p);      // sum_r, sum_g
-    const longlong2 a23 = __ldcg(p + 1);  // sum_b, c_new
-    float4 L = __ldcg(reinterpret_cast<const float4*>(p + 2));
-    const longlong2 co2 = __ldcg(p + 3);  // c_old, spare
-    const long long cn = a23.y;
     const longlong2 z = make_longlong2(0, 0);
+    const long long cn = d.a23.y;
+    if (cn > 0) {  // always true for a touched slot (accepted vertices add weight >= 1)
+        const long long co = d.co.x;
+        const long long ctot = co > (0x7fffffffffffffffll - cn) ? 0x7fffffffffffffffll : co + cn;
+        const float fcn = __ll2float_rn(cn);
+        float alpha = t.alpha_min;
+        if (t.blend_mode == 0) alpha = fmaxf(sqrtf(__fdiv_rn(fcn, __ll2float_rn(ctot))), t.alpha_min);
+        const float keep = 1.0f - alpha;
+        d.L.x = fmaf(alpha, __fdiv_rn(__ll2float_rn(d.a01.x), fcn), keep * d.L.x);
+        d.L.y = fmaf(alpha, __fdiv_rn(__ll2float_rn(d.a01.y), fcn), keep * d.L.y);
+        d.L.z = fmaf(alpha, __fdiv_rn(__ll2float_rn(d.a23.x), fcn), keep * d.L.z);
+        __stcg(reinterpret_cast<float4*>(p + 2), d.L);
+        __stcg(p + 3, make_longlong2(ctot, d.co.y));
+        if (t.mirror) t.mirror[s] = pack_half4(d.L.x, d.L.y, d.L.z);
+    }
     __stcg(p, z);
     __stcg(p + 1, z);
-    if (cn <= 0) return;  // not reachable for accepted vertices; keep the cell unchanged
-    const long long co = co2.x;
-    const long long ctot = co > (0x7fffffffffffffffll - cn) ? 0x7fffffffffffffffll : co + cn;
-    const float fcn = __ll2float_rn(cn);
-    float alpha = t.alpha_min;
-    if (t.blend_mode == 0) alpha = fmaxf(sqrtf(__fdiv_rn(fcn, __ll2float_rn(ctot))), t.alpha_min);
-    const float keep = 1.0f - alpha;
-    L.x = fmaf(alpha, __fdiv_rn(__ll2float_rn(a01.x), fcn), keep * L.x);
-    L.y = fmaf(alpha, __fdiv_rn(__ll2float_rn(a01.y), fcn), keep * L.y);
-    L.z = fmaf(alpha, __fdiv_rn(__ll2float_rn(a23.x), fcn), keep * L.z);
-    __stcg(reinterpret_cast<float4*>(p + 2), L);
-    __stcg(p + 3, make_longlong2(ctot, co2.y));
-    if (t.mirror) t.mirror[s] = pack_half4(L.x, L.y, L.z);
 }
 
 // Position of the n-th (0-based) set bit of w (n < popc(w)).
@@ -357,18 +374,30 @@ __device__ __forceinline__ unsigned update_words(const TableView& t, unsigned lo
     }
     const unsigned total = __shfl_sync(kFull, incl, 31);
     const unsigned excl = incl - cnt;
-    for (unsigned r = 0; r < total; r += 32) {
-        const unsigned idx = r + lane;
-        unsigned owner = 0;  // number of lanes whose inclusive count is <= idx
+    // two slots per lane per round: both slots' loads are in flight before either blends
+    for (unsigned r = 0; r < total; r += 64) {
+        unsigned long long slot[2];
+        bool have[2];
 #pragma unroll
-        for (unsigned step = 16; step > 0; step >>= 1) {
-            const unsigned v = __shfl_sync(kFull, incl, owner + step - 1);
-            if (v <= idx) owner += step;
+        for (int k = 0; k < 2; ++k) {
+            const unsigned idx = r + 32u * k + lane;
+            unsigned owner = 0;  // number of lanes whose inclusive count is <= idx
+#pragma unroll
+            for (unsigned step = 16; step > 0; step >>= 1) {
+                const unsigned v = __shfl_sync(kFull, incl, owner + step - 1);
+                if (v <= idx) owner += step;
+            }
+            owner &= 31u;
+            const unsigned ow = __shfl_sync(kFull, word, owner);
+            const unsigned oe = __shfl_sync(kFull, excl, owner);
+            have[k] = idx < total;
+            slot[k] = have[k] ? (w0 + owner) * 32ull + select_bit(ow, idx - oe) : 0ull;
         }
-        owner &= 31u;
-        const unsigned ow = __shfl_sync(kFull, word, owner);
-        const unsigned oe = __shfl_sync(kFull, excl, owner);
-        if (idx < total) blend_slot(t, (w0 + owner) * 32ull + select_bit(ow, idx - oe));
+        SlotData d0, d1;
+        if (have[0]) d0 = load_slot(t, slot[0]);
+        if (have[1]) d1 = load_slot(t, slot[1]);
+        if (have[0]) blend_store(t, slot[0], d0);
+        if (have[1]) blend_store(t, slot[1], d1);
     }
     return total;
 }
@@ -399,6 +428,44 @@ __device__ __forceinline__ float3 cell_value(const TableView& t, const float4& v
 __device__ __forceinline__ float cv_combine(float L, float tj, float c_next, float c_self, float beta) {
     const float h = __fmul_rn(tj, c_next);
     return __fadd_rn(__fsub_rn(L, __fmul_rn(beta, h)), __fmul_rn(beta, c_self));
+}
+
+// All vertices of path p (depth-major records j*P + p), last to first so that each vertex
+// is probed once: its cell value serves as C_j here and as C_{j+1} for vertex j - 1.  The
+// record of vertex j - 1 is loaded before vertex j is probed, so the two latencies overlap.
+__device__ __forceinline__ void query_path(const TableView& t, const float4* __restrict__ v, unsigned P, unsigned D,
+                                           unsigned long long p, float* __restrict__ out) {
+    float3 c_next = make_float3(0.0f, 0.0f, 0.0f);
+    int j = static_cast<int>(D) - 1;
+    const float4* r = v + 4 * (static_cast<unsigned long long>(j) * P + p);  // streamed once: evict-first
+    float4 v0 = __ldcs(r), v1 = __ldcs(r + 1), v2 = __ldcs(r + 2), v3 = __ldcs(r + 3);
+    for (; j >= 0; --j) {
+        float4 n0 = v0, n1 = v1, n2 = v2, n3 = v3;
+        if (j > 0) {
+            const float4* rn = v + 4 * (static_cast<unsigned long long>(j - 1) * P + p);
+            n0 = __ldcs(rn);
+            n1 = __ldcs(rn + 1);
+            n2 = __ldcs(rn + 2);
+            n3 = __ldcs(rn + 3);
+        }
+        const unsigned long long i = static_cast<unsigned long long>(j) * P + p;
+        const float3 c = cell_value(t, v0, v1, v2);
+        float o0 = v3.x, o1 = v3.y, o2 = v3.z;
+        if (j + 1 < static_cast<int>(D) && static_cast<unsigned>(j) < t.cv_max_depth) {
+            o0 = cv_combine(v3.x, v1.w, c_next.x, c.x, t.beta);
+            o1 = cv_combine(v3.y, v2.w, c_next.y, c.y, t.beta);
+            o2 = cv_combine(v3.z, v3.w, c_next.z, c.z, t.beta);
+        }
+        float* o = out + 3 * i;
+        o[0] = o0;
+        o[1] = o1;
+        o[2] = o2;
+        c_next = c;
+        v0 = n0;
+        v1 = n1;
+        v2 = n2;
+        v3 = n3;
+    }
 }
 
 }  // namespace psf

@@ -1,0 +1,204 @@
+"""Continuous-batching server for render sessions.
+
+Requests (render sessions: image size, path depth, number of iterations) arrive over
+time.  Each server tick:
+
+  1. admits queued requests, first come first served, while their tables fit the
+     device-memory budget and a batch slot is free (a new session's table is created
+     in caller-owned memory and lives on the device until the session retires);
+  2. runs ONE iteration of every live session: in "batched" mode a single fused
+     persistent kernel for all of them (captured once in a CUDA graph and replayed;
+     joins and leaves only rewrite the device descriptors), in "plain" mode one
+     psf_step per session, back to back;
+  3. retires sessions that reached their iteration count and frees their tables.
+
+Sessions are closed loops: a session's next iteration starts when its previous one has
+completed.  Per-iteration latency is the time from the start of a tick to the
+completion of that session's iteration; admission delay is the time from arrival to
+admission.  Every session's results are independent of who else is in the batch.
+"""
+
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _abi
+from .batch import Batch
+from .table import Table
+
+
+@dataclass
+class Session:
+    request: dict
+    table: Table
+    out: object
+    P: int
+    D: int
+    arrival: float
+    admitted: float
+    done: int = 0
+    latencies_ms: list = field(default_factory=list)
+
+
+def table_config(req: dict) -> _abi.Config:
+    return _abi.make_config(log2_capacity=req["log2_capacity"], pos_bits=req["pos_bits"], dir_bits=req["dir_bits"],
+                            alpha_min=req["alpha_min"], cache_fp16=req.get("cache_fp16", True))
+
+
+def table_bytes(req: dict) -> int:
+    import ctypes
+
+    return int(_abi.load().psf_table_bytes(ctypes.byref(table_config(req))))
+
+
+class Server:
+    def __init__(self, vertex_source, budget_bytes: float = 60e9, max_live: int = _abi.MAX_BATCH,
+                 mode: str = "batched", use_graph: bool = True, batch_knobs: dict | None = None,
+                 on_retire=None):
+        """vertex_source(request, iteration) -> (P*D, 16) float32 CUDA tensor of that iteration;
+        on_retire(session), if given, sees each session (table still open) before it is freed."""
+        if mode not in ("batched", "plain"):
+            raise ValueError("mode must be 'batched' or 'plain'")
+        self.source = vertex_source
+        self.budget = float(budget_bytes)
+        self.max_live = min(max_live, _abi.MAX_BATCH)
+        self.mode = mode
+        self.use_graph = use_graph and mode == "batched"
+        self.batch = Batch(self.max_live, **(batch_knobs or {})) if mode == "batched" else None
+        self.graph = None
+        self.live: list[Session] = []
+        self.used = 0
+        self.finished: list[Session] = []
+        self.ticks = 0
+        self.vertices = 0
+        self.admission_ms: list[float] = []
+        self.on_retire = on_retire
+
+    # -- membership ---------------------------------------------------------------------
+    def _admit(self, queue: deque, now: float) -> bool:
+        import torch
+
+        changed = False
+        while queue and len(self.live) < self.max_live:
+            req = queue[0]
+            need = table_bytes(req)
+            if self.used + need > self.budget:
+                break
+            queue.popleft()
+            P, D = req["width"] * req["height"], req["depth"]
+            t = Table(table_config(req))
+            out = torch.empty((P * D, 3), dtype=torch.float32, device="cuda")
+            self.live.append(Session(req, t, out, P, D, req["arrival_s"], now))
+            self.used += t.nbytes
+            self.admission_ms.append(1e3 * (now - req["arrival_s"]))
+            changed = True
+        return changed
+
+    def _retire(self) -> bool:
+        keep, changed = [], False
+        for s in self.live:
+            if s.done >= s.request["iterations"]:
+                if self.on_retire is not None:
+                    self.on_retire(s)
+                self.used -= s.table.nbytes
+                s.table.close()
+                s.out = None
+                self.finished.append(s)
+                changed = True
+            else:
+                keep.append(s)
+        self.live = keep
+        return changed
+
+    # -- one iteration of every live session ---------------------------------------------
+    def _entries(self):
+        return [(s.table, self.source(s.request, s.done), s.out, s.P, s.D) for s in self.live]
+
+    def _tick(self, membership_changed: bool) -> None:
+        import torch
+
+        start = torch.cuda.Event(enable_timing=True)
+        if self.mode == "batched":
+            end = torch.cuda.Event(enable_timing=True)
+            # the descriptors point at each session's input of its current iteration
+            self.batch.set(self._entries())
+            start.record()
+            if self.use_graph:
+                if self.graph is None:
+                    self.graph = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(self.graph):
+                        self.batch.launch()
+                    start.record()
+                self.graph.replay()
+            else:
+                self.batch.launch()
+            end.record()
+            end.synchronize()
+            ms = start.elapsed_time(end)
+            for s in self.live:
+                s.latencies_ms.append(ms)
+        else:
+            evs = []
+            start.record()
+            for s in self.live:
+                s.table.step(self.source(s.request, s.done), s.P, s.D, out=s.out)
+                e = torch.cuda.Event(enable_timing=True)
+                e.record()
+                evs.append(e)
+            evs[-1].synchronize()
+            for s, e in zip(self.live, evs):
+                s.latencies_ms.append(start.elapsed_time(e))
+        for s in self.live:
+            s.done += 1
+            self.vertices += s.P * s.D
+        self.ticks += 1
+
+    # -- driver ---------------------------------------------------------------------------
+    def run(self, requests: list[dict], duration_s: float, drain: bool = False) -> dict:
+        """Serve `requests` (sorted by arrival_s) for duration_s of wall time (then optionally
+        until every admitted session has finished).  Returns the report."""
+        pending = deque(sorted(requests, key=lambda r: r["arrival_s"]))
+        queue: deque = deque()
+        t0 = time.perf_counter()
+        changed = True
+        while True:
+            now = time.perf_counter() - t0
+            while pending and pending[0]["arrival_s"] <= now:
+                queue.append(pending.popleft())
+            if now < duration_s:
+                changed |= self._admit(queue, now)
+            elif not drain or not self.live:
+                break
+            if not self.live:
+                if not pending:
+                    break
+                time.sleep(max(0.0, min(pending[0]["arrival_s"] - now, 0.01)))
+                continue
+            self._tick(changed)
+            changed = self._retire()
+        wall = time.perf_counter() - t0
+        lat = [x for s in self.finished + self.live for x in s.latencies_ms]
+        report = {
+            "mode": self.mode, "graph": self.use_graph, "wall_s": wall, "ticks": self.ticks,
+            "vertices": self.vertices, "vertices_per_s": self.vertices / wall if wall > 0 else 0.0,
+            "sessions_finished": len(self.finished), "sessions_live_at_end": len(self.live),
+            "requests_waiting_at_end": len(queue) + len(pending),
+            "iteration_latency_ms": {"p50": float(np.percentile(lat, 50)) if lat else None,
+                                     "p99": float(np.percentile(lat, 99)) if lat else None},
+            "admission_delay_ms": {"p50": float(np.percentile(self.admission_ms, 50)) if self.admission_ms else None,
+                                   "p99": float(np.percentile(self.admission_ms, 99)) if self.admission_ms else None},
+            "peak_table_bytes_budget": self.budget,
+        }
+        return report
+
+    def close(self) -> None:
+        for s in self.live:
+            s.table.close()
+        self.live = []
+        if self.batch is not None:
+            self.batch.close()
+        self.graph = None
