@@ -219,6 +219,44 @@ class ClockSampler:
                 "power_w_max": max(s[2] for s in self.samples), "source": "NVML (libnvidia-ml), 1 ms"}
 
 
+def atomic_probe_rates(modes=(0, 1, 2, 3), n_words: int = 1 << 25, reps: int = 3) -> dict:
+    """Measured L2 64-bit atomic throughput (ops/s) on this GPU, per probe mode, on a buffer of
+    n_words 64-bit words (2^25 words = 256 MB, larger than L2, like a 2^22-slot table)."""
+    import ctypes
+
+    import torch
+
+    from paper_2005_07547_b300 import build as _b
+
+    _b.build()
+    lib = ctypes.CDLL(_b.PROBE_LIB)
+    lib.atomic_probe.restype = ctypes.c_int
+    lib.atomic_probe.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_void_p]
+    buf = torch.zeros(n_words * 8 + (n_words // 128) * 4, dtype=torch.uint8, device="cuda")
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    stream = torch.cuda.current_stream()
+    out = {}
+    names = {0: "red_random_u64", 1: "atom_random_u64", 2: "insert_pattern_4red_1or", 3: "red_warp_contended_u64"}
+    for mode in modes:
+        groups = (1 << 24) if mode == 2 else (1 << 26)
+        ops_per_group = 5 if mode == 2 else 1
+        args = (buf.data_ptr(), n_words, groups, mode, sms * 8, stream.cuda_stream)
+        if lib.atomic_probe(*args) != 0:
+            raise RuntimeError("atomic probe failed")
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(reps):
+            lib.atomic_probe(*args)
+        end.record(stream)
+        torch.cuda.synchronize()
+        sec = start.elapsed_time(end) / 1e3
+        out[names[mode]] = groups * ops_per_group * reps / sec
+    del buf
+    return out
+
+
 # ---------------------------------------------------------------------------
 # input generation (host, seeded; before any CUDA work)
 # ---------------------------------------------------------------------------
@@ -378,6 +416,7 @@ def run_psf(args) -> None:
           "k_query": [e[2].elapsed_time(e[3]) for e in ev]}
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     touched = (after["touched_cells"] - before["touched_cells"]) / args.steps
+    leaders = (after["leader_groups"] - before["leader_groups"]) / args.steps
 
     if world > 1:
         t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
@@ -401,6 +440,15 @@ def run_psf(args) -> None:
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
                 "algorithmic_bytes_per_launch": alg[dominant], "traffic": load_traffic(dominant)}
+    # atomic roofline of the insert: 5 atomics per (warp, key) group against the probe's rate
+    # for the same pattern (4 reductions into one random 32-byte sector + 1 bitmap reduction)
+    probe = atomic_probe_rates(modes=(2,)) if rank == 0 else {}
+    atom_rate = 5.0 * leaders / (avg["k_insert"] / 1e3)
+    atomic_roofline = {"kernel": "k_insert", "achieved": atom_rate / 1e9, "unit": "G atomics/s",
+                       "peak": probe.get("insert_pattern_4red_1or", float("nan")) / 1e9,
+                       "frac": atom_rate / probe["insert_pattern_4red_1or"] if probe else None,
+                       "atomics_per_launch": 5.0 * leaders, "leader_groups_per_launch": leaders,
+                       "peak_source": "live probe: 4 x red.add.u64 into one random 32-B sector + red.or, 256 MB"}
     kernels = {k: {"avg_ms": avg[k], "share": avg[k] / sum(avg.values()),
                    "algorithmic_GBps": alg[k] / (avg[k] / 1e3) / 1e9,
                    "frac_of_hbm": alg[k] / (avg[k] / 1e3) / 1e9 / peaks["hbm_gbs"]} for k in avg}
@@ -424,6 +472,7 @@ def run_psf(args) -> None:
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "mean": float(np.mean(step_ms))},
         "roofline": roofline,
+        "atomic_roofline": atomic_roofline,
         "kernels": kernels,
         "gpu_launches": 3 * args.steps,
         "clocks": clocks.summary(),
@@ -721,6 +770,13 @@ def main(argv=None) -> None:
         run_sessions(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "atomics":
+        import torch
+
+        torch.cuda.set_device(dist_env()[2])
+        rates = {"l2_resident_32MB": atomic_probe_rates(n_words=1 << 22),
+                 "dram_backed_256MB": atomic_probe_rates(n_words=1 << 25)}
+        print(json.dumps({"metric": "L2 64-bit atomic throughput", "unit": "ops/s", "rates": rates}), flush=True)
     else:
         run_psf(args)
 

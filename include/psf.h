@@ -107,6 +107,8 @@ typedef struct {
     uint32_t max_probe;            /* longest probe sequence seen by an insert */
     uint64_t table_bytes;          /* psf_table_bytes of the configuration */
     uint64_t touched_cells;        /* cells blended by all psf_update calls so far */
+    uint64_t leader_groups;        /* (warp, key) groups that probed and added, all inserts so far
+                                      (each issues five atomics); not counted by batched launches */
 } psf_stats;
 
 /* Bytes of device memory a table with this configuration needs (0 if the
@@ -125,6 +127,19 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
  * per iteration.  n = 0 is a no-op. */
 int psf_insert(psf_table* t, const float* d_vertices, uint64_t n, void* stream);
 
+/* Progressive update values (Section "Progressive solver", eq. (9); Alg. 1 and Alg. 2):
+ * instead of each vertex's own tail estimate, the value scattered for vertex j comes from
+ * the current approximant L~old of the cell of the next vertex of its path (read before
+ * this iteration's psf_update).  d_vertices: D*P records, depth-major; v3.xyz is read as
+ * the vertex's emitted radiance L_e and t_j as its throughput to vertex j + 1.
+ *   field 0 (L~_o, Alg. 1):      value_j = L_e,j + t_j * L~old(x_{j+1})     (last vertex: L_e,j)
+ *   field 1 (L~_{o\e}, Alg. 2):  value_j = t_j * (L_e,j+1 + L~old(x_{j+1}))  (last vertex: 0)
+ * computed in FP32 from the FP32 approximant (also with cache_fp16), then scattered
+ * exactly as psf_insert scatters L = value (range rule included).  The next-event term
+ * that Alg. 2 may add at a vertex is the caller's to add through a plain psf_insert. */
+int psf_insert_progressive(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, uint32_t field,
+                           void* stream);
+
 /* End of iteration: every cell with c_new > 0 gets
  *   alpha = max(sqrt(c_new / (c_old + c_new)), alpha_min)        (eq. 11; blend_mode 0)
  *   L~ = (1 - alpha) L~ + alpha * sum / c_new                    (eq. 10)
@@ -141,6 +156,16 @@ int psf_update(psf_table* t, void* stream);
  * next vertex, whose known integral is C_j.)  d_out_rgb receives D*P*3 float32 in the vertex order. */
 int psf_query_cv(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float* d_out_rgb,
                  void* stream);
+
+/* Biased predictor-corrector estimate (Section "Biased estimation", equation
+ * BiasedEstimator: the control variate at beta = 1 with its corrector scaled by gamma):
+ *   out_j = gamma * (L_j - t_j * C_{j+1}) + C_j   for j_begin <= j < j_end with j < D - 1
+ *   out_j = L_j                                    otherwise
+ * gamma = 0 at j_begin = 1, j_end = 2 is the paper's PSTF-B (the approximant replaces the
+ * path's estimate at the second vertex); gamma = 1 over all vertices equals psf_query_cv
+ * with beta = 1.  Layouts and errors as psf_query_cv; a NaN gamma is PSF_ERR_INVALID_ARG. */
+int psf_query_biased(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float gamma, uint32_t j_begin,
+                     uint32_t j_end, float* d_out_rgb, void* stream);
 
 /* One whole iteration: psf_insert of the D*P vertices, psf_update, psf_query_cv. */
 int psf_step(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float* d_out_rgb,

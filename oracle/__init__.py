@@ -46,9 +46,11 @@ _lib = None
 
 
 def lib() -> ctypes.CDLL:
+    """The oracle library; PSF_ORACLE_LIB names another build of it (the mutation tests
+    point it at deliberately broken copies to check that the pins catch them)."""
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
+        L = ctypes.CDLL(os.environ.get("PSF_ORACLE_LIB") or build())
         vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
         L.oracle_create.restype = vp
         L.oracle_create.argtypes = [ctypes.POINTER(_Config)]
@@ -57,11 +59,14 @@ def lib() -> ctypes.CDLL:
         L.oracle_key.argtypes = [ctypes.POINTER(_Config), vp, ctypes.POINTER(u64)]
         L.oracle_insert.restype = u32
         L.oracle_insert.argtypes = [vp, vp, u64]
+        L.oracle_insert_progressive.restype = u32
+        L.oracle_insert_progressive.argtypes = [vp, vp, u32, u32, u32]
         L.oracle_update.restype = u32
         L.oracle_update.argtypes = [vp]
         L.oracle_reset.argtypes = [vp]
         L.oracle_query_cv.argtypes = [vp, vp, u32, u32, vp]
         L.oracle_lookup.argtypes = [vp, vp, u64, vp]
+        L.oracle_query_biased.argtypes = [vp, vp, u32, u32, ctypes.c_double, u32, u32, vp]
         L.oracle_size.restype = u64
         L.oracle_size.argtypes = [vp]
         L.oracle_counters.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
@@ -113,6 +118,13 @@ class Oracle:
         v = _verts(verts)
         return int(lib().oracle_insert(self._h, v.ctypes.data, v.shape[0]))
 
+    def insert_progressive(self, verts: np.ndarray, P: int, D: int, field: int = 0) -> int:
+        """Scatter with update values from the approximant at the next vertex (eq. 9)."""
+        v = _verts(verts)
+        if v.shape[0] != P * D:
+            raise ValueError("vertex count must be P*D")
+        return int(lib().oracle_insert_progressive(self._h, v.ctypes.data, P, D, field))
+
     def update(self) -> int:
         return int(lib().oracle_update(self._h))
 
@@ -125,6 +137,15 @@ class Oracle:
             raise ValueError("vertex count must be P*D")
         out = np.empty((P * D, 3), dtype=np.float64)
         lib().oracle_query_cv(self._h, v.ctypes.data, P, D, out.ctypes.data)
+        return out
+
+    def query_biased(self, verts: np.ndarray, P: int, D: int, gamma: float, j_begin: int = 0,
+                     j_end: int = 0xFFFFFFFF) -> np.ndarray:
+        v = _verts(verts)
+        if v.shape[0] != P * D:
+            raise ValueError("vertex count must be P*D")
+        out = np.empty((P * D, 3), dtype=np.float64)
+        lib().oracle_query_biased(self._h, v.ctypes.data, P, D, float(gamma), j_begin, j_end, out.ctypes.data)
         return out
 
     def lookup(self, verts: np.ndarray) -> np.ndarray:

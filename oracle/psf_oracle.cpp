@@ -19,7 +19,10 @@
 //   * blend: Section "Temporal averaging", eq. (10) and eq. (11), with the global
 //     counter reset described after eq. (11);
 //   * query: Section "Control variates", equation CVEstimator, restated in the
-//     estimator-value form out = L - beta * (t * C_next) + beta * C_self.
+//     estimator-value form out = L - beta * (t * C_next) + beta * C_self;
+//   * biased query: Section "Biased estimation", equation BiasedEstimator,
+//     out = gamma * (L - t * C_next) + C_self;
+//   * progressive update values: Section "Progressive solver", eq. (9), Alg. 1 and 2.
 //
 // Precision: the decisions that produce integers (cell indices, direction bins,
 // fixed-point codes) are taken in FP32 with one correctly rounded IEEE operation
@@ -37,6 +40,7 @@
 #include <cstring>
 #include <map>
 #include <tuple>
+#include <vector>
 
 namespace {
 
@@ -231,6 +235,71 @@ uint32_t oracle_insert(void* h, const float* verts, uint64_t n) {
     return status;
 }
 
+// Progressive update values (Section "Progressive solver", eq. (9); Alg. 1 and Alg. 2):
+// the value scattered for vertex j comes from the current approximant L~old at the next
+// vertex of its path instead of from the path's own tail.  The record's v3.xyz is read as
+// the emitted radiance L_e of the vertex; t_j is its throughput to vertex j + 1.
+//   field 0, L~_o     (Alg. 1): value_j = L_e,j + t_j * L~old(x_{j+1})     (last vertex: L_e,j)
+//   field 1, L~_{o\e} (Alg. 2): value_j = t_j * (L_e,j+1 + L~old(x_{j+1}))  (last vertex: 0;
+//                               the optional next-event-estimation term is not modelled)
+// L~old is read before anything of this call is scattered.  Each vertex is then scattered
+// as oracle_insert does, with L = value_j (fixed point of w * value in FP64).
+uint32_t oracle_insert_progressive(void* h, const float* verts, uint32_t P, uint32_t D, uint32_t field) {
+    Oracle* o = static_cast<Oracle*>(h);
+    const Config& c = o->cfg;
+    const double scale = std::ldexp(1.0, static_cast<int>(c.frac_bits));
+    const uint64_t n = static_cast<uint64_t>(P) * D;
+    std::vector<double> value(3 * n, 0.0);
+    for (uint64_t p = 0; p < P; ++p) {
+        double C_next[3] = {0.0, 0.0, 0.0}, Le_next[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = static_cast<int64_t>(D) - 1; j >= 0; --j) {
+            const uint64_t idx = static_cast<uint64_t>(j) * P + p;
+            const float* v = verts + 16 * idx;
+            const double t[3] = {v[7], v[11], v[15]};
+            double C[3] = {0.0, 0.0, 0.0};
+            CellKey key;
+            if (vertex_cell(c, v, &key)) {
+                auto it = o->cells.find(key);
+                if (it != o->cells.end())
+                    for (int ch = 0; ch < 3; ++ch) C[ch] = it->second.L[ch];
+            }
+            for (int ch = 0; ch < 3; ++ch) {
+                const double Le = v[12 + ch];
+                value[3 * idx + ch] = field == 0 ? Le + t[ch] * C_next[ch] : t[ch] * (Le_next[ch] + C_next[ch]);
+                C_next[ch] = C[ch];
+                Le_next[ch] = Le;
+            }
+        }
+    }
+    uint32_t status = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        const float* v = verts + 16 * i;
+        CellKey key;
+        bool ok = vertex_cell(c, v, &key);
+        const double w = v[3];
+        ok = ok && (w >= 0.0) && (w <= 32768.0);
+        double prod[3] = {0.0, 0.0, 0.0};
+        for (int ch = 0; ch < 3 && ok; ++ch) {
+            prod[ch] = w * value[3 * i + ch];
+            ok = std::isfinite(prod[ch]) && std::fabs(prod[ch]) <= 32768.0;
+        }
+        if (!ok) {
+            status |= ST_RANGE;
+            o->dropped++;
+            continue;
+        }
+        const int64_t cw = std::llrint(w * scale);
+        if (cw == 0) {
+            o->zero_weight++;
+            continue;
+        }
+        Cell& cell = o->cells[key];
+        for (int ch = 0; ch < 3; ++ch) cell.sum[ch] += std::llrint(prod[ch] * scale);
+        cell.c_new += cw;
+    }
+    return status;
+}
+
 // End-of-iteration temporal blend, eq. (10)-(11), for every cell touched this iteration.
 uint32_t oracle_update(void* h) {
     Oracle* o = static_cast<Oracle*>(h);
@@ -288,6 +357,39 @@ void oracle_query_cv(void* h, const float* verts, uint32_t P, uint32_t D, double
             for (int ch = 0; ch < 3; ++ch) {
                 const double L = v[12 + ch];
                 out[3 * idx + ch] = cv ? (L - c.beta * (t[ch] * C_next[ch]) + c.beta * C[ch]) : L;
+            }
+            for (int ch = 0; ch < 3; ++ch) C_next[ch] = C[ch];
+        }
+    }
+}
+
+// Biased predictor-corrector estimator (Section "Biased estimation", equation
+// BiasedEstimator: the control-variate estimator at beta = 1 with the corrector scaled by
+// gamma).  For vertex j of a path with j_begin <= j < j_end and a successor:
+//   out_j = gamma * (L_j - t_j * C_{j+1}) + C_j
+// and out_j = L_j for every other vertex.  gamma = 0 at j = 1 alone is the paper's PSTF-B.
+void oracle_query_biased(void* h, const float* verts, uint32_t P, uint32_t D, double gamma, uint32_t j_begin,
+                         uint32_t j_end, double* out) {
+    Oracle* o = static_cast<Oracle*>(h);
+    const Config& c = o->cfg;
+    for (uint64_t p = 0; p < P; ++p) {
+        double C_next[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = static_cast<int64_t>(D) - 1; j >= 0; --j) {
+            const uint64_t idx = static_cast<uint64_t>(j) * P + p;
+            const float* v = verts + 16 * idx;
+            double C[3] = {0.0, 0.0, 0.0};
+            CellKey key;
+            if (vertex_cell(c, v, &key)) {
+                auto it = o->cells.find(key);
+                if (it != o->cells.end())
+                    for (int ch = 0; ch < 3; ++ch) C[ch] = it->second.L[ch];
+            }
+            const double t[3] = {v[7], v[11], v[15]};
+            const bool on = (j + 1 < static_cast<int64_t>(D)) && (static_cast<uint64_t>(j) >= j_begin) &&
+                            (static_cast<uint64_t>(j) < j_end);
+            for (int ch = 0; ch < 3; ++ch) {
+                const double L = v[12 + ch];
+                out[3 * idx + ch] = on ? (gamma * (L - t[ch] * C_next[ch]) + C[ch]) : L;
             }
             for (int ch = 0; ch < 3; ++ch) C_next[ch] = C[ch];
         }

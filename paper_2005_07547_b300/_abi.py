@@ -67,6 +67,7 @@ class Stats(ctypes.Structure):
         ("max_probe", ctypes.c_uint32),
         ("table_bytes", ctypes.c_uint64),
         ("touched_cells", ctypes.c_uint64),
+        ("leader_groups", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -120,9 +121,11 @@ SIGNATURES = {
     "psf_table_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config)]),
     "psf_create": (_i, [ctypes.POINTER(Config), _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
     "psf_insert": (_i, [_vp, _vp, _u64, _vp]),
+    "psf_insert_progressive": (_i, [_vp, _vp, _u32, _u32, _u32, _vp]),
     "psf_update": (_i, [_vp, _vp]),
     "psf_query_cv": (_i, [_vp, _vp, _u32, _u32, _vp, _vp]),
     "psf_step": (_i, [_vp, _vp, _u32, _u32, _vp, _vp]),
+    "psf_query_biased": (_i, [_vp, _vp, _u32, _u32, ctypes.c_float, _u32, _u32, _vp, _vp]),
     "psf_reset": (_i, [_vp, _vp]),
     "psf_export": (_i, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _vp]),
     "psf_get_stats": (_i, [_vp, ctypes.POINTER(Stats), _vp]),

@@ -19,6 +19,9 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libpsf.so")
 SOURCES = ["psf.cu", "psf_batch.cu"]
 DEPS = SOURCES + ["psf_device.cuh", "psf_table.h"]
+# measurement-only library: the L2 atomic-throughput probe (not part of the filtering path)
+PROBE_LIB = os.path.join(HERE, "libatomic_probe.so")
+PROBE_SOURCES = ["atomic_probe.cu"]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
@@ -35,25 +38,30 @@ def _nvcc() -> str:
     return "nvcc"
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str, deps: list[str]) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in DEPS] + [os.path.join(INCLUDE, "psf.h"), __file__]
-    return any(os.path.getmtime(d) > t for d in deps)
+    t = os.path.getmtime(lib)
+    paths = [os.path.join(CSRC, f) for f in deps] + [os.path.join(INCLUDE, "psf.h"), __file__]
+    return any(os.path.getmtime(d) > t for d in paths)
 
 
-def build(force: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
+def _compile(lib: str, sources: list[str], log: str) -> None:
     cmd = [_nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-I", CSRC,
-           *[os.path.join(CSRC, s) for s in SOURCES], "-o", LIB + ".tmp"]
+           *[os.path.join(CSRC, s) for s in sources], "-o", lib + ".tmp"]
     res = subprocess.run(cmd, capture_output=True, text=True)
-    with open(os.path.join(CSRC, "ptxas.log"), "w") as f:
+    with open(os.path.join(CSRC, log), "w") as f:
         f.write(res.stdout + res.stderr)
     if res.returncode != 0:
         raise RuntimeError("nvcc failed:\n" + res.stderr[-4000:])
-    os.replace(LIB + ".tmp", LIB)
+    os.replace(lib + ".tmp", lib)
+
+
+def build(force: bool = False) -> str:
+    if force or _stale(LIB, DEPS):
+        _compile(LIB, SOURCES, "ptxas.log")
+    if force or _stale(PROBE_LIB, PROBE_SOURCES):
+        _compile(PROBE_LIB, PROBE_SOURCES, "ptxas_probe.log")
     return LIB
 
 

@@ -91,9 +91,16 @@ int grid_for(const psf_table* t, int per_sm, unsigned long long work_items, uint
 template <int kMode>
 __global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* __restrict__ v, unsigned long long n) {
     __shared__ unsigned s_max_probe;
-    if (threadIdx.x == 0) s_max_probe = 0;
+    __shared__ unsigned long long s_leaders;
+    __shared__ psf::LaneSums s_stage[kThreads];
+    if (threadIdx.x == 0) {
+        s_max_probe = 0;
+        s_leaders = 0;
+    }
     __syncthreads();
+    psf::LaneSums* stage = s_stage + (threadIdx.x & ~31u);
     unsigned max_len = 0;
+    unsigned leaders = 0;  // counted by lane 0 of each warp
     const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
     // the next tile's records are loaded while the current tile probes and adds
     unsigned long long base = static_cast<unsigned long long>(blockIdx.x) * blockDim.x;
@@ -115,15 +122,78 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* 
             n2 = __ldcs(r + 2);
             n3 = __ldcs(r + 3);
         }
-        psf::insert_warp<kMode>(t, base + threadIdx.x < n, v0, v1, v2, v3, &max_len);
+        psf::insert_warp<kMode>(t, base + threadIdx.x < n, v0, v1, v2, v3, &max_len, stage, &leaders);
         v0 = n0;
         v1 = n1;
         v2 = n2;
         v3 = n3;
     }
     if (max_len) atomicMax(&s_max_probe, max_len);
+    if ((threadIdx.x & 31u) == 0 && leaders) atomicAdd(&s_leaders, static_cast<unsigned long long>(leaders));
     __syncthreads();
-    if (threadIdx.x == 0 && s_max_probe) atomicMax(&t.hdr->max_probe, s_max_probe);
+    if (threadIdx.x == 0) {
+        if (s_max_probe) atomicMax(&t.hdr->max_probe, s_max_probe);
+        if (s_leaders) atomicAdd(&t.hdr->leaders, s_leaders);
+    }
+}
+
+// Progressive update values (Section "Progressive solver", eq. (9); Alg. 1 and Alg. 2):
+// one thread per path walks its vertices last to first; the FP32 approximant of each
+// vertex's cell (read before this iteration's blend, so it is L~old) feeds the value of
+// the vertex before it, which is then scattered like a plain insert.  Warps hold 32 paths
+// at the same depth, so the warp-level merge of equal keys applies unchanged.
+template <int kMode>
+__global__ void __launch_bounds__(kThreads) k_insert_progressive(TableView t, const float4* __restrict__ v, unsigned P,
+                                                                 unsigned D, unsigned field) {
+    __shared__ unsigned s_max_probe;
+    __shared__ unsigned long long s_leaders;
+    __shared__ psf::LaneSums s_stage[kThreads];
+    if (threadIdx.x == 0) {
+        s_max_probe = 0;
+        s_leaders = 0;
+    }
+    __syncthreads();
+    psf::LaneSums* stage = s_stage + (threadIdx.x & ~31u);
+    unsigned max_len = 0, leaders = 0;
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+    for (unsigned long long base = static_cast<unsigned long long>(blockIdx.x) * blockDim.x; base < P; base += stride) {
+        const unsigned long long p = base + threadIdx.x;
+        const bool valid = p < P;
+        float3 c_next = make_float3(0.0f, 0.0f, 0.0f), le_next = c_next;
+        for (int j = static_cast<int>(D) - 1; j >= 0; --j) {
+            float4 v0 = make_float4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
+            float3 c = make_float3(0.0f, 0.0f, 0.0f);
+            if (valid) {
+                const float4* r = v + 4 * (static_cast<unsigned long long>(j) * P + p);
+                v0 = __ldcs(r);
+                v1 = __ldcs(r + 1);
+                v2 = __ldcs(r + 2);
+                v3 = __ldcs(r + 3);
+                c = psf::cell_value(t, v0, v1, v2, /*fp32_master=*/true);
+            }
+            const float3 le = make_float3(v3.x, v3.y, v3.z);
+            float4 val = v3;  // (value_r, value_g, value_b, t_b)
+            if (field == 0) {  // L~_o: L_e,j + t_j L~old(x_{j+1})
+                val.x = __fadd_rn(le.x, __fmul_rn(v1.w, c_next.x));
+                val.y = __fadd_rn(le.y, __fmul_rn(v2.w, c_next.y));
+                val.z = __fadd_rn(le.z, __fmul_rn(v3.w, c_next.z));
+            } else {  // L~_{o\e}: t_j (L_e,j+1 + L~old(x_{j+1}))
+                val.x = __fmul_rn(v1.w, __fadd_rn(le_next.x, c_next.x));
+                val.y = __fmul_rn(v2.w, __fadd_rn(le_next.y, c_next.y));
+                val.z = __fmul_rn(v3.w, __fadd_rn(le_next.z, c_next.z));
+            }
+            psf::insert_warp<kMode>(t, valid, v0, v1, v2, val, &max_len, stage, &leaders);
+            c_next = c;
+            le_next = le;
+        }
+    }
+    if (max_len) atomicMax(&s_max_probe, max_len);
+    if ((threadIdx.x & 31u) == 0 && leaders) atomicAdd(&s_leaders, static_cast<unsigned long long>(leaders));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_max_probe) atomicMax(&t.hdr->max_probe, s_max_probe);
+        if (s_leaders) atomicAdd(&t.hdr->leaders, s_leaders);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) k_update(TableView t) {
@@ -145,12 +215,12 @@ __global__ void __launch_bounds__(kThreads) k_update(TableView t) {
     if (threadIdx.x == 0 && s_touched) atomicAdd(&t.hdr->touched, s_touched);
 }
 
-__global__ void __launch_bounds__(kThreads) k_query(TableView t, const float4* __restrict__ v, unsigned P, unsigned D,
-                                                    float* __restrict__ out) {
+__global__ void __launch_bounds__(kThreads) k_query(TableView t, psf::Estimator e, const float4* __restrict__ v,
+                                                    unsigned P, unsigned D, float* __restrict__ out) {
     const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
     for (unsigned long long p = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < P;
          p += stride)
-        psf::query_path(t, v, P, D, p, out);
+        psf::query_path(t, e, v, P, D, p, out);
 }
 
 __global__ void __launch_bounds__(kThreads) k_export(TableView t, unsigned long long s0, unsigned long long s1,
@@ -307,6 +377,20 @@ int psf_insert(psf_table* t, const float* d_vertices, uint64_t n, void* stream) 
     return cuda_ok(cudaGetLastError(), "k_insert") ? PSF_OK : PSF_ERR_CUDA;
 }
 
+int psf_insert_progressive(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, uint32_t field, void* stream) {
+    if (!t || field > 1) return PSF_ERR_INVALID_ARG;
+    if (P == 0 || D == 0) return PSF_OK;
+    if (!d_vertices || (reinterpret_cast<uintptr_t>(d_vertices) & 15u)) return PSF_ERR_INVALID_ARG;
+    const int grid = grid_for(t, t->insert_blocks_per_sm, P, t->launch.insert_blocks_per_sm);
+    const float4* v = reinterpret_cast<const float4*>(d_vertices);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (t->launch.insert_mode == 1)
+        k_insert_progressive<psf::kAggNone><<<grid, kThreads, 0, st>>>(t->view, v, P, D, field);
+    else
+        k_insert_progressive<psf::kAggWarp><<<grid, kThreads, 0, st>>>(t->view, v, P, D, field);
+    return cuda_ok(cudaGetLastError(), "k_insert_progressive") ? PSF_OK : PSF_ERR_CUDA;
+}
+
 int psf_update(psf_table* t, void* stream) {
     if (!t) return PSF_ERR_INVALID_ARG;
     const unsigned long long nwords = ((1ull << t->cfg.log2_capacity) + 31ull) >> 5;
@@ -316,16 +400,32 @@ int psf_update(psf_table* t, void* stream) {
     return static_cast<int>(*reinterpret_cast<volatile unsigned*>(t->h_status) & 0x7fffffffu);
 }
 
-int psf_query_cv(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float* d_out_rgb, void* stream) {
+namespace {
+
+int launch_query(psf_table* t, const psf::Estimator& e, const float* d_vertices, uint32_t P, uint32_t D, float* d_out_rgb,
+                 void* stream) {
     if (!t) return PSF_ERR_INVALID_ARG;
     if (P == 0 || D == 0) return PSF_OK;
     if (!d_vertices || !d_out_rgb || (reinterpret_cast<uintptr_t>(d_vertices) & 15u) ||
         (reinterpret_cast<uintptr_t>(d_out_rgb) & 3u))
         return PSF_ERR_INVALID_ARG;
     const int grid = grid_for(t, t->query_blocks_per_sm, P, t->launch.query_blocks_per_sm);
-    k_query<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view, reinterpret_cast<const float4*>(d_vertices), P,
-                                                                      D, d_out_rgb);
+    k_query<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view, e, reinterpret_cast<const float4*>(d_vertices),
+                                                                      P, D, d_out_rgb);
     return cuda_ok(cudaGetLastError(), "k_query") ? PSF_OK : PSF_ERR_CUDA;
+}
+
+}  // namespace
+
+int psf_query_cv(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float* d_out_rgb, void* stream) {
+    if (!t) return PSF_ERR_INVALID_ARG;
+    return launch_query(t, psf::cv_estimator(t->view), d_vertices, P, D, d_out_rgb, stream);
+}
+
+int psf_query_biased(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float gamma, uint32_t j_begin,
+                     uint32_t j_end, float* d_out_rgb, void* stream) {
+    if (!t || !(gamma == gamma)) return PSF_ERR_INVALID_ARG;
+    return launch_query(t, psf::Estimator{gamma, gamma, 1.0f, j_begin, j_end}, d_vertices, P, D, d_out_rgb, stream);
 }
 
 int psf_step(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float* d_out_rgb, void* stream) {
@@ -425,6 +525,7 @@ int psf_get_stats(psf_table* t, psf_stats* out, void* stream) {
     out->max_probe = h.max_probe;
     out->table_bytes = layout_of(&t->cfg).total;
     out->touched_cells = h.touched;
+    out->leader_groups = h.leaders;
     return PSF_OK;
 }
 

@@ -121,6 +121,8 @@ __global__ void __launch_bounds__(kThreads)
     k_batch(BatchCtl* ctl, const BatchHdr* __restrict__ h, const unsigned long long* __restrict__ begin,
             const BatchItemDev* __restrict__ items) {
     __shared__ unsigned long long s_begin[kMaxItems + 1];
+    __shared__ psf::LaneSums s_stage[kThreads];
+    psf::LaneSums* stage = s_stage + (threadIdx.x & ~31u);
     const unsigned n = h->n;
     if (n == 0) return;
     const unsigned lane = threadIdx.x & 31u;
@@ -142,8 +144,8 @@ __global__ void __launch_bounds__(kThreads)
             v2 = __ldcs(r + 2);
             v3 = __ldcs(r + 3);
         }
-        unsigned len = 0;
-        psf::insert_warp<kMode>(b.t, valid, v0, v1, v2, v3, &len);
+        unsigned len = 0, leaders = 0;
+        psf::insert_warp<kMode>(b.t, valid, v0, v1, v2, v3, &len, stage, &leaders);
         if (len > 16u) atomicMax(&b.t.hdr->max_probe, len);  // only long probes are recorded here
     }
     if (!grid_barrier(ctl, h, items)) return;
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(kThreads)
         const unsigned it = find_item(s_begin, n, u);
         const BatchItemDev& b = items[it];
         const unsigned long long p = (u - s_begin[it]) * 32ull + lane;
-        if (p < b.P) psf::query_path(b.t, b.v, b.P, b.D, p, b.out);
+        if (p < b.P) psf::query_path(b.t, psf::cv_estimator(b.t), b.v, b.P, b.D, p, b.out);
     }
 }
 

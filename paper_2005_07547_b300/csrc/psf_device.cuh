@@ -34,9 +34,10 @@ struct DevHeader {
     unsigned long long zero_weight;
     unsigned long long iterations;
     unsigned long long touched;  // cells blended by all updates so far
+    unsigned long long leaders;  // (warp, key) groups scattered by all inserts so far
     unsigned int barrier_count;  // grid barrier of the batched kernel
     unsigned int barrier_gen;
-    unsigned int pad[52];
+    unsigned int pad[50];
 };
 static_assert(sizeof(DevHeader) == 256, "header is one 256-byte block");
 
@@ -207,6 +208,8 @@ __device__ __forceinline__ long long probe_find(const TableView& t, unsigned lon
 }
 
 // Leader of a group of lanes holding the same key: probe once, add the group's sums.
+// Every atomic is a reduction whose result is not read (fire and forget); the touched
+// bit is set unconditionally, so no warp waits on an atomic round trip.
 __device__ __forceinline__ void scatter_group(const TableView& t, unsigned long long key, unsigned members,
                                               const long long sums[4], unsigned* max_len) {
     unsigned len = 0;
@@ -221,25 +224,25 @@ __device__ __forceinline__ void scatter_group(const TableView& t, unsigned long 
     atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[0]), static_cast<unsigned long long>(sums[0]));
     atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[1]), static_cast<unsigned long long>(sums[1]));
     atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[2]), static_cast<unsigned long long>(sums[2]));
-    const unsigned long long old =
-        atomicAdd(reinterpret_cast<unsigned long long*>(&a->c), static_cast<unsigned long long>(sums[3]));
-    if (old == 0ull)  // first touch this iteration (every accepted vertex adds weight >= 1)
-        atomicOr(t.dirty + (slot >> 5), 1u << (slot & 31));
+    atomicAdd(reinterpret_cast<unsigned long long*>(&a->c), static_cast<unsigned long long>(sums[3]));
+    atomicOr(t.dirty + (slot >> 5), 1u << (slot & 31));
 }
 
-__device__ __forceinline__ long long shfl64(long long v, int src) {
-    return static_cast<long long>(__shfl_sync(kFull, static_cast<unsigned long long>(v), src));
-}
+// Per-warp staging of the lanes' sums for the donor merge (32 B per lane).
+struct alignas(16) LaneSums {
+    long long v[4];
+};
 
 // One warp's worth of vertices (one per lane, `valid` lanes only): classify, then add each
 // accepted vertex to its cell.  With kAggWarp, lanes holding the same key are found with
-// match_any; the lowest lane of each group (its leader) collects the others' sums through
-// a warp-uniform shuffle loop that visits only the donor lanes, then probes once and adds.
-// A warp whose keys are all distinct (the common case after the first bounce) skips the
-// loop.  Integer sums are exact, so every mode gives bit-identical tables.
+// match_any; a group's lowest lane (its leader) adds the other members' sums, read from
+// the warp's shared-memory staging area, then probes once and adds.  A warp whose keys
+// are all distinct (the common case after the first bounce) skips the merge.  Integer
+// sums are exact, so every mode gives bit-identical tables.
 template <int kMode>
 __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, const float4& v0, const float4& v1,
-                                            const float4& v2, const float4& v3, unsigned* max_len) {
+                                            const float4& v2, const float4& v3, unsigned* max_len,
+                                            LaneSums* stage, unsigned* leaders) {
     const unsigned lane = threadIdx.x & 31u;
     unsigned long long key = 0;
     long long sums[4] = {0, 0, 0, 0};
@@ -262,29 +265,30 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
     }
     if (kMode == kAggNone) {
         if (cls == 1) scatter_group(t, key, 1u << lane, sums, max_len);
+        *leaders += __popc(accepted);
         return;
     }
     unsigned group = 0;
     if (cls == 1) group = __match_any_sync(accepted, key);
     const bool donor = cls == 1 && (group & ((1u << lane) - 1u)) != 0u;
-    unsigned donors = __ballot_sync(kFull, donor);
-    if (donors) {
-        const int my_leader = cls == 1 ? __ffs(group) - 1 : 0;
-        while (donors) {  // the same iterations in every lane
-            const int src = __ffs(donors) - 1;
-            donors &= donors - 1u;
-            const int dst = __shfl_sync(kFull, my_leader, src);
-            const long long a0 = shfl64(sums[0], src), a1 = shfl64(sums[1], src);
-            const long long a2 = shfl64(sums[2], src), a3 = shfl64(sums[3], src);
-            if (static_cast<int>(lane) == dst) {
-                sums[0] += a0;
-                sums[1] += a1;
-                sums[2] += a2;
-                sums[3] += a3;
+    if (__any_sync(kFull, donor)) {
+        if (donor) stage[lane] = LaneSums{{sums[0], sums[1], sums[2], sums[3]}};
+        __syncwarp();
+        if (cls == 1 && !donor) {
+            unsigned rest = group & ~(1u << lane);
+            while (rest) {
+                const LaneSums m = stage[__ffs(rest) - 1];
+                rest &= rest - 1u;
+                sums[0] += m.v[0];
+                sums[1] += m.v[1];
+                sums[2] += m.v[2];
+                sums[3] += m.v[3];
             }
         }
+        __syncwarp();
     }
     if (cls == 1 && !donor) scatter_group(t, key, group, sums, max_len);
+    *leaders += __popc(__ballot_sync(kFull, cls == 1 && !donor));
 }
 
 // ---------------------------------------------------------------------------
@@ -405,66 +409,80 @@ __device__ __forceinline__ unsigned update_words(const TableView& t, unsigned lo
 // ---------------------------------------------------------------------------
 // Control-variate query: Section "Control variates", equation CVEstimator.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float3 cell_value(const TableView& t, const float4& v0, const float4& v1,
-                                             const float4& v2) {
-    float3 c = make_float3(0.0f, 0.0f, 0.0f);
-    unsigned long long key;
-    if (!cell_key(t, v0, v1, v2, &key)) return c;
-    const long long s = probe_find(t, key);
-    if (s < 0) return c;
-    if (t.mirror) {
+__device__ __forceinline__ float3 value_at(const TableView& t, unsigned long long s, bool fp32_master = false) {
+    if (t.mirror && !fp32_master) {
         const uint2 h = __ldcg(t.mirror + s);
-        c.x = __half2float(__ushort_as_half(static_cast<unsigned short>(h.x & 0xffffu)));
-        c.y = __half2float(__ushort_as_half(static_cast<unsigned short>(h.x >> 16)));
-        c.z = __half2float(__ushort_as_half(static_cast<unsigned short>(h.y & 0xffffu)));
-    } else {
-        const float4 L = __ldcg(&t.slots[s].L);
-        c = make_float3(L.x, L.y, L.z);
+        return make_float3(__half2float(__ushort_as_half(static_cast<unsigned short>(h.x & 0xffffu))),
+                           __half2float(__ushort_as_half(static_cast<unsigned short>(h.x >> 16))),
+                           __half2float(__ushort_as_half(static_cast<unsigned short>(h.y & 0xffffu))));
     }
-    return c;
+    const float4 L = __ldcg(&t.slots[s].L);
+    return make_float3(L.x, L.y, L.z);
 }
 
-// out_j = L_j - beta * t_j * C_{j+1} + beta * C_j  (or L_j without a control variate)
-__device__ __forceinline__ float cv_combine(float L, float tj, float c_next, float c_self, float beta) {
+// The approximant of the vertex's cell, 0 if the cell is absent.  The value at the home
+// slot is loaded together with its key, so the common case (key found at its home slot)
+// costs one round trip instead of two.
+__device__ __forceinline__ float3 cell_value(const TableView& t, const float4& v0, const float4& v1,
+                                             const float4& v2, bool fp32_master = false) {
+    const float3 zero = make_float3(0.0f, 0.0f, 0.0f);
+    unsigned long long key;
+    if (!cell_key(t, v0, v1, v2, &key)) return zero;
+    const unsigned long long mask = (1ull << t.log2cap) - 1ull;
+    unsigned long long s = home_slot(t, key);
+    const unsigned long long k0 = __ldcg(t.keys + s);
+    const float3 c0 = value_at(t, s, fp32_master);
+    if (k0 == key) return c0;
+    if (k0 == kEmpty) return zero;
+    for (unsigned i = 1; i < t.max_probe; ++i) {
+        s = (s + 1) & mask;
+        const unsigned long long k = __ldcg(t.keys + s);
+        if (k == key) return value_at(t, s, fp32_master);
+        if (k == kEmpty) return zero;
+    }
+    return zero;
+}
+
+// The estimators that use the approximant are affine in (L_j, t_j C_{j+1}, C_j):
+//   control variate (Section "Control variates", CVEstimator):  a = 1, b = c = beta
+//   biased predictor-corrector (Section "Biased estimation"):    a = b = gamma, c = 1
+// applied to vertices j_begin <= j < j_end that have a successor; other vertices keep L_j.
+struct Estimator {
+    float a, b, c;
+    unsigned j_begin, j_end;
+};
+
+__host__ __device__ __forceinline__ Estimator cv_estimator(const TableView& t) {
+    return Estimator{1.0f, t.beta, t.beta, 0u, t.cv_max_depth};
+}
+
+// out_j = a L_j - b (t_j C_{j+1}) + c C_j
+__device__ __forceinline__ float combine(const Estimator& e, float L, float tj, float c_next, float c_self) {
     const float h = __fmul_rn(tj, c_next);
-    return __fadd_rn(__fsub_rn(L, __fmul_rn(beta, h)), __fmul_rn(beta, c_self));
+    return __fadd_rn(__fsub_rn(__fmul_rn(e.a, L), __fmul_rn(e.b, h)), __fmul_rn(e.c, c_self));
 }
 
 // All vertices of path p (depth-major records j*P + p), last to first so that each vertex
-// is probed once: its cell value serves as C_j here and as C_{j+1} for vertex j - 1.  The
-// record of vertex j - 1 is loaded before vertex j is probed, so the two latencies overlap.
-__device__ __forceinline__ void query_path(const TableView& t, const float4* __restrict__ v, unsigned P, unsigned D,
-                                           unsigned long long p, float* __restrict__ out) {
+// is probed once: its cell value serves as C_j here and as C_{j+1} for vertex j - 1.
+__device__ __forceinline__ void query_path(const TableView& t, const Estimator& e, const float4* __restrict__ v,
+                                           unsigned P, unsigned D, unsigned long long p, float* __restrict__ out) {
     float3 c_next = make_float3(0.0f, 0.0f, 0.0f);
-    int j = static_cast<int>(D) - 1;
-    const float4* r = v + 4 * (static_cast<unsigned long long>(j) * P + p);  // streamed once: evict-first
-    float4 v0 = __ldcs(r), v1 = __ldcs(r + 1), v2 = __ldcs(r + 2), v3 = __ldcs(r + 3);
-    for (; j >= 0; --j) {
-        float4 n0 = v0, n1 = v1, n2 = v2, n3 = v3;
-        if (j > 0) {
-            const float4* rn = v + 4 * (static_cast<unsigned long long>(j - 1) * P + p);
-            n0 = __ldcs(rn);
-            n1 = __ldcs(rn + 1);
-            n2 = __ldcs(rn + 2);
-            n3 = __ldcs(rn + 3);
-        }
+    for (int j = static_cast<int>(D) - 1; j >= 0; --j) {
         const unsigned long long i = static_cast<unsigned long long>(j) * P + p;
+        const float4* r = v + 4 * i;  // streamed once: evict-first
+        const float4 v0 = __ldcs(r), v1 = __ldcs(r + 1), v2 = __ldcs(r + 2), v3 = __ldcs(r + 3);
         const float3 c = cell_value(t, v0, v1, v2);
         float o0 = v3.x, o1 = v3.y, o2 = v3.z;
-        if (j + 1 < static_cast<int>(D) && static_cast<unsigned>(j) < t.cv_max_depth) {
-            o0 = cv_combine(v3.x, v1.w, c_next.x, c.x, t.beta);
-            o1 = cv_combine(v3.y, v2.w, c_next.y, c.y, t.beta);
-            o2 = cv_combine(v3.z, v3.w, c_next.z, c.z, t.beta);
+        if (j + 1 < static_cast<int>(D) && static_cast<unsigned>(j) >= e.j_begin && static_cast<unsigned>(j) < e.j_end) {
+            o0 = combine(e, v3.x, v1.w, c_next.x, c.x);
+            o1 = combine(e, v3.y, v2.w, c_next.y, c.y);
+            o2 = combine(e, v3.z, v3.w, c_next.z, c.z);
         }
         float* o = out + 3 * i;
         o[0] = o0;
         o[1] = o1;
         o[2] = o2;
         c_next = c;
-        v0 = n0;
-        v1 = n1;
-        v2 = n2;
-        v3 = n3;
     }
 }
 

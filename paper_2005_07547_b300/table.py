@@ -56,6 +56,15 @@ class Table:
         _abi.check(_abi.load().psf_insert(self._h, verts.data_ptr(), verts.shape[0], _stream_handle(stream)),
                    "psf_insert")
 
+    def insert_progressive(self, verts, P: int, D: int, field: int = 0, stream=None) -> None:
+        """Scatter values computed from the approximant at each next vertex (eq. 9; field 0:
+        L~_o as in Alg. 1, field 1: L~_{o\\e} as in Alg. 2)."""
+        _check_vertices(verts, "insert_progressive")
+        if verts.shape[0] != P * D:
+            raise ValueError("insert_progressive: vertex count must be P*D")
+        _abi.check(_abi.load().psf_insert_progressive(self._h, verts.data_ptr(), P, D, field, _stream_handle(stream)),
+                   "psf_insert_progressive")
+
     def update(self, stream=None) -> int:
         return _abi.check(_abi.load().psf_update(self._h, _stream_handle(stream)), "psf_update")
 
@@ -69,6 +78,20 @@ class Table:
             out = torch.empty((P * D, 3), dtype=torch.float32, device=verts.device)
         _abi.check(_abi.load().psf_query_cv(self._h, verts.data_ptr(), P, D, out.data_ptr(),
                                             _stream_handle(stream)), "psf_query_cv")
+        return out
+
+    def query_biased(self, verts, P: int, D: int, gamma: float, j_begin: int = 0, j_end: int = 0xFFFFFFFF, out=None,
+                     stream=None):
+        """gamma * (L - t * C_next) + C on vertices j_begin <= j < j_end (PSTF-B: gamma 0, j 1..2)."""
+        import torch
+
+        _check_vertices(verts, "query_biased")
+        if verts.shape[0] != P * D:
+            raise ValueError("query_biased: vertex count must be P*D")
+        if out is None:
+            out = torch.empty((P * D, 3), dtype=torch.float32, device=verts.device)
+        _abi.check(_abi.load().psf_query_biased(self._h, verts.data_ptr(), P, D, gamma, j_begin, j_end, out.data_ptr(),
+                                                _stream_handle(stream)), "psf_query_biased")
         return out
 
     def step(self, verts, P: int, D: int, out=None, stream=None):

@@ -4,9 +4,10 @@ Bars:
   * keys, fixed-point sums, c_new and c_old: bit-exact (integer work);
   * approximant L~ (FP32 blend): |x - ref| <= 1e-5 * max(|ref|, 2^-14 * max|ref|);
   * FP16 copy of L~: the same with 2e-3 (binary16 has an 11-bit significand);
-  * CV output (norm-wise, the formula can cancel):
-      |out - ref| <= tol * (|L| + beta |t| |C_next| + beta |C| + beta (1 + |t|) * floor)
-    with floor = 2^-14 * max|ref L~| and tol = 1e-5 (FP32 cache) or 2e-3 (FP16 cache).
+  * estimator outputs out = a L - b t C_next + c C (norm-wise, the formula can cancel):
+      |out - ref| <= tol * (|a||L| + |b||t|(|C_next| + floor) + |c|(|C| + floor))
+    with floor = 2^-14 * max|ref L~| and tol = 1e-5 (FP32 cache) or 2e-3 (FP16 cache);
+    the control variate is a = 1, b = c = beta, the biased estimator a = b = gamma, c = 1.
 The floor covers values below binary16's normal range; for FP32 it is never the
 binding term on these workloads.
 """
@@ -53,8 +54,9 @@ def check_after_update(gpu, ora, fp16=False):
     return rel32, rel16
 
 
-def check_cv(out_gpu, out_ref, verts, C_ref, P, D, beta, cv_max_depth, ref_L_all, fp16=False):
-    """Norm-wise comparison of the control-variate outputs; returns the worst ratio err/bound."""
+def check_estimator(out_gpu, out_ref, verts, C_ref, P, D, a, b, c, j_begin, j_end, ref_L_all, fp16=False):
+    """Norm-wise comparison of out_j = a L_j - b t_j C_{j+1} + c C_j (vertices j_begin <= j < j_end
+    with a successor; others must be L_j exactly).  Returns the worst ratio err / bound."""
     tol = TOL_FP16 if fp16 else TOL_FP32
     out_gpu = np.asarray(out_gpu, dtype=np.float64).reshape(D * P, 3)
     L = verts[:, 12:15].astype(np.float64)
@@ -63,17 +65,22 @@ def check_cv(out_gpu, out_ref, verts, C_ref, P, D, beta, cv_max_depth, ref_L_all
     C_next = np.zeros_like(C)
     C_next[:-1] = C[1:]
     j = np.repeat(np.arange(D), P)
-    has_cv = ((j + 1 < D) & (j < cv_max_depth))[:, None]
+    on = ((j + 1 < D) & (j >= j_begin) & (j < j_end))[:, None]
     fl = _floor(ref_L_all)
-    bound = tol * (np.abs(L) + has_cv * beta * (np.abs(t) * np.abs(C_next.reshape(-1, 3)) + np.abs(C_ref)
-                                               + (1.0 + np.abs(t)) * fl))
+    bound = tol * (np.where(on, abs(a), 1.0) * np.abs(L)
+                   + on * (abs(b) * np.abs(t) * (np.abs(C_next.reshape(-1, 3)) + fl) + abs(c) * (np.abs(C_ref) + fl)))
     # non-finite inputs propagate identically on both sides
     assert np.array_equal(np.isnan(out_gpu), np.isnan(out_ref))
     err = np.abs(out_gpu - out_ref)
     err[np.isnan(out_ref)] = 0.0
     bad = err > bound
     assert not np.any(bad), (np.argwhere(bad)[:5], out_gpu[bad][:5], out_ref[bad][:5])
-    # vertices without a control variate are copied exactly
-    no_cv = ~has_cv[:, 0]
-    assert np.array_equal(out_gpu[no_cv], L[no_cv].astype(np.float32).astype(np.float64), equal_nan=True)
+    # vertices without an estimator are copied exactly
+    off = ~on[:, 0]
+    assert np.array_equal(out_gpu[off], L[off].astype(np.float32).astype(np.float64), equal_nan=True)
     return float(np.max(err / np.maximum(bound, 1e-300))) if err.size else 0.0
+
+
+def check_cv(out_gpu, out_ref, verts, C_ref, P, D, beta, cv_max_depth, ref_L_all, fp16=False):
+    """The control variate: a = 1, b = c = beta on vertices j < cv_max_depth."""
+    return check_estimator(out_gpu, out_ref, verts, C_ref, P, D, 1.0, beta, beta, 0, cv_max_depth, ref_L_all, fp16)

@@ -271,3 +271,65 @@ def test_launch_knobs_do_not_change_results(psf_mod, knobs):
         runs.append((table.export().tobytes(), np.concatenate(outs).tobytes()))
         table.close()
     assert runs[0] == runs[1]
+
+
+@pytest.mark.parametrize("fp16", [False, True])
+@pytest.mark.parametrize("gamma,jb,je", [(0.0, 1, 2), (0.5, 0, 0xFFFFFFFF), (1.0, 0, 0xFFFFFFFF), (0.25, 0, 1)])
+def test_biased_estimator(psf_mod, oracle_mod, fp16, gamma, jb, je):
+    """Section 'Biased estimation': gamma (L - t C_next) + C; gamma = 0 at the second vertex
+    is PSTF-B; gamma = 1 everywhere equals the control variate with beta = 1."""
+    import torch
+
+    from parity import check_estimator
+
+    w, batches = _workload_batches("64x64_d3", 3)
+    cfg = _cfg_for(psf_mod, w, cache_fp16=fp16)
+    P, D = w["width"] * w["height"], w["depth"]
+    table = psf_mod.Table(cfg)
+    ora = _oracle_for(oracle_mod, cfg)
+    for v in batches:
+        dv = torch.from_numpy(v).cuda()
+        table.insert(dv)
+        table.update()
+        ora.insert(v)
+        ora.update()
+        out = table.query_biased(dv, P, D, gamma, jb, je).cpu().numpy()
+        ref = ora.query_biased(v, P, D, gamma, jb, je)
+        check_estimator(out, ref, v, ora.lookup(v), P, D, gamma, gamma, 1.0, jb, je, ora.export()["L"], fp16=fp16)
+        if gamma == 1.0 and jb == 0:
+            assert np.array_equal(out, table.query_cv(dv, P, D).cpu().numpy())
+    table.close()
+
+
+@pytest.mark.parametrize("field", [0, 1])
+@pytest.mark.parametrize("fp16", [False, True])
+def test_progressive_insert(psf_mod, oracle_mod, field, fp16):
+    """eq. (9) update values computed in the library from the approximant at the next vertex.
+    Cells and counters are exact; the value of a vertex depends on the FP32 (GPU) or FP64
+    (oracle) approximant, so the fixed-point sums agree within
+      |sum - ref| <= 1e-5 |ref| + 2 * (vertices in the cell) + 2
+    (relative error of the fed-back approximant well below 1e-5, plus one rounding of each
+    vertex's fixed-point code) and the blended values within the FP32 bound."""
+    import torch
+
+    w, batches = _workload_batches("64x64_d3", 4)
+    cfg = _cfg_for(psf_mod, w, cache_fp16=fp16)
+    P, D = w["width"] * w["height"], w["depth"]
+    table = psf_mod.Table(cfg)
+    ora = _oracle_for(oracle_mod, cfg)
+    for it, v in enumerate(batches):
+        dv = torch.from_numpy(v).cuda()
+        table.insert_progressive(dv, P, D, field)
+        ora.insert_progressive(v, P, D, field)
+        g, r = table.export(), ora.export()
+        assert np.array_equal(g["key"], r["key"]) and np.array_equal(g["c_new"], r["c_new"])
+        assert np.array_equal(g["c_old"], r["c_old"])
+        slack = 1e-5 * np.abs(r["sum"]).astype(np.float64) + 2.0 * (r["c_new"] / 2.0 ** 24)[:, None] + 2.0
+        diff = np.abs(g["sum"].astype(np.float64) - r["sum"].astype(np.float64))
+        assert np.all(diff <= slack), (it, np.max(diff / slack))
+        if it == 0:  # an empty table feeds back zeros: the sums are those of the values alone
+            assert np.max(diff) <= 2.0
+        table.update()
+        ora.update()
+        check_after_update(table.export(), ora.export(), fp16=fp16)
+    table.close()

@@ -112,3 +112,54 @@ def test_cv_depth_limit_absent_cells_and_single_vertex_paths(oracle_mod):
     assert np.array_equal(o0.query_cv(v, 3, 2), v[:, 12:15].astype(np.float64))
     # paths of depth 1 have no successor
     assert np.array_equal(o.query_cv(v[:3], 3, 1), v[:3, 12:15].astype(np.float64))
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.5, 1.0])
+def test_biased_estimator_mean_matches_closed_form(oracle_mod, gamma):
+    """BiasedEstimator: mean(gamma (L - t C_next) + C) = gamma mean(L) + (1 - gamma) I_h,
+    with I_h = 2 pi / 33 from the cos^32 quadrature."""
+    mu, wq = _nodes()
+    o = _filled_oracle(oracle_mod, 1.0)
+    rng = np.random.default_rng(6)
+    t0 = np.outer(2.0 * math.pi * wq * K, np.ones(3))
+    L0 = rng.lognormal(0.0, 1.0, size=(K, 3))
+    v = _paths(list(range(K)), L0, t0)
+    out = o.query_biased(v, K, 2, gamma, 0, 1)
+    plain = v[:K, 12:15].astype(np.float64)
+    want = gamma * plain.mean(axis=0) + (1.0 - gamma) * I_H * SCALE
+    assert np.all(np.abs(out[:K].mean(axis=0) - want) < 1e-6)
+    assert np.array_equal(out[K:], v[K:, 12:15].astype(np.float64))
+
+
+def test_biased_estimator_gamma_zero_returns_the_approximant(oracle_mod):
+    o = _filled_oracle(oracle_mod, 1.0)
+    v = _paths([0, 3, 5], np.full((3, 3), 7.0), np.full((3, 3), 2.0))
+    out = o.query_biased(v, 3, 2, 0.0, 0, 1)
+    np.testing.assert_array_equal(out[:3], o.lookup(v)[:3])
+    # outside [j_begin, j_end) the plain estimate passes through
+    assert np.array_equal(o.query_biased(v, 3, 2, 0.0, 1, 2), v[:, 12:15].astype(np.float64))
+    # gamma = 1 is the control-variate estimator with beta = 1
+    np.testing.assert_allclose(o.query_biased(v, 3, 2, 1.0), o.query_cv(v, 3, 2), rtol=1e-15)
+
+
+def test_biased_estimator_vertex_range_on_three_vertex_paths(oracle_mod):
+    """Only vertices j_begin <= j < j_end (with a successor) get the estimator."""
+    o = _filled_oracle(oracle_mod, 1.0)
+    P, D = 4, 3
+    v = np.empty((P * D, 16), dtype=np.float32)
+    for p in range(P):
+        v[p] = vertex(SELF_POS, L=(1.0, 2.0, 3.0), t=(0.5, 0.5, 0.5))
+        v[P + p] = vertex(_next_pos(p), L=(4.0, 5.0, 6.0), t=(0.25, 0.25, 0.25))
+        v[2 * P + p] = vertex(_next_pos(p + 5), L=(7.0, 8.0, 9.0), t=(0.1, 0.1, 0.1))
+    C = o.lookup(v)
+    L = v[:, 12:15].astype(np.float64)
+    t = v[:, [7, 11, 15]].astype(np.float64)
+    for jb, je in [(0, 1), (1, 2), (0, 2), (1, 1), (0, 3)]:
+        out = o.query_biased(v, P, D, 0.25, jb, je)
+        for j in range(D):
+            rows = slice(j * P, (j + 1) * P)
+            if jb <= j < je and j + 1 < D:
+                want = 0.25 * (L[rows] - t[rows] * C[(j + 1) * P:(j + 2) * P]) + C[rows]
+                np.testing.assert_allclose(out[rows], want, rtol=1e-15)
+            else:
+                assert np.array_equal(out[rows], L[rows]), (jb, je, j)

@@ -1,0 +1,71 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case plants one mistake (a flipped sign, a swapped index, a dropped term, a
+transposed operand, a wrong rounding or comparison) in a copy of the oracle source,
+compiles it, and runs the pin suite against the broken build in a fresh process: the
+suite must fail.  The planted mistakes live only in temporary copies, on the CPU."""
+
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "psf_oracle.cpp")
+PINS = ["tests/test_oracle_keys.py", "tests/test_oracle_accumulate.py", "tests/test_oracle_cv.py"]
+
+MUTANTS = {
+    "cv_sign_of_control": ("L - c.beta * (t[ch] * C_next[ch]) + c.beta * C[ch]",
+                           "L + c.beta * (t[ch] * C_next[ch]) + c.beta * C[ch]"),
+    "cv_swapped_vertices": ("L - c.beta * (t[ch] * C_next[ch]) + c.beta * C[ch]",
+                            "L - c.beta * (t[ch] * C[ch]) + c.beta * C_next[ch]"),
+    "cv_dropped_integral": ("L - c.beta * (t[ch] * C_next[ch]) + c.beta * C[ch]",
+                            "L - c.beta * (t[ch] * C_next[ch])"),
+    "cv_last_vertex": ("const bool cv = (j + 1 < static_cast<int64_t>(D))", "const bool cv = (j < static_cast<int64_t>(D))"),
+    "biased_range_inclusive": ("(static_cast<uint64_t>(j) < j_end)", "(static_cast<uint64_t>(j) <= j_end)"),
+    "alpha_transposed": ("std::sqrt(cn / (co + cn))", "std::sqrt(co / (co + cn))"),
+    "alpha_no_sqrt": ("std::sqrt(cn / (co + cn))", "(cn / (co + cn))"),
+    "alpha_min_not_max": ("std::max(std::sqrt(cn / (co + cn)), c.alpha_min)",
+                          "std::min(std::sqrt(cn / (co + cn)), c.alpha_min)"),
+    "blend_weights_swapped": ("(1.0 - alpha) * cell.L[ch] + alpha * mean", "alpha * cell.L[ch] + (1.0 - alpha) * mean"),
+    "c_old_not_cumulative": ("cell.c_old = sat_add(cell.c_old, cell.c_new);", "cell.c_old = cell.c_new;"),
+    "untouched_cells_blended": ("if (cell.c_new == 0) continue;", "if (cell.c_new < 0) continue;"),
+    "octahedral_fold_swapped": ("float fu = 1.0f - std::fabs(v);", "float fu = 1.0f - std::fabs(u);"),
+    "no_lower_hemisphere_fold": ("if (wz < 0.0f) {", "if (wz < -2.0f) {"),
+    "direction_not_reversed": ("direction_bins(-d[0], -d[1], -d[2]", "direction_bins(d[0], d[1], d[2]"),
+    "cell_index_truncates": ("std::floor(static_cast<double>(p) *", "std::trunc(static_cast<double>(p) *"),
+    "normal_tie_break": ("if (ax >= ay && ax >= az)", "if (ax > ay && ax >= az)"),
+    "fixed_point_truncates": ("std::llrint(static_cast<double>(prod[ch]) * scale)",
+                              "static_cast<int64_t>(static_cast<double>(prod[ch]) * scale)"),
+    "range_bound_exclusive": ("std::fabs(prod[ch]) <= 32768.0f", "std::fabs(prod[ch]) < 32768.0f"),
+    "packed_axes_swapped": ("(bx << 32) | (by << 16) | bz", "(bz << 32) | (by << 16) | bx"),
+    "biased_gamma_on_approximant": ("gamma * (L - t[ch] * C_next[ch]) + C[ch]", "(L - t[ch] * C_next[ch]) + gamma * C[ch]"),
+    "biased_corrector_sign": ("gamma * (L - t[ch] * C_next[ch]) + C[ch]", "gamma * (L + t[ch] * C_next[ch]) + C[ch]"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    mutant = tmp_path / "mutant.cpp"
+    mutant.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", str(mutant), "-o", str(so)],
+                   check=True)
+    env = dict(os.environ, PSF_ORACLE_LIB=str(so))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS], cwd=ROOT,
+                         env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode != 0, f"the pins did not catch the planted mistake '{name}'"
+
+
+def test_unmodified_copy_passes(tmp_path):
+    """Control: the same mechanism with no mistake planted passes the pins."""
+    so = tmp_path / "libcopy.so"
+    subprocess.run(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", SRC, "-o", str(so)], check=True)
+    env = dict(os.environ, PSF_ORACLE_LIB=str(so))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS], cwd=ROOT,
+                         env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stdout[-2000:]
