@@ -327,7 +327,7 @@ def test_progressive_insert(psf_mod, oracle_mod, field, fp16):
         slack = 1e-5 * np.abs(r["sum"]).astype(np.float64) + 2.0 * (r["c_new"] / 2.0 ** 24)[:, None] + 2.0
         diff = np.abs(g["sum"].astype(np.float64) - r["sum"].astype(np.float64))
         assert np.all(diff <= slack), (it, np.max(diff / slack))
-        if it == 0:  # an empty table feeds back zeros: the sums are those of the values alone
+        if it == 0 and field == 0:  # empty table: the Alg. 1 value is exactly L_e, so the sums agree
             assert np.max(diff) <= 2.0
         table.update()
         ora.update()
