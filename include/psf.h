@@ -63,6 +63,7 @@ extern "C" {
 #define PSF_ERR_INVALID_ARG (-1) /* bad pointer, size, alignment or configuration */
 #define PSF_ERR_NO_MEM (-2)      /* table memory or host buffer too small */
 #define PSF_ERR_CUDA (-3)        /* a CUDA runtime call failed; see psf_last_cuda_error */
+#define PSF_ERR_TOO_MANY (-4)    /* more items than psf_batch_step_noalloc's fixed array holds */
 
 #define PSF_STATUS_TABLE_FULL 1u /* a key found no slot within the probe bound; its vertices were dropped */
 #define PSF_STATUS_RANGE 2u      /* at least one vertex failed the range rule */
@@ -253,6 +254,28 @@ int psf_batch_status(psf_batch* b, uint32_t* status, void* stream);
 
 /* Release the batch (its work must have completed).  NULL is a no-op. */
 int psf_batch_destroy(psf_batch* b);
+
+/* The batched fused iteration without any allocation.  (The paper has no counterpart:
+ * this serves callers that cannot allocate device memory on the path that drives the
+ * filter -- an application that reserved all device memory in its own pool up front, or
+ * a per-frame loop that must not call cudaMalloc/cudaFree because they can synchronize
+ * the whole device.)  Same items, results and bounded barrier as psf_batch_step, but the
+ * descriptors and barrier words live in a fixed device array inside the library
+ * (PSF_NOALLOC_MAX_ITEMS items, about 16 KB), which every GPU that loads the library
+ * holds until the process exits; nothing is allocated or freed.  The caller still passes
+ * the tables (their memory is the caller's), vertices and outputs.
+ *   - n > PSF_NOALLOC_MAX_ITEMS returns PSF_ERR_TOO_MANY (with a message in
+ *     psf_last_cuda_error) and enqueues nothing; n = 0 is a no-op.
+ *   - The first call on a device resolves the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the one array: the barrier words and the status are
+ *     cleared at the start of each call, the descriptors overwritten.  Calls whose work
+ *     could overlap on the GPU (different streams without ordering between them) race on
+ *     it; order them on one stream or with events.
+ *   - A barrier that gives up sets PSF_STATUS_TIMEOUT in every item's table. */
+#define PSF_NOALLOC_MAX_ITEMS 64u
+int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, const psf_batch_config* cfg, void* stream);
 
 /* Text of the last CUDA error seen by this thread's calls (empty if none). */
 const char* psf_last_cuda_error(void);

@@ -18,6 +18,8 @@ PSF_OK = 0
 PSF_ERR_INVALID_ARG = -1
 PSF_ERR_NO_MEM = -2
 PSF_ERR_CUDA = -3
+PSF_ERR_TOO_MANY = -4
+NOALLOC_MAX_ITEMS = 64
 
 STATUS_TABLE_FULL = 1
 STATUS_RANGE = 2
@@ -137,6 +139,7 @@ SIGNATURES = {
     "psf_batch_step": (_i, [_vp, ctypes.POINTER(BatchItem), _u32, _vp]),
     "psf_batch_status": (_i, [_vp, ctypes.POINTER(_u32), _vp]),
     "psf_batch_destroy": (_i, [_vp]),
+    "psf_batch_step_noalloc": (_i, [ctypes.POINTER(BatchItem), _u32, ctypes.POINTER(BatchConfig), _vp]),
     "psf_get_launch_config": (_i, [_vp, ctypes.POINTER(LaunchConfig)]),
 }
 

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "psf.h"
@@ -336,3 +337,125 @@ int psf_batch_destroy(psf_batch* b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched step.  Some callers cannot allocate device memory on the
+// path that drives the filter: an application that reserved all device memory in its
+// own pool up front (a cudaMalloc there fails or fragments the pool), or a renderer
+// whose per-frame loop must not call cudaMalloc/cudaFree because they can synchronize
+// the whole device and stall its other streams.  This entry point runs the same fused
+// kernel with its descriptors and barrier words in a fixed array that is part of the
+// library image on every GPU that loads it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr unsigned kNoAllocMaxItems = PSF_NOALLOC_MAX_ITEMS;
+constexpr size_t kNoAllocBytes =
+    sizeof(BatchCtl) + sizeof(BatchHdr) + kBeginBytes + static_cast<size_t>(kNoAllocMaxItems) * sizeof(BatchItemDev);
+constexpr int kNoAllocMaxDevices = 64;
+
+// Shared by every call on a device and kept between calls.  Host code may not use the
+// name as an address: the device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mutex;
+char* g_noalloc_base[kNoAllocMaxDevices];  // device address of g_noalloc_scratch, per device
+int g_noalloc_sms[kNoAllocMaxDevices];
+int g_noalloc_per_sm[kNoAllocMaxDevices][2];
+
+// Once per device, with that device current: resolve the array's device address.
+bool noalloc_setup(int dev) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_base[dev]) return true;
+    void* p = nullptr;
+    int sms = 0, m0 = 0, m1 = 0;
+    if (!psf_cuda_ok(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress") ||
+        !psf_cuda_ok(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attribute") ||
+        !psf_cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m0, k_batch<psf::kAggWarp>, kThreads, 0), "occupancy") ||
+        !psf_cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m1, k_batch<psf::kAggNone>, kThreads, 0), "occupancy"))
+        return false;
+    g_noalloc_sms[dev] = sms;
+    g_noalloc_per_sm[dev][0] = m0;
+    g_noalloc_per_sm[dev][1] = m1;
+    g_noalloc_base[dev] = static_cast<char*>(p);
+    return true;
+}
+
+}  // namespace
+
+extern "C" int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, const psf_batch_config* cfg,
+                                      void* stream) {
+    if (n > kNoAllocMaxItems) {
+        psf_cuda_ok(cudaErrorInvalidValue, "psf_batch_step_noalloc: more items than PSF_NOALLOC_MAX_ITEMS");
+        return PSF_ERR_TOO_MANY;
+    }
+    if (n && !items) return PSF_ERR_INVALID_ARG;
+    const psf_batch_config c = cfg ? *cfg : psf_batch_config{0u, 0u, 0u, 0u};
+    if (c.insert_mode > 1) return PSF_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < n; ++i) {
+        const psf_batch_item& it = items[i];
+        if (!it.table) return PSF_ERR_INVALID_ARG;
+        const unsigned long long nv = static_cast<unsigned long long>(it.P) * it.D;
+        if (nv && (!it.d_vertices || !it.d_out_rgb || (reinterpret_cast<uintptr_t>(it.d_vertices) & 15u) ||
+                   (reinterpret_cast<uintptr_t>(it.d_out_rgb) & 3u)))
+            return PSF_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    if (!psf_cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return PSF_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return PSF_ERR_INVALID_ARG;
+    if (!noalloc_setup(dev)) return PSF_ERR_CUDA;
+    if (n == 0) return PSF_OK;
+
+    // descriptors are built in this thread's static staging area (no heap), then copied
+    alignas(64) thread_local unsigned char stage[kNoAllocBytes];
+    BatchHdr* h = reinterpret_cast<BatchHdr*>(stage + sizeof(BatchCtl));
+    unsigned long long* begin = reinterpret_cast<unsigned long long*>(stage + sizeof(BatchCtl) + sizeof(BatchHdr));
+    BatchItemDev* dev_items = reinterpret_cast<BatchItemDev*>(stage + sizeof(BatchCtl) + sizeof(BatchHdr) + kBeginBytes);
+    std::memset(h, 0, sizeof(BatchHdr));
+    h->n = n;
+    h->phantom = c.test_phantom_blocks;
+    h->timeout_ns = 1000ull * (c.barrier_timeout_us ? c.barrier_timeout_us : 2000000u);
+    unsigned long long acc[3] = {0, 0, 0};
+    for (uint32_t i = 0; i < n; ++i) {
+        const psf_batch_item& it = items[i];
+        BatchItemDev& d = dev_items[i];
+        d.t = it.table->view;
+        d.v = reinterpret_cast<const float4*>(it.d_vertices);
+        d.out = it.d_out_rgb;
+        d.P = it.P;
+        d.D = it.D;
+        d.nverts = static_cast<unsigned long long>(it.P) * it.D;
+        const unsigned long long nwords = ((1ull << it.table->cfg.log2_capacity) + 31ull) >> 5;
+        const unsigned long long units[3] = {(d.nverts + 31) / 32, (nwords + 31) / 32,
+                                             (static_cast<unsigned long long>(it.P) + 31) / 32};
+        for (int ph = 0; ph < 3; ++ph) {
+            begin[ph * (kMaxItems + 1) + i] = acc[ph];
+            acc[ph] += units[ph];
+        }
+    }
+    for (int ph = 0; ph < 3; ++ph) {
+        begin[ph * (kMaxItems + 1) + n] = acc[ph];
+        h->units[ph] = acc[ph];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* base = g_noalloc_base[dev];
+    const size_t len = sizeof(BatchHdr) + kBeginBytes + static_cast<size_t>(n) * sizeof(BatchItemDev);
+    // the barrier words and the status start at zero on every call
+    if (!psf_cuda_ok(cudaMemsetAsync(base, 0, sizeof(BatchCtl), st), "cudaMemsetAsync") ||
+        !psf_cuda_ok(cudaMemcpyAsync(base + sizeof(BatchCtl), stage + sizeof(BatchCtl), len, cudaMemcpyHostToDevice, st),
+                     "cudaMemcpyAsync"))
+        return PSF_ERR_CUDA;
+    const int mode = c.insert_mode == 1 ? 1 : 0;
+    int per_sm = g_noalloc_per_sm[dev][mode];
+    if (c.blocks_per_sm && static_cast<int>(c.blocks_per_sm) < per_sm) per_sm = static_cast<int>(c.blocks_per_sm);
+    if (per_sm < 1) return PSF_ERR_INVALID_ARG;
+    BatchCtl* ctl = reinterpret_cast<BatchCtl*>(base);
+    const BatchHdr* dh = reinterpret_cast<const BatchHdr*>(base + sizeof(BatchCtl));
+    const unsigned long long* dbegin = reinterpret_cast<const unsigned long long*>(base + sizeof(BatchCtl) + sizeof(BatchHdr));
+    const BatchItemDev* ditems = reinterpret_cast<const BatchItemDev*>(base + sizeof(BatchCtl) + sizeof(BatchHdr) + kBeginBytes);
+    void* args[] = {&ctl, &dh, &dbegin, &ditems};
+    const dim3 grid(static_cast<unsigned>(g_noalloc_sms[dev] * per_sm)), block(kThreads);
+    const void* fn = mode == 1 ? reinterpret_cast<const void*>(k_batch<psf::kAggNone>)
+                               : reinterpret_cast<const void*>(k_batch<psf::kAggWarp>);
+    return psf_cuda_ok(cudaLaunchCooperativeKernel(fn, grid, block, args, 0, st), "k_batch") ? PSF_OK : PSF_ERR_CUDA;
+}
