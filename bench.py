@@ -374,7 +374,7 @@ def run_psf(args) -> None:
     cfg = psf.make_config(log2_capacity=w["log2_capacity"], pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],
                           alpha_min=w["alpha_min"], cache_fp16=args.fp16 or w["cache_fp16"])
     table = psf.Table(cfg)
-    table.set_launch(insert_mode=args.insert_mode)
+    table.set_launch(insert_mode=args.insert_mode, vertex_staging=args.staging)
     dev = [torch.from_numpy(v).cuda() for v in host]
     out = torch.empty((V, 3), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -479,7 +479,7 @@ def run_psf(args) -> None:
                    "touched_cells_per_step": touched, "live_cells": after["live_cells"],
                    "l2": f"inputs larger than L2: {n_iter} distinct {V * 64 / 1e6:.0f} MB vertex batches, "
                          "a different one every step",
-                   "insert_mode": args.insert_mode,
+                   "insert_mode": args.insert_mode, "vertex_staging": args.staging,
                    "parallelism": f"sessions x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "mean": float(np.mean(step_ms))},
@@ -767,6 +767,7 @@ def main(argv=None) -> None:
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--insert-mode", type=int, default=0, help="0: warp aggregation of equal keys; 1: none")
+    ap.add_argument("--staging", type=int, default=0, help="1: stage vertex records through shared memory (TMA)")
     ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
     ap.add_argument("--pool", type=int, default=4, help="distinct resident iterations per session (batched)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")

@@ -84,6 +84,7 @@ class LaunchConfig(ctypes.Structure):
         ("insert_blocks_per_sm", ctypes.c_uint32),
         ("update_blocks_per_sm", ctypes.c_uint32),
         ("query_blocks_per_sm", ctypes.c_uint32),
+        ("vertex_staging", ctypes.c_uint32),
     ]
 
 

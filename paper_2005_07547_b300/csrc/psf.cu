@@ -196,6 +196,137 @@ __global__ void __launch_bounds__(kThreads) k_insert_progressive(TableView t, co
     }
 }
 
+// k_insert with the vertex records staged through shared memory: thread 0 copies the
+// next 16 KB tile (256 records) with cp.async.bulk while the block works on the current
+// one; each thread reads its record from shared memory without bank conflicts.
+template <int kMode>
+__global__ void __launch_bounds__(kThreads) k_insert_staged(TableView t, const float4* __restrict__ v, unsigned long long n) {
+    __shared__ alignas(128) float4 s_tile[2][psf::kTileVerts * 4];
+    __shared__ alignas(8) unsigned long long s_bar[2];
+    __shared__ int s_ok;
+    __shared__ unsigned s_max_probe;
+    __shared__ unsigned long long s_leaders;
+    __shared__ psf::LaneSums s_stage[kThreads];
+    const unsigned long long ntiles = (n + psf::kTileVerts - 1) / psf::kTileVerts;
+    if (threadIdx.x == 0) {
+        psf::mbar_init(&s_bar[0]);
+        psf::mbar_init(&s_bar[1]);
+        psf::mbar_init_fence();
+        s_ok = 1;
+        s_max_probe = 0;
+        s_leaders = 0;
+    }
+    __syncthreads();
+    auto issue = [&](unsigned long long tile, unsigned buf) {
+        const unsigned long long first = tile * psf::kTileVerts;
+        const unsigned long long cnt = n - first < psf::kTileVerts ? n - first : psf::kTileVerts;
+        psf::bulk_load(s_tile[buf], v + 4 * first, static_cast<unsigned>(cnt * 64), &s_bar[buf]);
+    };
+    psf::LaneSums* stage = s_stage + (threadIdx.x & ~31u);
+    unsigned max_len = 0, leaders = 0;
+    unsigned long long tile = blockIdx.x;
+    if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
+    bool pending_other = false;  // a copy into the other buffer is in flight
+    unsigned k = 0;
+    for (; tile < ntiles; tile += gridDim.x, ++k) {
+        const unsigned buf = k & 1u;
+        if (threadIdx.x == 0) {
+            const unsigned long long next = tile + gridDim.x;
+            pending_other = next < ntiles;
+            if (pending_other) issue(next, buf ^ 1u);
+            s_ok = psf::mbar_wait(&s_bar[buf], (k >> 1) & 1u);
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const unsigned long long i = tile * psf::kTileVerts + threadIdx.x;
+        const bool valid = i < n;
+        float4 v0 = make_float4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
+        if (valid) psf::read_staged(s_tile[buf], threadIdx.x, v0, v1, v2, v3);
+        psf::insert_warp<kMode>(t, valid, v0, v1, v2, v3, &max_len, stage, &leaders);
+        __syncthreads();  // the tile is consumed before its buffer is refilled
+    }
+    if (!s_ok && threadIdx.x == 0) {
+        atomicOr(&t.hdr->status, psf::kStatusTimeout);
+        // let a copy still in flight land before the block leaves (bounded)
+        if (pending_other) psf::mbar_wait(&s_bar[(k & 1u) ^ 1u], ((k + 1) >> 1) & 1u);
+    }
+    if (max_len) atomicMax(&s_max_probe, max_len);
+    if ((threadIdx.x & 31u) == 0 && leaders) atomicAdd(&s_leaders, static_cast<unsigned long long>(leaders));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_max_probe) atomicMax(&t.hdr->max_probe, s_max_probe);
+        if (s_leaders) atomicAdd(&t.hdr->leaders, s_leaders);
+    }
+}
+
+// k_query with the vertex records staged through shared memory.  A block owns 256
+// consecutive paths; it walks their depths from last to first, each depth being one
+// contiguous 16 KB tile, while the next (block, depth) tile is copied in.
+__global__ void __launch_bounds__(kThreads) k_query_staged(TableView t, psf::Estimator e, const float4* __restrict__ v,
+                                                           unsigned P, unsigned D, float* __restrict__ out) {
+    __shared__ alignas(128) float4 s_tile[2][psf::kTileVerts * 4];
+    __shared__ alignas(8) unsigned long long s_bar[2];
+    __shared__ int s_ok;
+    const unsigned long long nblk = (static_cast<unsigned long long>(P) + psf::kTileVerts - 1) / psf::kTileVerts;
+    if (threadIdx.x == 0) {
+        psf::mbar_init(&s_bar[0]);
+        psf::mbar_init(&s_bar[1]);
+        psf::mbar_init_fence();
+        s_ok = 1;
+    }
+    __syncthreads();
+    auto issue = [&](unsigned long long b, unsigned j, unsigned buf) {
+        const unsigned long long first = b * psf::kTileVerts;
+        const unsigned long long cnt = P - first < psf::kTileVerts ? P - first : psf::kTileVerts;
+        psf::bulk_load(s_tile[buf], v + 4 * (static_cast<unsigned long long>(j) * P + first), static_cast<unsigned>(cnt * 64),
+                       &s_bar[buf]);
+    };
+    unsigned long long b = blockIdx.x;
+    unsigned j = D - 1;
+    if (threadIdx.x == 0 && b < nblk) issue(b, j, 0);
+    bool pending_other = false;
+    unsigned k = 0;
+    float3 c_next = make_float3(0.0f, 0.0f, 0.0f);
+    while (b < nblk) {
+        const unsigned buf = k & 1u;
+        const unsigned long long nb = j > 0 ? b : b + gridDim.x;
+        const unsigned nj = j > 0 ? j - 1 : D - 1;
+        if (threadIdx.x == 0) {
+            pending_other = nb < nblk;
+            if (pending_other) issue(nb, nj, buf ^ 1u);
+            s_ok = psf::mbar_wait(&s_bar[buf], (k >> 1) & 1u);
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        if (j == D - 1) c_next = make_float3(0.0f, 0.0f, 0.0f);
+        const unsigned long long p = b * psf::kTileVerts + threadIdx.x;
+        if (p < P) {
+            float4 v0, v1, v2, v3;
+            psf::read_staged(s_tile[buf], threadIdx.x, v0, v1, v2, v3);
+            const float3 c = psf::cell_value(t, v0, v1, v2);
+            float o0 = v3.x, o1 = v3.y, o2 = v3.z;
+            if (j + 1 < D && j >= e.j_begin && j < e.j_end) {
+                o0 = psf::combine(e, v3.x, v1.w, c_next.x, c.x);
+                o1 = psf::combine(e, v3.y, v2.w, c_next.y, c.y);
+                o2 = psf::combine(e, v3.z, v3.w, c_next.z, c.z);
+            }
+            float* o = out + 3 * (static_cast<unsigned long long>(j) * P + p);
+            o[0] = o0;
+            o[1] = o1;
+            o[2] = o2;
+            c_next = c;
+        }
+        __syncthreads();  // the tile is consumed before its buffer is refilled
+        b = nb;
+        j = nj;
+        ++k;
+    }
+    if (!s_ok && threadIdx.x == 0) {
+        atomicOr(&t.hdr->status, psf::kStatusTimeout);
+        if (pending_other) psf::mbar_wait(&s_bar[(k & 1u) ^ 1u], ((k + 1) >> 1) & 1u);
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_update(TableView t) {
     __shared__ unsigned long long s_touched;
     if (threadIdx.x == 0) s_touched = 0;
@@ -319,13 +450,18 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
                  "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->update_blocks_per_sm, k_update, kThreads, 0), "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->query_blocks_per_sm, k_query, kThreads, 0), "occupancy") ||
+        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->staged_blocks_per_sm, k_insert_staged<psf::kAggWarp>,
+                                                               kThreads, 0),
+                 "occupancy") ||
+        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->staged_query_blocks_per_sm, k_query_staged, kThreads, 0),
+                 "occupancy") ||
         !cuda_ok(cudaHostAlloc(reinterpret_cast<void**>(&t->h_status), sizeof(unsigned), cudaHostAllocMapped),
                  "cudaHostAlloc")) {
         delete t;
         return PSF_ERR_CUDA;
     }
     *t->h_status = 0;
-    t->launch = psf_launch_config{0u, 0u, 0u, 0u};
+    t->launch = psf_launch_config{0u, 0u, 0u, 0u, 0u};
     char* base = static_cast<char*>(d_mem);
     TableView& v = t->view;
     v.hdr = reinterpret_cast<DevHeader*>(base + L.hdr);
@@ -370,10 +506,17 @@ int psf_insert(psf_table* t, const float* d_vertices, uint64_t n, void* stream) 
     const int grid = grid_for(t, t->insert_blocks_per_sm, n, t->launch.insert_blocks_per_sm);
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->launch.insert_mode == 1)
+    if (t->launch.vertex_staging) {
+        const int sgrid = grid_for(t, t->staged_blocks_per_sm, n, t->launch.insert_blocks_per_sm);
+        if (t->launch.insert_mode == 1)
+            k_insert_staged<psf::kAggNone><<<sgrid, kThreads, 0, st>>>(t->view, v, n);
+        else
+            k_insert_staged<psf::kAggWarp><<<sgrid, kThreads, 0, st>>>(t->view, v, n);
+    } else if (t->launch.insert_mode == 1) {
         k_insert<psf::kAggNone><<<grid, kThreads, 0, st>>>(t->view, v, n);
-    else
+    } else {
         k_insert<psf::kAggWarp><<<grid, kThreads, 0, st>>>(t->view, v, n);
+    }
     return cuda_ok(cudaGetLastError(), "k_insert") ? PSF_OK : PSF_ERR_CUDA;
 }
 
@@ -409,9 +552,15 @@ int launch_query(psf_table* t, const psf::Estimator& e, const float* d_vertices,
     if (!d_vertices || !d_out_rgb || (reinterpret_cast<uintptr_t>(d_vertices) & 15u) ||
         (reinterpret_cast<uintptr_t>(d_out_rgb) & 3u))
         return PSF_ERR_INVALID_ARG;
-    const int grid = grid_for(t, t->query_blocks_per_sm, P, t->launch.query_blocks_per_sm);
-    k_query<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view, e, reinterpret_cast<const float4*>(d_vertices),
-                                                                      P, D, d_out_rgb);
+    const float4* v = reinterpret_cast<const float4*>(d_vertices);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (t->launch.vertex_staging) {
+        const int grid = grid_for(t, t->staged_query_blocks_per_sm, P, t->launch.query_blocks_per_sm);
+        k_query_staged<<<grid, kThreads, 0, st>>>(t->view, e, v, P, D, d_out_rgb);
+    } else {
+        const int grid = grid_for(t, t->query_blocks_per_sm, P, t->launch.query_blocks_per_sm);
+        k_query<<<grid, kThreads, 0, st>>>(t->view, e, v, P, D, d_out_rgb);
+    }
     return cuda_ok(cudaGetLastError(), "k_query") ? PSF_OK : PSF_ERR_CUDA;
 }
 
@@ -444,7 +593,7 @@ int psf_reset(psf_table* t, void* stream) {
 }
 
 int psf_set_launch_config(psf_table* t, const psf_launch_config* c) {
-    if (!t || !c || c->insert_mode > 1) return PSF_ERR_INVALID_ARG;
+    if (!t || !c || c->insert_mode > 1 || c->vertex_staging > 1) return PSF_ERR_INVALID_ARG;
     t->launch = *c;
     return PSF_OK;
 }

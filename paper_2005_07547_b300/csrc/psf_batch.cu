@@ -57,12 +57,6 @@ size_t batch_bytes(uint32_t max_items) {
     return sizeof(BatchCtl) + sizeof(BatchHdr) + kBeginBytes + static_cast<size_t>(max_items) * sizeof(BatchItemDev);
 }
 
-__device__ __forceinline__ unsigned long long global_timer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // Grid-wide barrier for a co-resident grid.  The wait is bounded: on timeout the block
 // records PSF_STATUS_TIMEOUT (batch and every table) and the kernel leaves.
 __device__ bool grid_barrier(BatchCtl* ctl, const BatchHdr* h, const BatchItemDev* __restrict__ items) {
@@ -80,9 +74,9 @@ __device__ bool grid_barrier(BatchCtl* ctl, const BatchHdr* h, const BatchItemDe
             __threadfence();
             atomicAdd(&ctl->barrier_gen, 1u);
         } else {
-            const unsigned long long t0 = global_timer_ns();
+            const unsigned long long t0 = psf::global_timer_ns();
             while (*gen_p == gen) {
-                if (global_timer_ns() - t0 > h->timeout_ns) {
+                if (psf::global_timer_ns() - t0 > h->timeout_ns) {
                     ok = 0;
                     atomicOr(&ctl->status, psf::kStatusTimeout);
                     for (unsigned i = 0; i < h->n; ++i) atomicOr(&items[i].t.hdr->status, psf::kStatusTimeout);

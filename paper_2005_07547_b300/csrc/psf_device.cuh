@@ -73,6 +73,75 @@ struct TableView {
     float beta;
 };
 
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk staging of vertex tiles into shared memory: one thread arms an mbarrier with the
+// tile's byte count and starts a cp.async.bulk copy (the TMA unit moves the bytes, not the
+// load/store units); the block waits on the barrier's phase.  Waits are bounded.
+// ---------------------------------------------------------------------------
+constexpr unsigned kTileVerts = kThreads;  // one vertex per thread
+constexpr unsigned long long kStageTimeoutNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Arm `bar` for `bytes` and copy them from global to shared memory (called by one thread).
+// Both addresses are 16-byte aligned and bytes is a multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait (at most about a second) for the phase of `bar` with this parity to complete.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_timer_ns();
+    while (!mbar_test(bar, parity))
+        if (global_timer_ns() - t0 > kStageTimeoutNs) return false;
+    return true;
+}
+
+// Vertex t of a staged tile.  Lanes read the four 16-byte vectors of their 64-byte records
+// in an order rotated by (t >> 1) & 3, so the eight lanes of each quarter-warp touch eight
+// different groups of banks; selects put the vectors back in order.
+__device__ __forceinline__ void read_staged(const float4* tile, unsigned t, float4& v0, float4& v1, float4& v2,
+                                            float4& v3) {
+    const unsigned rot = (t >> 1) & 3u;
+    const float4* rec = tile + 4 * t;
+    const float4 r0 = rec[rot], r1 = rec[(1u + rot) & 3u], r2 = rec[(2u + rot) & 3u], r3 = rec[(3u + rot) & 3u];
+    // vector m was read at step (m - rot) & 3
+    v0 = rot == 0 ? r0 : rot == 1 ? r3 : rot == 2 ? r2 : r1;
+    v1 = rot == 0 ? r1 : rot == 1 ? r0 : rot == 2 ? r3 : r2;
+    v2 = rot == 0 ? r2 : rot == 1 ? r1 : rot == 2 ? r0 : r3;
+    v3 = rot == 0 ? r3 : rot == 1 ? r2 : rot == 2 ? r1 : r0;
+}
+
 // ---------------------------------------------------------------------------
 // Cell key: Section "Basis functions and data structures: spatio-directional
 // hashing".  Every decision that yields an integer is taken in FP32 with explicitly

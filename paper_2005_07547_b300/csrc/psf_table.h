@@ -19,6 +19,8 @@ struct psf_table {
     int insert_blocks_per_sm;  // occupancy limits of the kernels
     int update_blocks_per_sm;
     int query_blocks_per_sm;
+    int staged_blocks_per_sm;  // the shared-memory staged insert and query
+    int staged_query_blocks_per_sm;
     psf_launch_config launch;  // tuning knobs (psf_set_launch_config)
 };
 

@@ -254,7 +254,8 @@ def test_1920x1080_depth5_full_size_fp32_and_fp16(psf_mod, oracle_mod):
 
 @pytest.mark.parametrize("knobs", [dict(insert_mode=1), dict(insert_blocks_per_sm=1, update_blocks_per_sm=1,
                                                               query_blocks_per_sm=1),
-                                   dict(insert_mode=1, insert_blocks_per_sm=2)])
+                                   dict(insert_mode=1, insert_blocks_per_sm=2), dict(vertex_staging=1),
+                                   dict(vertex_staging=1, insert_mode=1, insert_blocks_per_sm=1, query_blocks_per_sm=1)])
 def test_launch_knobs_do_not_change_results(psf_mod, knobs):
     """Aggregation mode and grid shape change only the order of the integer additions."""
     import torch
@@ -333,3 +334,24 @@ def test_progressive_insert(psf_mod, oracle_mod, field, fp16):
         ora.update()
         check_after_update(table.export(), ora.export(), fp16=fp16)
     table.close()
+
+
+@pytest.mark.parametrize("P,D", [(1, 1), (255, 2), (257, 3), (4103, 2), (70001, 1), (33, 6)])
+def test_staged_vertex_tiles_with_ragged_tails(psf_mod, P, D):
+    """Bulk-copied vertex tiles (256 records) give the same tables and outputs as direct
+    loads, including partial last tiles of every depth row."""
+    import torch
+
+    rng = np.random.default_rng(P * 10 + D)
+    v = random_vertices(rng, P * D, q=3, cells_per_axis=4)
+    dv = torch.from_numpy(v).cuda()
+    cfg = psf_mod.make_config(log2_capacity=14, pos_bits=3, dir_bits=2, cache_fp16=bool(P % 2))
+    res = []
+    for staging in (0, 1):
+        t = psf_mod.Table(cfg)
+        t.set_launch(vertex_staging=staging)
+        outs = [t.step(dv, P, D).cpu().numpy() for _ in range(2)]
+        outs.append(t.query_biased(dv, P, D, 0.5).cpu().numpy())
+        res.append((t.export().tobytes(), np.concatenate(outs).tobytes(), t.stats()["status"]))
+        t.close()
+    assert res[0] == res[1]
