@@ -767,7 +767,7 @@ def main(argv=None) -> None:
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--insert-mode", type=int, default=0, help="0: warp aggregation of equal keys; 1: none")
-    ap.add_argument("--staging", type=int, default=0, help="1: stage vertex records through shared memory (TMA)")
+    ap.add_argument("--staging", type=int, default=0, help="bit 0: insert, bit 1: query stage vertex records through shared memory (TMA)")
     ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
     ap.add_argument("--pool", type=int, default=4, help="distinct resident iterations per session (batched)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")

@@ -196,8 +196,9 @@ typedef struct {
     uint32_t insert_blocks_per_sm; /* cap on resident 256-thread blocks per SM (0 = occupancy limit) */
     uint32_t update_blocks_per_sm;
     uint32_t query_blocks_per_sm;
-    uint32_t vertex_staging;       /* 1: psf_insert and psf_query_cv/_biased stage vertex records through
-                                      shared memory with bulk (TMA) copies; 0: direct 16-byte loads */
+    uint32_t vertex_staging;       /* bit 0: psf_insert, bit 1: psf_query_cv/_biased stage the vertex
+                                      records through shared memory with bulk (TMA) copies, per warp;
+                                      a clear bit means direct 16-byte loads */
 } psf_launch_config;
 
 /* Set / read the launch knobs of a table (host-side only; affects later calls). */

@@ -21,7 +21,7 @@ from .batch import Batch
 from .table import Table
 
 TABLE_SPACE = {
-    "vertex_staging": (0, 1),
+    "vertex_staging": (0, 1, 2, 3),
     "insert_mode": (0, 1),
     "insert_blocks_per_sm": (0, 4, 2),
     "query_blocks_per_sm": (0, 4),

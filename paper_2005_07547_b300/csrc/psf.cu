@@ -196,62 +196,69 @@ __global__ void __launch_bounds__(kThreads) k_insert_progressive(TableView t, co
     }
 }
 
-// k_insert with the vertex records staged through shared memory: thread 0 copies the
-// next 16 KB tile (256 records) with cp.async.bulk while the block works on the current
-// one; each thread reads its record from shared memory without bank conflicts.
+// k_insert with the vertex records staged through shared memory.  Every warp owns a
+// double buffer of 2 KB tiles (32 records) and its own mbarriers: lane 0 starts the bulk
+// copy of the warp's next tile, then waits for the current one; the warps of a block
+// never wait for each other.
+constexpr unsigned kWarpsPerBlock = kThreads / 32;
+
 template <int kMode>
-__global__ void __launch_bounds__(kThreads) k_insert_staged(TableView t, const float4* __restrict__ v, unsigned long long n) {
-    __shared__ alignas(128) float4 s_tile[2][psf::kTileVerts * 4];
-    __shared__ alignas(8) unsigned long long s_bar[2];
-    __shared__ int s_ok;
+__global__ void __launch_bounds__(kThreads, 5) k_insert_staged(TableView t, const float4* __restrict__ v, unsigned long long n) {
+    __shared__ alignas(128) float4 s_tile[kWarpsPerBlock][2][32 * 4];
+    __shared__ alignas(8) unsigned long long s_bar[kWarpsPerBlock][2];
     __shared__ unsigned s_max_probe;
     __shared__ unsigned long long s_leaders;
     __shared__ psf::LaneSums s_stage[kThreads];
-    const unsigned long long ntiles = (n + psf::kTileVerts - 1) / psf::kTileVerts;
-    if (threadIdx.x == 0) {
-        psf::mbar_init(&s_bar[0]);
-        psf::mbar_init(&s_bar[1]);
+    const unsigned lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    if (lane == 0) {
+        psf::mbar_init(&s_bar[wib][0]);
+        psf::mbar_init(&s_bar[wib][1]);
         psf::mbar_init_fence();
-        s_ok = 1;
+    }
+    if (threadIdx.x == 0) {
         s_max_probe = 0;
         s_leaders = 0;
     }
     __syncthreads();
+    const unsigned long long ntiles = (n + 31) / 32;
+    const unsigned long long nwarps = static_cast<unsigned long long>(gridDim.x) * kWarpsPerBlock;
     auto issue = [&](unsigned long long tile, unsigned buf) {
-        const unsigned long long first = tile * psf::kTileVerts;
-        const unsigned long long cnt = n - first < psf::kTileVerts ? n - first : psf::kTileVerts;
-        psf::bulk_load(s_tile[buf], v + 4 * first, static_cast<unsigned>(cnt * 64), &s_bar[buf]);
+        const unsigned long long first = tile * 32;
+        const unsigned long long cnt = n - first < 32 ? n - first : 32;
+        psf::bulk_load(s_tile[wib][buf], v + 4 * first, static_cast<unsigned>(cnt * 64), &s_bar[wib][buf]);
     };
     psf::LaneSums* stage = s_stage + (threadIdx.x & ~31u);
     unsigned max_len = 0, leaders = 0;
-    unsigned long long tile = blockIdx.x;
-    if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
-    bool pending_other = false;  // a copy into the other buffer is in flight
+    unsigned long long tile = static_cast<unsigned long long>(blockIdx.x) * kWarpsPerBlock + wib;
+    if (lane == 0 && tile < ntiles) issue(tile, 0);
+    bool ok = true, pending_other = false;
     unsigned k = 0;
-    for (; tile < ntiles; tile += gridDim.x, ++k) {
+    for (; tile < ntiles; tile += nwarps, ++k) {
         const unsigned buf = k & 1u;
-        if (threadIdx.x == 0) {
-            const unsigned long long next = tile + gridDim.x;
+        int got = 1;
+        if (lane == 0) {
+            const unsigned long long next = tile + nwarps;
             pending_other = next < ntiles;
             if (pending_other) issue(next, buf ^ 1u);
-            s_ok = psf::mbar_wait(&s_bar[buf], (k >> 1) & 1u);
+            got = psf::mbar_wait(&s_bar[wib][buf], (k >> 1) & 1u);
         }
-        __syncthreads();
-        if (!s_ok) break;
-        const unsigned long long i = tile * psf::kTileVerts + threadIdx.x;
+        ok = __shfl_sync(psf::kFull, got, 0) != 0;
+        __syncwarp();  // lane 0 saw the tile land; order the other lanes' reads after it
+        if (!ok) break;
+        const unsigned long long i = tile * 32 + lane;
         const bool valid = i < n;
         float4 v0 = make_float4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
-        if (valid) psf::read_staged(s_tile[buf], threadIdx.x, v0, v1, v2, v3);
+        if (valid) psf::read_staged(s_tile[wib][buf], lane, v0, v1, v2, v3);
         psf::insert_warp<kMode>(t, valid, v0, v1, v2, v3, &max_len, stage, &leaders);
-        __syncthreads();  // the tile is consumed before its buffer is refilled
+        __syncwarp();  // the tile is consumed before its buffer is refilled
     }
-    if (!s_ok && threadIdx.x == 0) {
+    if (!ok && lane == 0) {
         atomicOr(&t.hdr->status, psf::kStatusTimeout);
-        // let a copy still in flight land before the block leaves (bounded)
-        if (pending_other) psf::mbar_wait(&s_bar[(k & 1u) ^ 1u], ((k + 1) >> 1) & 1u);
+        // let a copy still in flight land before the warp leaves (bounded)
+        if (pending_other) psf::mbar_wait(&s_bar[wib][(k & 1u) ^ 1u], ((k + 1) >> 1) & 1u);
     }
     if (max_len) atomicMax(&s_max_probe, max_len);
-    if ((threadIdx.x & 31u) == 0 && leaders) atomicAdd(&s_leaders, static_cast<unsigned long long>(leaders));
+    if (lane == 0 && leaders) atomicAdd(&s_leaders, static_cast<unsigned long long>(leaders));
     __syncthreads();
     if (threadIdx.x == 0) {
         if (s_max_probe) atomicMax(&t.hdr->max_probe, s_max_probe);
@@ -259,50 +266,52 @@ __global__ void __launch_bounds__(kThreads) k_insert_staged(TableView t, const f
     }
 }
 
-// k_query with the vertex records staged through shared memory.  A block owns 256
-// consecutive paths; it walks their depths from last to first, each depth being one
-// contiguous 16 KB tile, while the next (block, depth) tile is copied in.
-__global__ void __launch_bounds__(kThreads) k_query_staged(TableView t, psf::Estimator e, const float4* __restrict__ v,
+// k_query with the vertex records staged through shared memory, per warp: a warp owns 32
+// consecutive paths and walks their depths from last to first; each depth of those paths
+// is one contiguous 2 KB tile, copied while the previous one is probed.
+__global__ void __launch_bounds__(kThreads, 5) k_query_staged(TableView t, psf::Estimator e, const float4* __restrict__ v,
                                                            unsigned P, unsigned D, float* __restrict__ out) {
-    __shared__ alignas(128) float4 s_tile[2][psf::kTileVerts * 4];
-    __shared__ alignas(8) unsigned long long s_bar[2];
-    __shared__ int s_ok;
-    const unsigned long long nblk = (static_cast<unsigned long long>(P) + psf::kTileVerts - 1) / psf::kTileVerts;
-    if (threadIdx.x == 0) {
-        psf::mbar_init(&s_bar[0]);
-        psf::mbar_init(&s_bar[1]);
+    __shared__ alignas(128) float4 s_tile[kWarpsPerBlock][2][32 * 4];
+    __shared__ alignas(8) unsigned long long s_bar[kWarpsPerBlock][2];
+    const unsigned lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    if (lane == 0) {
+        psf::mbar_init(&s_bar[wib][0]);
+        psf::mbar_init(&s_bar[wib][1]);
         psf::mbar_init_fence();
-        s_ok = 1;
     }
-    __syncthreads();
-    auto issue = [&](unsigned long long b, unsigned j, unsigned buf) {
-        const unsigned long long first = b * psf::kTileVerts;
-        const unsigned long long cnt = P - first < psf::kTileVerts ? P - first : psf::kTileVerts;
-        psf::bulk_load(s_tile[buf], v + 4 * (static_cast<unsigned long long>(j) * P + first), static_cast<unsigned>(cnt * 64),
-                       &s_bar[buf]);
+    __syncwarp();
+    const unsigned long long nunits = (static_cast<unsigned long long>(P) + 31) / 32;
+    const unsigned long long nwarps = static_cast<unsigned long long>(gridDim.x) * kWarpsPerBlock;
+    auto issue = [&](unsigned long long u, unsigned j, unsigned buf) {
+        const unsigned long long first = u * 32;
+        const unsigned long long cnt = P - first < 32 ? P - first : 32;
+        psf::bulk_load(s_tile[wib][buf], v + 4 * (static_cast<unsigned long long>(j) * P + first), static_cast<unsigned>(cnt * 64),
+                       &s_bar[wib][buf]);
     };
-    unsigned long long b = blockIdx.x;
+    unsigned long long u = static_cast<unsigned long long>(blockIdx.x) * kWarpsPerBlock + wib;
     unsigned j = D - 1;
-    if (threadIdx.x == 0 && b < nblk) issue(b, j, 0);
-    bool pending_other = false;
+    if (lane == 0 && u < nunits) issue(u, j, 0);
+    bool ok = true, pending_other = false;
     unsigned k = 0;
     float3 c_next = make_float3(0.0f, 0.0f, 0.0f);
-    while (b < nblk) {
+    while (u < nunits) {
         const unsigned buf = k & 1u;
-        const unsigned long long nb = j > 0 ? b : b + gridDim.x;
+        const unsigned long long nu = j > 0 ? u : u + nwarps;
         const unsigned nj = j > 0 ? j - 1 : D - 1;
-        if (threadIdx.x == 0) {
-            pending_other = nb < nblk;
-            if (pending_other) issue(nb, nj, buf ^ 1u);
-            s_ok = psf::mbar_wait(&s_bar[buf], (k >> 1) & 1u);
+        int got = 1;
+        if (lane == 0) {
+            pending_other = nu < nunits;
+            if (pending_other) issue(nu, nj, buf ^ 1u);
+            got = psf::mbar_wait(&s_bar[wib][buf], (k >> 1) & 1u);
         }
-        __syncthreads();
-        if (!s_ok) break;
+        ok = __shfl_sync(psf::kFull, got, 0) != 0;
+        __syncwarp();
+        if (!ok) break;
         if (j == D - 1) c_next = make_float3(0.0f, 0.0f, 0.0f);
-        const unsigned long long p = b * psf::kTileVerts + threadIdx.x;
+        const unsigned long long p = u * 32 + lane;
         if (p < P) {
             float4 v0, v1, v2, v3;
-            psf::read_staged(s_tile[buf], threadIdx.x, v0, v1, v2, v3);
+            psf::read_staged(s_tile[wib][buf], lane, v0, v1, v2, v3);
             const float3 c = psf::cell_value(t, v0, v1, v2);
             float o0 = v3.x, o1 = v3.y, o2 = v3.z;
             if (j + 1 < D && j >= e.j_begin && j < e.j_end) {
@@ -316,14 +325,14 @@ __global__ void __launch_bounds__(kThreads) k_query_staged(TableView t, psf::Est
             o[2] = o2;
             c_next = c;
         }
-        __syncthreads();  // the tile is consumed before its buffer is refilled
-        b = nb;
+        __syncwarp();  // the tile is consumed before its buffer is refilled
+        u = nu;
         j = nj;
         ++k;
     }
-    if (!s_ok && threadIdx.x == 0) {
+    if (!ok && lane == 0) {
         atomicOr(&t.hdr->status, psf::kStatusTimeout);
-        if (pending_other) psf::mbar_wait(&s_bar[(k & 1u) ^ 1u], ((k + 1) >> 1) & 1u);
+        if (pending_other) psf::mbar_wait(&s_bar[wib][(k & 1u) ^ 1u], ((k + 1) >> 1) & 1u);
     }
 }
 
@@ -506,7 +515,7 @@ int psf_insert(psf_table* t, const float* d_vertices, uint64_t n, void* stream) 
     const int grid = grid_for(t, t->insert_blocks_per_sm, n, t->launch.insert_blocks_per_sm);
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->launch.vertex_staging) {
+    if (t->launch.vertex_staging & 1u) {
         const int sgrid = grid_for(t, t->staged_blocks_per_sm, n, t->launch.insert_blocks_per_sm);
         if (t->launch.insert_mode == 1)
             k_insert_staged<psf::kAggNone><<<sgrid, kThreads, 0, st>>>(t->view, v, n);
@@ -554,7 +563,7 @@ int launch_query(psf_table* t, const psf::Estimator& e, const float* d_vertices,
         return PSF_ERR_INVALID_ARG;
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->launch.vertex_staging) {
+    if (t->launch.vertex_staging & 2u) {
         const int grid = grid_for(t, t->staged_query_blocks_per_sm, P, t->launch.query_blocks_per_sm);
         k_query_staged<<<grid, kThreads, 0, st>>>(t->view, e, v, P, D, d_out_rgb);
     } else {
@@ -593,7 +602,7 @@ int psf_reset(psf_table* t, void* stream) {
 }
 
 int psf_set_launch_config(psf_table* t, const psf_launch_config* c) {
-    if (!t || !c || c->insert_mode > 1 || c->vertex_staging > 1) return PSF_ERR_INVALID_ARG;
+    if (!t || !c || c->insert_mode > 1 || c->vertex_staging > 3) return PSF_ERR_INVALID_ARG;
     t->launch = *c;
     return PSF_OK;
 }

@@ -254,8 +254,8 @@ def test_1920x1080_depth5_full_size_fp32_and_fp16(psf_mod, oracle_mod):
 
 @pytest.mark.parametrize("knobs", [dict(insert_mode=1), dict(insert_blocks_per_sm=1, update_blocks_per_sm=1,
                                                               query_blocks_per_sm=1),
-                                   dict(insert_mode=1, insert_blocks_per_sm=2), dict(vertex_staging=1),
-                                   dict(vertex_staging=1, insert_mode=1, insert_blocks_per_sm=1, query_blocks_per_sm=1)])
+                                   dict(insert_mode=1, insert_blocks_per_sm=2), dict(vertex_staging=3),
+                                   dict(vertex_staging=3, insert_mode=1, insert_blocks_per_sm=1, query_blocks_per_sm=1)])
 def test_launch_knobs_do_not_change_results(psf_mod, knobs):
     """Aggregation mode and grid shape change only the order of the integer additions."""
     import torch
@@ -347,7 +347,7 @@ def test_staged_vertex_tiles_with_ragged_tails(psf_mod, P, D):
     dv = torch.from_numpy(v).cuda()
     cfg = psf_mod.make_config(log2_capacity=14, pos_bits=3, dir_bits=2, cache_fp16=bool(P % 2))
     res = []
-    for staging in (0, 1):
+    for staging in (0, 3):
         t = psf_mod.Table(cfg)
         t.set_launch(vertex_staging=staging)
         outs = [t.step(dv, P, D).cpu().numpy() for _ in range(2)]
