@@ -75,13 +75,13 @@ def algorithmic_bytes(V: int, touched: float, cache_fp16: bool) -> dict:
     insert: read the 64-B vertex record of every vertex; per touched cell read its
             8-B key and read-modify-write its 32-B accumulator (8 + 64).
     update: per touched cell read + zero the 32-B accumulator, read + write the 16-B
-            approximant and the 8-B c_old, write the 8-B FP16 copy (112 or 120).
+            approximant and the 8-B c_old, write the query copy: 8-B FP16 (120) or 16-B FP32 (128).
     query:  read the 64-B record and write the 12-B output of every vertex; per
             touched cell read its key and its approximant (8 + 16, or 8 + 8 for FP16).
     """
     return {
         "k_insert": 64.0 * V + 72.0 * touched,
-        "k_update": (120.0 if cache_fp16 else 112.0) * touched,
+        "k_update": (120.0 if cache_fp16 else 128.0) * touched,
         "k_query": 76.0 * V + (16.0 if cache_fp16 else 24.0) * touched,
     }
 
@@ -767,7 +767,7 @@ def main(argv=None) -> None:
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--insert-mode", type=int, default=0, help="0: warp aggregation of equal keys; 1: none")
-    ap.add_argument("--staging", type=int, default=0, help="bit 0: insert, bit 1: query stage vertex records through shared memory (TMA)")
+    ap.add_argument("--staging", type=int, default=1, help="bit 0: insert, bit 1: query stage vertex records through shared memory (TMA)")
     ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
     ap.add_argument("--pool", type=int, default=4, help="distinct resident iterations per session (batched)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")

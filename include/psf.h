@@ -83,7 +83,8 @@ typedef struct {
     float beta;             /* control-variate coefficient (the paper uses [0.5, 1]) */
     uint32_t cv_max_depth;  /* the CV is applied to vertices j < cv_max_depth only */
     uint32_t frac_bits;     /* F: fixed-point fraction bits of the accumulators, 8..32 */
-    uint32_t cache_fp16;    /* 1: the update also writes an FP16 copy of L~ and queries read it */
+    uint32_t cache_fp16;    /* queries read a compact copy of L~ written by the update: 1 = FP16 (8 B/slot),
+                               0 = FP32 (16 B/slot); the blend always keeps the FP32 master */
     uint32_t blend_mode;    /* 0: eq. (11) square-root blend; 1: constant alpha = alpha_min */
 } psf_config;
 
@@ -189,7 +190,9 @@ int psf_get_stats(psf_table* t, psf_stats* out, void* stream);
 int psf_destroy(psf_table* t);
 
 /* Launch knobs of a table's kernels (the autotuner's search space).  Results do not
- * depend on them: the integer sums are order-independent.  Zero fields mean "default". */
+ * depend on them: the integer sums are order-independent.  psf_create starts from
+ * {0, 0, 0, 0, 1} (warp merge, occupancy-limited grids, insert tiles staged); a zero
+ * grid cap means the occupancy limit. */
 typedef struct {
     uint32_t insert_mode;          /* 0: lanes of a warp holding the same key are merged (match_any)
                                       and one leader probes and adds; 1: every vertex adds on its own */
