@@ -75,13 +75,13 @@ def algorithmic_bytes(V: int, touched: float, cache_fp16: bool) -> dict:
     insert: read the 64-B vertex record of every vertex; per touched cell read its
             8-B key and read-modify-write its 32-B accumulator (8 + 64).
     update: per touched cell read + zero the 32-B accumulator, read + write the 16-B
-            approximant and the 8-B c_old, write the query copy: 8-B FP16 (120) or 16-B FP32 (128).
+            approximant and the 8-B c_old, write the 8-B FP16 copy (112 or 120).
     query:  read the 64-B record and write the 12-B output of every vertex; per
             touched cell read its key and its approximant (8 + 16, or 8 + 8 for FP16).
     """
     return {
         "k_insert": 64.0 * V + 72.0 * touched,
-        "k_update": (120.0 if cache_fp16 else 128.0) * touched,
+        "k_update": (120.0 if cache_fp16 else 112.0) * touched,
         "k_query": 76.0 * V + (16.0 if cache_fp16 else 24.0) * touched,
     }
 

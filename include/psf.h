@@ -83,8 +83,8 @@ typedef struct {
     float beta;             /* control-variate coefficient (the paper uses [0.5, 1]) */
     uint32_t cv_max_depth;  /* the CV is applied to vertices j < cv_max_depth only */
     uint32_t frac_bits;     /* F: fixed-point fraction bits of the accumulators, 8..32 */
-    uint32_t cache_fp16;    /* queries read a compact copy of L~ written by the update: 1 = FP16 (8 B/slot),
-                               0 = FP32 (16 B/slot); the blend always keeps the FP32 master */
+    uint32_t cache_fp16;    /* 1: the update also writes an 8-byte FP16 copy of L~ and queries read it
+                               (the blend always keeps the FP32 master, which queries read otherwise) */
     uint32_t blend_mode;    /* 0: eq. (11) square-root blend; 1: constant alpha = alpha_min */
 } psf_config;
 

@@ -42,7 +42,7 @@ namespace {
 bool cuda_ok(cudaError_t e, const char* what) { return psf_cuda_ok(e, what); }
 
 struct Layout {
-    size_t hdr, keys, slots, mirror, qval, dirty, total;
+    size_t hdr, keys, slots, mirror, dirty, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -69,8 +69,6 @@ Layout layout_of(const psf_config* c) {
     off = align256(off + cap * sizeof(Slot));
     L.mirror = off;
     if (c->cache_fp16) off = align256(off + cap * sizeof(uint2));
-    L.qval = off;
-    if (!c->cache_fp16) off = align256(off + cap * sizeof(float4));
     L.dirty = off;
     off = align256(off + ((cap + 31) / 32) * sizeof(unsigned));
     L.total = off;
@@ -479,7 +477,6 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     v.keys = reinterpret_cast<unsigned long long*>(base + L.keys);
     v.slots = reinterpret_cast<Slot*>(base + L.slots);
     v.mirror = cfg->cache_fp16 ? reinterpret_cast<uint2*>(base + L.mirror) : nullptr;
-    v.qval = cfg->cache_fp16 ? nullptr : reinterpret_cast<float4*>(base + L.qval);
     v.dirty = reinterpret_cast<unsigned*>(base + L.dirty);
     unsigned* dev_status = nullptr;
     if (!cuda_ok(cudaHostGetDevicePointer(reinterpret_cast<void**>(&dev_status), t->h_status, 0), "cudaHostGetDevicePointer")) {

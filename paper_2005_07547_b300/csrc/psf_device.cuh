@@ -6,12 +6,11 @@
 //   slots  Slot[cap]  (64 B)        sums + c_new (bytes 0-31), approximant L~ (32-47),
 //                                   c_old (48-55): one aligned 64-byte block per cell
 //   mirror uint2[cap] (8 B)         FP16 copy of L~ read by queries (cache_fp16 = 1)
-//   qval   float4[cap] (16 B)       FP32 copy of L~ read by queries (cache_fp16 = 0)
 //   dirty  u32[cap/32]              one bit per slot: touched this iteration
 // Inserts touch keys + the first 32-byte sector of a slot (atomics); the blend reads and
 // writes exactly one 64-byte block per touched cell, the DRAM access granularity, so
-// scattered cells cost no partial bursts, plus the cell's compact query copy; queries read
-// keys + the compact copy, a working set small enough to stay in L2.
+// scattered cells cost no partial bursts; queries read keys + the second sector of the
+// slot (FP32) or the compact 8-byte FP16 copy.
 
 #pragma once
 
@@ -60,7 +59,6 @@ struct TableView {
     unsigned long long* keys;
     Slot* slots;
     uint2* mirror;  // FP16 query copy (cache_fp16), else nullptr
-    float4* qval;   // FP32 query copy (no cache_fp16), else nullptr
     unsigned* dirty;
     unsigned* h_status;  // host-mapped copy of the status word (may be nullptr)
     uint32_t log2cap;
@@ -412,7 +410,6 @@ __device__ __forceinline__ void blend_store(const TableView& t, unsigned long lo
         __stcg(reinterpret_cast<float4*>(p + 2), d.L);
         __stcg(p + 3, make_longlong2(ctot, d.co.y));
         if (t.mirror) t.mirror[s] = pack_half4(d.L.x, d.L.y, d.L.z);
-        if (t.qval) t.qval[s] = d.L;
     }
     __stcg(p, z);
     __stcg(p + 1, z);
@@ -488,7 +485,7 @@ __device__ __forceinline__ float3 value_at(const TableView& t, unsigned long lon
                            __half2float(__ushort_as_half(static_cast<unsigned short>(h.x >> 16))),
                            __half2float(__ushort_as_half(static_cast<unsigned short>(h.y & 0xffffu))));
     }
-    const float4 L = __ldcg(t.qval ? t.qval + s : &t.slots[s].L);
+    const float4 L = __ldcg(&t.slots[s].L);
     return make_float3(L.x, L.y, L.z);
 }
 

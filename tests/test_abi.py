@@ -80,11 +80,11 @@ def test_table_bytes_and_config_validation(lib):
 
     good = _abi.make_config(log2_capacity=16)
     n16 = lib.psf_table_bytes(ctypes.byref(good))
-    # header + 8-byte key + 64-byte slot record + 16-byte FP32 query copy per slot + dirty bits
-    assert n16 >= (1 << 16) * (8 + 64 + 16) + (1 << 16) // 8
+    # header + 8-byte key + 64-byte slot record per slot + dirty bits
+    assert n16 >= (1 << 16) * (8 + 64) + (1 << 16) // 8
     assert n16 % 256 == 0
-    fp16 = _abi.make_config(log2_capacity=16, cache_fp16=True)  # an 8-byte FP16 copy instead
-    assert lib.psf_table_bytes(ctypes.byref(fp16)) == n16 - (1 << 16) * 8
+    fp16 = _abi.make_config(log2_capacity=16, cache_fp16=True)  # plus the 8-byte FP16 copy
+    assert lib.psf_table_bytes(ctypes.byref(fp16)) == n16 + (1 << 16) * 8
     assert lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=17))) > 2 * n16 - 4096
     for bad in (dict(log2_capacity=3), dict(log2_capacity=31), dict(dir_bits=6), dict(pos_bits=21),
                 dict(frac_bits=7), dict(frac_bits=33), dict(alpha_min=1.5), dict(alpha_min=-0.1),
