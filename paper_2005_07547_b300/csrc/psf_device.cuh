@@ -91,6 +91,27 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
+// L2 eviction-priority policies for per-access cache hints (createpolicy, sm_80+).
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// A hash key read at L2 (bypassing L1) that asks L2 to keep the line: the key array is the
+// part of the table every probe touches.
+__device__ __forceinline__ unsigned long long load_key(const unsigned long long* p, unsigned long long policy) {
+    unsigned long long v;
+    asm volatile("ld.global.cg.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(policy));
+    return v;
+}
+
 __device__ __forceinline__ void mbar_init(unsigned long long* bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -99,13 +120,17 @@ __device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier
 
 // Arm `bar` for `bytes` and copy them from global to shared memory (called by one thread).
 // Both addresses are 16-byte aligned and bytes is a multiple of 16.
+// The vertex records are read once: the copy carries an evict-first L2 policy so the stream
+// does not push the table out of L2.
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    const unsigned long long policy = policy_evict_first();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
 }
 
 __device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
@@ -243,9 +268,10 @@ __device__ __forceinline__ unsigned long long home_slot(const TableView& t, unsi
 // Returns the slot, or -1 when max_probe slots were visited without success.
 __device__ __forceinline__ long long probe_claim(const TableView& t, unsigned long long key, unsigned* len) {
     const unsigned long long mask = (1ull << t.log2cap) - 1ull;
+    const unsigned long long keep = policy_evict_last();
     unsigned long long s = home_slot(t, key);
     for (unsigned i = 0; i < t.max_probe; ++i) {
-        const unsigned long long k = __ldcg(t.keys + s);
+        const unsigned long long k = load_key(t.keys + s, keep);
         if (k == key) {
             *len = i + 1;
             return static_cast<long long>(s);
@@ -260,19 +286,6 @@ __device__ __forceinline__ long long probe_claim(const TableView& t, unsigned lo
         s = (s + 1) & mask;
     }
     *len = t.max_probe;
-    return -1;
-}
-
-// Read-only lookup: slot of `key` or -1 if absent.
-__device__ __forceinline__ long long probe_find(const TableView& t, unsigned long long key) {
-    const unsigned long long mask = (1ull << t.log2cap) - 1ull;
-    unsigned long long s = home_slot(t, key);
-    for (unsigned i = 0; i < t.max_probe; ++i) {
-        const unsigned long long k = __ldcg(t.keys + s);
-        if (k == key) return static_cast<long long>(s);
-        if (k == kEmpty) return -1;
-        s = (s + 1) & mask;
-    }
     return -1;
 }
 
@@ -498,14 +511,15 @@ __device__ __forceinline__ float3 cell_value(const TableView& t, const float4& v
     unsigned long long key;
     if (!cell_key(t, v0, v1, v2, &key)) return zero;
     const unsigned long long mask = (1ull << t.log2cap) - 1ull;
+    const unsigned long long keep = policy_evict_last();
     unsigned long long s = home_slot(t, key);
-    const unsigned long long k0 = __ldcg(t.keys + s);
+    const unsigned long long k0 = load_key(t.keys + s, keep);
     const float3 c0 = value_at(t, s, fp32_master);
     if (k0 == key) return c0;
     if (k0 == kEmpty) return zero;
     for (unsigned i = 1; i < t.max_probe; ++i) {
         s = (s + 1) & mask;
-        const unsigned long long k = __ldcg(t.keys + s);
+        const unsigned long long k = load_key(t.keys + s, keep);
         if (k == key) return value_at(t, s, fp32_master);
         if (k == kEmpty) return zero;
     }
