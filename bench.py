@@ -95,8 +95,9 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6400.0, "source": "fallback"}
 
 
-def load_traffic(kernel: str) -> float | None:
-    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+def load_traffic(kernel: str, staged: bool = False) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged
+    (the insert with staged vertex tiles is the kernel k_insert_staged)."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
@@ -104,7 +105,8 @@ def load_traffic(kernel: str) -> float | None:
         d = json.load(f)
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    k = d.get("kernels", {}).get(kernel)
+    name = kernel + "_staged" if staged and kernel in ("k_insert", "k_query") else kernel
+    k = d.get("kernels", {}).get(name)
     return float(k["bytes_per_launch"]) if k else None
 
 
@@ -452,7 +454,8 @@ def run_psf(args) -> None:
     # the dominant kernel's binding roof: the larger of its HBM and L2-atomic fractions
     hbm = {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
            "peak_source": peaks["source"], "algorithmic_bytes_per_launch": alg[dominant]}
-    roofline = {"kernel": dominant, "traffic": load_traffic(dominant), "hbm": hbm}
+    staged = {"k_insert": bool(args.staging & 1), "k_query": bool(args.staging & 2)}.get(dominant, False)
+    roofline = {"kernel": dominant, "traffic": load_traffic(dominant, staged), "hbm": hbm}
     binding = hbm
     roofline["bound"] = "hbm"
     if dominant == "k_insert" and atomic_roofline["frac"] is not None:
