@@ -374,7 +374,8 @@ def run_psf(args) -> None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     psf.load()
     cfg = psf.make_config(log2_capacity=w["log2_capacity"], pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],
-                          alpha_min=w["alpha_min"], cache_fp16=args.fp16 or w["cache_fp16"])
+                          alpha_min=w["alpha_min"], cache_fp16=args.fp16 or w["cache_fp16"],
+                          key_layout=args.key_layout)
     table = psf.Table(cfg)
     table.set_launch(insert_mode=args.insert_mode, vertex_staging=args.staging)
     dev = [torch.from_numpy(v).cuda() for v in host]
@@ -483,6 +484,7 @@ def run_psf(args) -> None:
                    "l2": f"inputs larger than L2: {n_iter} distinct {V * 64 / 1e6:.0f} MB vertex batches, "
                          "a different one every step",
                    "insert_mode": args.insert_mode, "vertex_staging": args.staging,
+                   "key_layout": {0: "auto", 1: "dense key array", 2: "keys in slot records"}[args.key_layout],
                    "parallelism": f"sessions x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "mean": float(np.mean(step_ms))},
@@ -772,6 +774,7 @@ def main(argv=None) -> None:
     ap.add_argument("--insert-mode", type=int, default=0, help="0: warp aggregation of equal keys; 1: none")
     ap.add_argument("--staging", type=int, default=1, help="bit 0: insert, bit 1: query stage vertex records through shared memory (TMA)")
     ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
+    ap.add_argument("--key-layout", type=int, default=0, help="0: auto, 1: dense key array, 2: keys in slot records")
     ap.add_argument("--pool", type=int, default=4, help="distinct resident iterations per session (batched)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")

@@ -47,8 +47,13 @@ struct Layout {
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
+bool keys_inline(const psf_config* c) {
+    return c->key_layout == 2 || (c->key_layout == 0 && c->log2_capacity >= 23);
+}
+
 bool config_valid(const psf_config* c) {
     if (!c) return false;
+    if (c->key_layout > 2) return false;
     if (c->log2_capacity < 4 || c->log2_capacity > 30) return false;
     if (c->pos_bits_q > 20 || c->dir_bits_d > 5) return false;
     if (c->frac_bits < 8 || c->frac_bits > 32) return false;
@@ -64,7 +69,7 @@ Layout layout_of(const psf_config* c) {
     L.hdr = off;
     off = align256(off + sizeof(DevHeader));
     L.keys = off;
-    off = align256(off + cap * sizeof(unsigned long long));
+    if (!keys_inline(c)) off = align256(off + cap * sizeof(unsigned long long));
     L.slots = off;
     off = align256(off + cap * sizeof(Slot));
     L.mirror = off;
@@ -370,7 +375,7 @@ __global__ void __launch_bounds__(kThreads) k_export(TableView t, unsigned long 
     for (unsigned long long base = s0 + static_cast<unsigned long long>(blockIdx.x) * blockDim.x; base < s1;
          base += stride) {
         const unsigned long long s = base + threadIdx.x;
-        const unsigned long long key = s < s1 ? t.keys[s] : psf::kEmpty;
+        const unsigned long long key = s < s1 ? *psf::key_ptr(t, s) : psf::kEmpty;
         const bool live = key != psf::kEmpty;
         const unsigned m = __ballot_sync(psf::kFull, live);
         if (!m) continue;
@@ -411,10 +416,18 @@ __global__ void __launch_bounds__(kThreads) k_count_live(TableView t, unsigned l
     unsigned long long mine = 0;
     const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
     for (unsigned long long s = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; s < cap; s += stride)
-        mine += t.keys[s] != psf::kEmpty;
+        mine += *psf::key_ptr(t, s) != psf::kEmpty;
     if (mine) atomicAdd(&s_count, mine);
     __syncthreads();
     if (threadIdx.x == 0 && s_count) atomicAdd(count, s_count);
+}
+
+// Empty key fields of a table whose keys live inside the slot records.
+__global__ void __launch_bounds__(kThreads) k_init_keys(TableView t) {
+    const unsigned long long cap = 1ull << t.log2cap;
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+    for (unsigned long long s = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; s < cap; s += stride)
+        *psf::key_ptr(t, s) = psf::kEmpty;
 }
 
 // Global counter reset: c_old := 0 in every slot (the approximant is kept).
@@ -474,7 +487,14 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     char* base = static_cast<char*>(d_mem);
     TableView& v = t->view;
     v.hdr = reinterpret_cast<DevHeader*>(base + L.hdr);
-    v.keys = reinterpret_cast<unsigned long long*>(base + L.keys);
+    v.slots = reinterpret_cast<Slot*>(base + L.slots);
+    if (keys_inline(cfg)) {
+        v.keys = &v.slots[0].key;
+        v.key_stride = sizeof(Slot) / sizeof(unsigned long long);
+    } else {
+        v.keys = reinterpret_cast<unsigned long long*>(base + L.keys);
+        v.key_stride = 1;
+    }
     v.slots = reinterpret_cast<Slot*>(base + L.slots);
     v.mirror = cfg->cache_fp16 ? reinterpret_cast<uint2*>(base + L.mirror) : nullptr;
     v.dirty = reinterpret_cast<unsigned*>(base + L.dirty);
@@ -497,8 +517,13 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     v.beta = cfg->beta;
 
     const size_t cap = size_t{1} << cfg->log2_capacity;
-    bool ok = cuda_ok(cudaMemsetAsync(base, 0, L.total, st), "cudaMemsetAsync") &&
-              cuda_ok(cudaMemsetAsync(base + L.keys, 0xff, cap * sizeof(unsigned long long), st), "cudaMemsetAsync");
+    bool ok = cuda_ok(cudaMemsetAsync(base, 0, L.total, st), "cudaMemsetAsync");
+    if (ok && !keys_inline(cfg)) {
+        ok = cuda_ok(cudaMemsetAsync(base + L.keys, 0xff, cap * sizeof(unsigned long long), st), "cudaMemsetAsync");
+    } else if (ok) {
+        k_init_keys<<<grid_for(t, 4, cap), kThreads, 0, st>>>(v);
+        ok = cuda_ok(cudaGetLastError(), "k_init_keys");
+    }
     if (!ok) {
         cudaFreeHost(t->h_status);
         delete t;

@@ -2,9 +2,11 @@
 //
 // Table memory (one contiguous caller-owned allocation, every array 256-byte aligned):
 //   DevHeader                       status word and counters
-//   keys   u64[cap]                 packed cell key or kEmpty (open addressing, linear probe)
-//   slots  Slot[cap]  (64 B)        sums + c_new (bytes 0-31), approximant L~ (32-47),
-//                                   c_old (48-55): one aligned 64-byte block per cell
+//   keys   u64[cap]                 packed cell key or kEmpty (open addressing, linear probe);
+//                                   absent when the keys live inside the slot records
+//   slots  Slot[cap]  (64 B)        sums + c_new (bytes 0-31), key (32-39, when inside),
+//                                   c_old (40-47), approximant L~ (48-63): one aligned
+//                                   64-byte block per cell
 //   mirror uint2[cap] (8 B)         FP16 copy of L~ read by queries (cache_fp16 = 1)
 //   dirty  u32[cap/32]              one bit per slot: touched this iteration
 // Inserts touch keys + the first 32-byte sector of a slot (atomics); the blend reads and
@@ -42,11 +44,11 @@ struct DevHeader {
 static_assert(sizeof(DevHeader) == 256, "header is one 256-byte block");
 
 struct alignas(64) Slot {
-    long long s[3];  // this iteration's sum of round(w L_c 2^F)
-    long long c;     // this iteration's counter c_new = sum of round(w 2^F)
-    float4 L;        // the approximant (r, g, b, unused)
-    long long c_old; // cumulative counter of blended iterations
-    long long spare;
+    long long s[3];          // this iteration's sum of round(w L_c 2^F)
+    long long c;             // this iteration's counter c_new = sum of round(w 2^F)
+    unsigned long long key;  // the cell key when keys live in the slots (unused otherwise)
+    long long c_old;         // cumulative counter of blended iterations
+    float4 L;                // the approximant (r, g, b, unused)
 };
 static_assert(sizeof(Slot) == 64, "one slot is one 64-byte block");
 
@@ -56,7 +58,8 @@ constexpr int kAggNone = 1;  // every vertex probes and adds on its own
 
 struct TableView {
     DevHeader* hdr;
-    unsigned long long* keys;
+    unsigned long long* keys;  // key of slot s at keys[s * key_stride]
+    unsigned key_stride;       // 1: dense key array; 8: the key field of the 64-byte slot records
     Slot* slots;
     uint2* mirror;  // FP16 query copy (cache_fp16), else nullptr
     unsigned* dirty;
@@ -167,6 +170,10 @@ __device__ __forceinline__ void read_staged(const float4* tile, unsigned t, floa
     v3 = rot == 0 ? r3 : rot == 1 ? r2 : rot == 2 ? r1 : r0;
 }
 
+__device__ __forceinline__ unsigned long long* key_ptr(const TableView& t, unsigned long long s) {
+    return t.keys + s * t.key_stride;
+}
+
 // ---------------------------------------------------------------------------
 // Cell key: Section "Basis functions and data structures: spatio-directional
 // hashing".  Every decision that yields an integer is taken in FP32 with explicitly
@@ -271,13 +278,13 @@ __device__ __forceinline__ long long probe_claim(const TableView& t, unsigned lo
     const unsigned long long keep = policy_evict_last();
     unsigned long long s = home_slot(t, key);
     for (unsigned i = 0; i < t.max_probe; ++i) {
-        const unsigned long long k = load_key(t.keys + s, keep);
+        const unsigned long long k = load_key(key_ptr(t, s), keep);
         if (k == key) {
             *len = i + 1;
             return static_cast<long long>(s);
         }
         if (k == kEmpty) {
-            const unsigned long long old = atomicCAS(t.keys + s, kEmpty, key);
+            const unsigned long long old = atomicCAS(key_ptr(t, s), kEmpty, key);
             if (old == kEmpty || old == key) {
                 *len = i + 1;
                 return static_cast<long long>(s);
@@ -390,8 +397,8 @@ __device__ __forceinline__ uint2 pack_half4(float a, float b, float c) {
 struct SlotData {
     longlong2 a01;  // sum_r, sum_g
     longlong2 a23;  // sum_b, c_new
+    longlong2 kc;   // key field, c_old
     float4 L;
-    longlong2 co;   // c_old, spare
 };
 
 __device__ __forceinline__ SlotData load_slot(const TableView& t, unsigned long long s) {
@@ -399,8 +406,8 @@ __device__ __forceinline__ SlotData load_slot(const TableView& t, unsigned long 
     SlotData d;
     d.a01 = __ldcg(p);
     d.a23 = __ldcg(p + 1);
-    d.L = __ldcg(reinterpret_cast<const float4*>(p + 2));
-    d.co = __ldcg(p + 3);
+    d.kc = __ldcg(p + 2);
+    d.L = __ldcg(reinterpret_cast<const float4*>(p + 3));
     return d;
 }
 
@@ -411,7 +418,7 @@ __device__ __forceinline__ void blend_store(const TableView& t, unsigned long lo
     const longlong2 z = make_longlong2(0, 0);
     const long long cn = d.a23.y;
     if (cn > 0) {  // always true for a touched slot (accepted vertices add weight >= 1)
-        const long long co = d.co.x;
+        const long long co = d.kc.y;
         const long long ctot = co > (0x7fffffffffffffffll - cn) ? 0x7fffffffffffffffll : co + cn;
         const float fcn = __ll2float_rn(cn);
         float alpha = t.alpha_min;
@@ -420,8 +427,8 @@ __device__ __forceinline__ void blend_store(const TableView& t, unsigned long lo
         d.L.x = fmaf(alpha, __fdiv_rn(__ll2float_rn(d.a01.x), fcn), keep * d.L.x);
         d.L.y = fmaf(alpha, __fdiv_rn(__ll2float_rn(d.a01.y), fcn), keep * d.L.y);
         d.L.z = fmaf(alpha, __fdiv_rn(__ll2float_rn(d.a23.x), fcn), keep * d.L.z);
-        __stcg(reinterpret_cast<float4*>(p + 2), d.L);
-        __stcg(p + 3, make_longlong2(ctot, d.co.y));
+        __stcg(p + 2, make_longlong2(d.kc.x, ctot));  // the key field is written back unchanged
+        __stcg(reinterpret_cast<float4*>(p + 3), d.L);
         if (t.mirror) t.mirror[s] = pack_half4(d.L.x, d.L.y, d.L.z);
     }
     __stcg(p, z);
@@ -513,13 +520,13 @@ __device__ __forceinline__ float3 cell_value(const TableView& t, const float4& v
     const unsigned long long mask = (1ull << t.log2cap) - 1ull;
     const unsigned long long keep = policy_evict_last();
     unsigned long long s = home_slot(t, key);
-    const unsigned long long k0 = load_key(t.keys + s, keep);
+    const unsigned long long k0 = load_key(key_ptr(t, s), keep);
     const float3 c0 = value_at(t, s, fp32_master);
     if (k0 == key) return c0;
     if (k0 == kEmpty) return zero;
     for (unsigned i = 1; i < t.max_probe; ++i) {
         s = (s + 1) & mask;
-        const unsigned long long k = load_key(t.keys + s, keep);
+        const unsigned long long k = load_key(key_ptr(t, s), keep);
         if (k == key) return value_at(t, s, fp32_master);
         if (k == kEmpty) return zero;
     }

@@ -86,9 +86,14 @@ def test_table_bytes_and_config_validation(lib):
     fp16 = _abi.make_config(log2_capacity=16, cache_fp16=True)  # plus the 8-byte FP16 copy
     assert lib.psf_table_bytes(ctypes.byref(fp16)) == n16 + (1 << 16) * 8
     assert lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=17))) > 2 * n16 - 4096
+    # keys inside the slot records: no separate 8-byte key array
+    inl = lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=16, key_layout=2)))
+    assert inl == n16 - (1 << 16) * 8
+    big = [lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=23, key_layout=k))) for k in (0, 1, 2)]
+    assert big[0] == big[2] == big[1] - (1 << 23) * 8  # the automatic choice keeps large tables' keys inline
     for bad in (dict(log2_capacity=3), dict(log2_capacity=31), dict(dir_bits=6), dict(pos_bits=21),
                 dict(frac_bits=7), dict(frac_bits=33), dict(alpha_min=1.5), dict(alpha_min=-0.1),
-                dict(blend_mode=2), dict(beta=float("nan"))):
+                dict(blend_mode=2), dict(beta=float("nan")), dict(key_layout=3)):
         assert lib.psf_table_bytes(ctypes.byref(_abi.make_config(**bad))) == 0, bad
     assert lib.psf_table_bytes(None) == 0
 
@@ -110,7 +115,7 @@ def test_host_detected_argument_errors(lib):
     assert lib.psf_query_cv(None, None, 1, 1, None, None) == _abi.PSF_ERR_INVALID_ARG
     assert lib.psf_reset(None, None) == _abi.PSF_ERR_INVALID_ARG
     assert lib.psf_destroy(None) == _abi.PSF_OK
-    assert lib.psf_abi_version() == 1
+    assert lib.psf_abi_version() == 2
 
 
 def test_product_package_does_not_touch_the_oracle():

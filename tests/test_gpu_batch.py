@@ -22,7 +22,8 @@ def _session(k, w, d):
     log2cap = int(math.ceil(math.log2(v))) + 1
     return dict(name=f"s{k}", width=w, height=h, depth=d, log2_capacity=log2cap,
                 pos_bits=config4_q_bits(log2cap, 3), dir_bits=3, alpha_min=0.1, radiance="glossy",
-                seed=4000 + k, camera_step=0.0, camera_x0=0.5, cache_fp16=bool(k % 2))
+                seed=4000 + k, camera_step=0.0, camera_x0=0.5, cache_fp16=bool(k % 2),
+                key_layout=2 if k % 3 == 2 else 0)  # some tables keep their keys in the slot records
 
 
 def _data(sessions, iterations):
@@ -33,7 +34,8 @@ def _data(sessions, iterations):
 
 def _table(psf, s):
     return psf.Table(psf.make_config(log2_capacity=s["log2_capacity"], pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
-                                      alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"]))
+                                      alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"],
+                                      key_layout=s.get("key_layout", 0)))
 
 
 @pytest.mark.parametrize("insert_mode", [0, 1])

@@ -80,7 +80,8 @@ def test_64x64_depth3_all_iterations(psf_mod, oracle_mod, fp16):
 
 @pytest.mark.parametrize("over", [dict(use_normal=False), dict(blend_mode=1), dict(cv_max_depth=1),
                                   dict(beta=0.5), dict(frac_bits=16), dict(frac_bits=32), dict(dir_bits=5, pos_bits=6),
-                                  dict(dir_bits=0), dict(alpha_min=0.0)])
+                                  dict(dir_bits=0), dict(alpha_min=0.0), dict(key_layout=2),
+                                  dict(key_layout=2, cache_fp16=True)])
 def test_configuration_variants(psf_mod, oracle_mod, over):
     w, batches = _workload_batches("64x64_d3", 3)
     _run_and_compare(psf_mod, oracle_mod, _cfg_for(psf_mod, w, **over), batches, w["width"] * w["height"], w["depth"])
@@ -355,3 +356,27 @@ def test_staged_vertex_tiles_with_ragged_tails(psf_mod, P, D):
         res.append((t.export().tobytes(), np.concatenate(outs).tobytes(), t.stats()["status"]))
         t.close()
     assert res[0] == res[1]
+
+
+@pytest.mark.parametrize("fp16", [False, True])
+def test_key_layouts_give_identical_tables(psf_mod, fp16):
+    """Keys in a dense array or inside the slot records: same slots, same results."""
+    import torch
+
+    w, batches = _workload_batches("64x64_d3", 3)
+    P, D = w["width"] * w["height"], w["depth"]
+    runs = []
+    for layout in (1, 2):
+        t = psf_mod.Table(_cfg_for(psf_mod, w, cache_fp16=fp16, key_layout=layout))
+        outs = []
+        for v in batches:
+            dv = torch.from_numpy(v).cuda()
+            outs.append(t.step(dv, P, D).cpu().numpy())
+            t.insert_progressive(dv, P, D, 0)
+            t.update()
+            outs.append(t.query_biased(dv, P, D, 0.0, 1, 2).cpu().numpy())
+        t.reset()
+        st = t.stats()
+        runs.append((t.export().tobytes(), np.concatenate(outs).tobytes(), st["live_cells"], st["status"]))
+        t.close()
+    assert runs[0] == runs[1]
