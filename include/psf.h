@@ -86,10 +86,10 @@ typedef struct {
     uint32_t cache_fp16;    /* 1: the update also writes an 8-byte FP16 copy of L~ and queries read it
                                (the blend always keeps the FP32 master, which queries read otherwise) */
     uint32_t blend_mode;    /* 0: eq. (11) square-root blend; 1: constant alpha = alpha_min */
-    uint32_t key_layout;    /* where the cell keys live: 1 = a dense 8-byte array (probes stay in L2 for
-                               small tables), 2 = inside each 64-byte slot record (a probe and the
-                               accumulation it leads to touch one memory block, for tables far larger
-                               than L2), 0 = 2 from 2^23 slots up, else 1.  Results do not depend on it. */
+    uint32_t key_layout;    /* where the cell keys live: 1 = a dense 8-byte array, 2 = inside each 64-byte
+                               slot record (a query reads key and approximant from one sector), 0 = 2 up
+                               to 2^22 slots and 1 above (measured: beyond that the dense array keeps
+                               more probes in L2).  Results do not depend on it. */
 } psf_config;
 
 /* One exported cell (psf_export), in ascending key order. */

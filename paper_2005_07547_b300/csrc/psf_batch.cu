@@ -112,67 +112,36 @@ __device__ __forceinline__ unsigned find_item(const unsigned long long* s_begin,
 }
 
 template <int kMode>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads)
     k_batch(BatchCtl* ctl, const BatchHdr* __restrict__ h, const unsigned long long* __restrict__ begin,
             const BatchItemDev* __restrict__ items) {
-    constexpr unsigned kWarps = kThreads / 32;
     __shared__ unsigned long long s_begin[kMaxItems + 1];
     __shared__ psf::LaneSums s_stage[kThreads];
-    __shared__ alignas(128) float4 s_tile[kWarps][2][32 * 4];
-    __shared__ alignas(8) unsigned long long s_bar[kWarps][2];
     psf::LaneSums* stage = s_stage + (threadIdx.x & ~31u);
     const unsigned n = h->n;
     if (n == 0) return;
-    const unsigned lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const unsigned lane = threadIdx.x & 31u;
     const unsigned long long warp = (static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nwarps = (static_cast<unsigned long long>(gridDim.x) * blockDim.x) >> 5;
-    if (lane == 0) {
-        psf::mbar_init(&s_bar[wib][0]);
-        psf::mbar_init(&s_bar[wib][1]);
-        psf::mbar_init_fence();
-    }
 
-    // phase 1: scatter every table's vertices; each warp double-buffers its 2 KB units of
-    // vertex records with bulk copies, like k_insert_staged
+    // phase 1: scatter every table's vertices
     load_begin(s_begin, begin, n);
-    auto issue = [&](unsigned long long u, unsigned buf) {
-        const unsigned it = find_item(s_begin, n, u);
-        const unsigned long long first = (u - s_begin[it]) * 32ull;
-        const unsigned long long nv = items[it].nverts;
-        const unsigned long long cnt = nv - first < 32 ? nv - first : 32;
-        psf::bulk_load(s_tile[wib][buf], items[it].v + 4 * first, static_cast<unsigned>(cnt * 64), &s_bar[wib][buf]);
-    };
-    unsigned long long u = warp;
-    if (lane == 0 && u < h->units[0]) issue(u, 0);
-    bool ok = true, pending_other = false;
-    unsigned k = 0;
-    for (; u < h->units[0]; u += nwarps, ++k) {
-        const unsigned buf = k & 1u;
-        int got = 1;
-        if (lane == 0) {
-            pending_other = u + nwarps < h->units[0];
-            if (pending_other) issue(u + nwarps, buf ^ 1u);
-            got = psf::mbar_wait(&s_bar[wib][buf], (k >> 1) & 1u);
-        }
-        ok = __shfl_sync(psf::kFull, got, 0) != 0;
-        __syncwarp();
-        if (!ok) break;
+    for (unsigned long long u = warp; u < h->units[0]; u += nwarps) {
         const unsigned it = find_item(s_begin, n, u);
         const BatchItemDev& b = items[it];
         const unsigned long long i = (u - s_begin[it]) * 32ull + lane;
         const bool valid = i < b.nverts;
         float4 v0 = make_float4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
-        if (valid) psf::read_staged(s_tile[wib][buf], lane, v0, v1, v2, v3);
+        if (valid) {
+            const float4* r = b.v + 4 * i;
+            v0 = __ldcs(r);
+            v1 = __ldcs(r + 1);
+            v2 = __ldcs(r + 2);
+            v3 = __ldcs(r + 3);
+        }
         unsigned len = 0, leaders = 0;
         psf::insert_warp<kMode>(b.t, valid, v0, v1, v2, v3, &len, stage, &leaders);
         if (len > 16u) atomicMax(&b.t.hdr->max_probe, len);  // only long probes are recorded here
-        __syncwarp();
-    }
-    if (!ok) {
-        if (lane == 0) {
-            atomicOr(&ctl->status, psf::kStatusTimeout);
-            if (pending_other) psf::mbar_wait(&s_bar[wib][(k & 1u) ^ 1u], ((k + 1) >> 1) & 1u);
-        }
     }
     if (!grid_barrier(ctl, h, items)) return;
 

@@ -80,17 +80,17 @@ def test_table_bytes_and_config_validation(lib):
 
     good = _abi.make_config(log2_capacity=16)
     n16 = lib.psf_table_bytes(ctypes.byref(good))
-    # header + 8-byte key + 64-byte slot record per slot + dirty bits
-    assert n16 >= (1 << 16) * (8 + 64) + (1 << 16) // 8
+    # header + 64-byte slot record (key inside, the automatic choice at 2^16 slots) + dirty bits
+    assert n16 >= (1 << 16) * 64 + (1 << 16) // 8
     assert n16 % 256 == 0
     fp16 = _abi.make_config(log2_capacity=16, cache_fp16=True)  # plus the 8-byte FP16 copy
     assert lib.psf_table_bytes(ctypes.byref(fp16)) == n16 + (1 << 16) * 8
     assert lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=17))) > 2 * n16 - 4096
-    # keys inside the slot records: no separate 8-byte key array
-    inl = lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=16, key_layout=2)))
-    assert inl == n16 - (1 << 16) * 8
+    # a dense key array costs 8 bytes per slot more than keys inside the slot records
+    dense = lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=16, key_layout=1)))
+    assert dense == n16 + (1 << 16) * 8  # the automatic choice keeps a 2^16 table's keys inline
     big = [lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=23, key_layout=k))) for k in (0, 1, 2)]
-    assert big[0] == big[2] == big[1] - (1 << 23) * 8  # the automatic choice keeps large tables' keys inline
+    assert big[0] == big[1] == big[2] + (1 << 23) * 8  # and uses the dense array from 2^23 slots
     for bad in (dict(log2_capacity=3), dict(log2_capacity=31), dict(dir_bits=6), dict(pos_bits=21),
                 dict(frac_bits=7), dict(frac_bits=33), dict(alpha_min=1.5), dict(alpha_min=-0.1),
                 dict(blend_mode=2), dict(beta=float("nan")), dict(key_layout=3)):
