@@ -87,9 +87,10 @@ typedef struct {
                                (the blend always keeps the FP32 master, which queries read otherwise) */
     uint32_t blend_mode;    /* 0: eq. (11) square-root blend; 1: constant alpha = alpha_min */
     uint32_t key_layout;    /* where the cell keys live: 1 = a dense 8-byte array, 2 = inside each 64-byte
-                               slot record (a query reads key and approximant from one sector), 0 = 2 up
-                               to 2^22 slots and 1 above (measured: beyond that the dense array keeps
-                               more probes in L2).  Results do not depend on it. */
+                               slot record (an FP32 query reads key and approximant from one sector),
+                               0 = 2 for FP32 tables up to 2^22 slots, else 1 (measured: larger tables
+                               keep more probes in L2 with the dense array, and FP16 queries read the
+                               dense keys beside the compact FP16 copy).  Results do not depend on it. */
 } psf_config;
 
 /* One exported cell (psf_export), in ascending key order. */

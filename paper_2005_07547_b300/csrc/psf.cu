@@ -47,12 +47,13 @@ struct Layout {
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
-// Measured on the B300: with keys in the slot records a query reads key and approximant
-// from one sector (1280x720: 12.8 -> 13.4 G vertices/s at 2^22 slots), but for 2^24 slots a
-// dense 128 MB key array still partly stays in L2 while probes into 1 GB of records all go
-// to DRAM (1920x1080: 7.1 vs 6.25 G vertices/s).
+// Measured on the B300: with keys in the slot records an FP32 query reads key and
+// approximant from one sector (1280x720: 12.8 -> 13.4 G vertices/s at 2^22 slots); for 2^24
+// slots a dense 128 MB key array still partly stays in L2 while probes into 1 GB of records
+// all go to DRAM (1920x1080: 7.1 vs 6.25 G vertices/s); and an FP16 query reads the compact
+// copy, so its keys are best in the dense array beside it (12.95 vs 12.34 G vertices/s).
 bool keys_inline(const psf_config* c) {
-    return c->key_layout == 2 || (c->key_layout == 0 && c->log2_capacity <= 22);
+    return c->key_layout == 2 || (c->key_layout == 0 && c->log2_capacity <= 22 && !c->cache_fp16);
 }
 
 bool config_valid(const psf_config* c) {
