@@ -115,7 +115,7 @@ typedef struct {
     uint64_t table_bytes;          /* psf_table_bytes of the configuration */
     uint64_t touched_cells;        /* cells blended by all psf_update calls so far */
     uint64_t leader_groups;        /* (warp, key) groups that probed and added, all inserts so far
-                                      (each issues four atomics, plus one per touched cell); not counted by batched launches */
+                                      (each issues five atomics); not counted by batched launches */
 } psf_stats;
 
 /* Bytes of device memory a table with this configuration needs (0 if the

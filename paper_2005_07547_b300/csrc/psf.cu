@@ -111,7 +111,6 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* 
     psf::LaneSums* stage = s_stage + (threadIdx.x & ~31u);
     unsigned max_len = 0;
     unsigned leaders = 0;  // counted by lane 0 of each warp
-    psf::PendingTouch pend;
     const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
     // the next tile's records are loaded while the current tile probes and adds
     unsigned long long base = static_cast<unsigned long long>(blockIdx.x) * blockDim.x;
@@ -133,13 +132,12 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* 
             n2 = __ldcs(r + 2);
             n3 = __ldcs(r + 3);
         }
-        psf::insert_warp<kMode>(t, base + threadIdx.x < n, v0, v1, v2, v3, &max_len, stage, &leaders, pend);
+        psf::insert_warp<kMode>(t, base + threadIdx.x < n, v0, v1, v2, v3, &max_len, stage, &leaders);
         v0 = n0;
         v1 = n1;
         v2 = n2;
         v3 = n3;
     }
-    psf::settle(pend);
     if (max_len) atomicMax(&s_max_probe, max_len);
     if ((threadIdx.x & 31u) == 0 && leaders) atomicAdd(&s_leaders, static_cast<unsigned long long>(leaders));
     __syncthreads();
@@ -167,7 +165,6 @@ __global__ void __launch_bounds__(kThreads) k_insert_progressive(TableView t, co
     __syncthreads();
     psf::LaneSums* stage = s_stage + (threadIdx.x & ~31u);
     unsigned max_len = 0, leaders = 0;
-    psf::PendingTouch pend;
     const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
     for (unsigned long long base = static_cast<unsigned long long>(blockIdx.x) * blockDim.x; base < P; base += stride) {
         const unsigned long long p = base + threadIdx.x;
@@ -195,12 +192,11 @@ __global__ void __launch_bounds__(kThreads) k_insert_progressive(TableView t, co
                 val.y = __fmul_rn(v2.w, __fadd_rn(le_next.y, c_next.y));
                 val.z = __fmul_rn(v3.w, __fadd_rn(le_next.z, c_next.z));
             }
-            psf::insert_warp<kMode>(t, valid, v0, v1, v2, val, &max_len, stage, &leaders, pend);
+            psf::insert_warp<kMode>(t, valid, v0, v1, v2, val, &max_len, stage, &leaders);
             c_next = c;
             le_next = le;
         }
     }
-    psf::settle(pend);
     if (max_len) atomicMax(&s_max_probe, max_len);
     if ((threadIdx.x & 31u) == 0 && leaders) atomicAdd(&s_leaders, static_cast<unsigned long long>(leaders));
     __syncthreads();
@@ -243,7 +239,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_insert_staged(TableView t, cons
     };
     psf::LaneSums* stage = s_stage + (threadIdx.x & ~31u);
     unsigned max_len = 0, leaders = 0;
-    psf::PendingTouch pend;
     unsigned long long tile = static_cast<unsigned long long>(blockIdx.x) * kWarpsPerBlock + wib;
     if (lane == 0 && tile < ntiles) issue(tile, 0);
     bool ok = true, pending_other = false;
@@ -264,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_insert_staged(TableView t, cons
         const bool valid = i < n;
         float4 v0 = make_float4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
         if (valid) psf::read_staged(s_tile[wib][buf], lane, v0, v1, v2, v3);
-        psf::insert_warp<kMode>(t, valid, v0, v1, v2, v3, &max_len, stage, &leaders, pend);
+        psf::insert_warp<kMode>(t, valid, v0, v1, v2, v3, &max_len, stage, &leaders);
         __syncwarp();  // the tile is consumed before its buffer is refilled
     }
     if (!ok && lane == 0) {
@@ -272,7 +267,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_insert_staged(TableView t, cons
         // let a copy still in flight land before the warp leaves (bounded)
         if (pending_other) psf::mbar_wait(&s_bar[wib][(k & 1u) ^ 1u], ((k + 1) >> 1) & 1u);
     }
-    psf::settle(pend);
     if (max_len) atomicMax(&s_max_probe, max_len);
     if (lane == 0 && leaders) atomicAdd(&s_leaders, static_cast<unsigned long long>(leaders));
     __syncthreads();

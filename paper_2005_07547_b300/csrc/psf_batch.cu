@@ -126,7 +126,6 @@ __global__ void __launch_bounds__(kThreads)
 
     // phase 1: scatter every table's vertices
     load_begin(s_begin, begin, n);
-    psf::PendingTouch pend;
     for (unsigned long long u = warp; u < h->units[0]; u += nwarps) {
         const unsigned it = find_item(s_begin, n, u);
         const BatchItemDev& b = items[it];
@@ -141,10 +140,9 @@ __global__ void __launch_bounds__(kThreads)
             v3 = __ldcs(r + 3);
         }
         unsigned len = 0, leaders = 0;
-        psf::insert_warp<kMode>(b.t, valid, v0, v1, v2, v3, &len, stage, &leaders, pend);
+        psf::insert_warp<kMode>(b.t, valid, v0, v1, v2, v3, &len, stage, &leaders);
         if (len > 16u) atomicMax(&b.t.hdr->max_probe, len);  // only long probes are recorded here
     }
-    psf::settle(pend);  // every dirty bit is set before the barrier
     if (!grid_barrier(ctl, h, items)) return;
 
     // phase 2: blend every table's touched cells

@@ -296,24 +296,11 @@ __device__ __forceinline__ long long probe_claim(const TableView& t, unsigned lo
     return -1;
 }
 
-// The first touch of a slot in an iteration sets its dirty bit.  The leader's addition to
-// c_new returns the previous value (every accepted vertex adds at least 1, so exactly one
-// addition per touched slot sees 0); the bit is set one scatter later, so the warp never
-// waits on that atomic's round trip.  settle() must run before the blend reads the bits.
-struct PendingTouch {
-    unsigned* word = nullptr;
-    unsigned bit = 0;
-    unsigned long long old = 1;
-};
-
-__device__ __forceinline__ void settle(PendingTouch& p) {
-    if (p.word && p.old == 0ull) atomicOr(p.word, p.bit);
-    p.word = nullptr;
-}
-
 // Leader of a group of lanes holding the same key: probe once, add the group's sums.
+// Every atomic is a reduction whose result is not read (fire and forget); the touched
+// bit is set unconditionally, so no warp waits on an atomic round trip.
 __device__ __forceinline__ void scatter_group(const TableView& t, unsigned long long key, unsigned members,
-                                              const long long sums[4], unsigned* max_len, PendingTouch& pend) {
+                                              const long long sums[4], unsigned* max_len) {
     unsigned len = 0;
     const long long slot = probe_claim(t, key, &len);
     *max_len = len > *max_len ? len : *max_len;
@@ -326,12 +313,8 @@ __device__ __forceinline__ void scatter_group(const TableView& t, unsigned long 
     atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[0]), static_cast<unsigned long long>(sums[0]));
     atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[1]), static_cast<unsigned long long>(sums[1]));
     atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[2]), static_cast<unsigned long long>(sums[2]));
-    const unsigned long long old =
-        atomicAdd(reinterpret_cast<unsigned long long*>(&a->c), static_cast<unsigned long long>(sums[3]));
-    settle(pend);  // the previous scatter's result has had a whole scatter to arrive
-    pend.word = t.dirty + (slot >> 5);
-    pend.bit = 1u << (slot & 31);
-    pend.old = old;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&a->c), static_cast<unsigned long long>(sums[3]));
+    atomicOr(t.dirty + (slot >> 5), 1u << (slot & 31));
 }
 
 // Per-warp staging of the lanes' sums for the donor merge (32 B per lane).
@@ -348,7 +331,7 @@ struct alignas(16) LaneSums {
 template <int kMode>
 __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, const float4& v0, const float4& v1,
                                             const float4& v2, const float4& v3, unsigned* max_len,
-                                            LaneSums* stage, unsigned* leaders, PendingTouch& pend) {
+                                            LaneSums* stage, unsigned* leaders) {
     const unsigned lane = threadIdx.x & 31u;
     unsigned long long key = 0;
     long long sums[4] = {0, 0, 0, 0};
@@ -370,7 +353,7 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
         if (zero_w) atomicAdd(&t.hdr->zero_weight, static_cast<unsigned long long>(__popc(zero_w)));
     }
     if (kMode == kAggNone) {
-        if (cls == 1) scatter_group(t, key, 1u << lane, sums, max_len, pend);
+        if (cls == 1) scatter_group(t, key, 1u << lane, sums, max_len);
         *leaders += __popc(accepted);
         return;
     }
@@ -393,7 +376,7 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
         }
         __syncwarp();
     }
-    if (cls == 1 && !donor) scatter_group(t, key, group, sums, max_len, pend);
+    if (cls == 1 && !donor) scatter_group(t, key, group, sums, max_len);
     *leaders += __popc(__ballot_sync(kFull, cls == 1 && !donor));
 }
 
