@@ -442,13 +442,15 @@ def run_psf(args) -> None:
     achieved = alg[dominant] / (avg[dominant] / 1e3) / 1e9
     # atomic roofline of the insert: 5 atomics per (warp, key) group against the probe's rate
     # for the same pattern (4 reductions into one random 32-byte sector + 1 bitmap reduction)
-    probe = atomic_probe_rates(modes=(2,)) if rank == 0 else {}
+    probe_words = 8 << w["log2_capacity"]  # a buffer the size of the table's 64-byte slot records
+    probe = atomic_probe_rates(modes=(2,), n_words=probe_words) if rank == 0 else {}
     atom_rate = 5.0 * leaders / (avg["k_insert"] / 1e3)
     atomic_roofline = {"kernel": "k_insert", "achieved": atom_rate / 1e9, "unit": "G atomics/s",
                        "peak": probe.get("insert_pattern_4red_1or", float("nan")) / 1e9,
                        "frac": atom_rate / probe["insert_pattern_4red_1or"] if probe else None,
                        "atomics_per_launch": 5.0 * leaders, "leader_groups_per_launch": leaders,
-                       "peak_source": "live probe: 4 x red.add.u64 into one random 32-B sector + red.or, 256 MB"}
+                       "peak_source": f"live probe: 4 x red.add.u64 into one random 32-B sector + red.or, "
+                                      f"{probe_words * 8 / 1e6:.0f} MB (the slot records)"}
     kernels = {k: {"avg_ms": avg[k], "share": avg[k] / sum(avg.values()),
                    "algorithmic_GBps": alg[k] / (avg[k] / 1e3) / 1e9,
                    "frac_of_hbm": alg[k] / (avg[k] / 1e3) / 1e9 / peaks["hbm_gbs"]} for k in avg}
