@@ -29,7 +29,8 @@ class _Config(ctypes.Structure):
     _fields_ = [("pos_bits_q", ctypes.c_uint32), ("dir_bits_d", ctypes.c_uint32),
                 ("use_normal", ctypes.c_uint32), ("frac_bits", ctypes.c_uint32),
                 ("blend_mode", ctypes.c_uint32), ("cv_max_depth", ctypes.c_uint32),
-                ("alpha_min", ctypes.c_double), ("beta", ctypes.c_double)]
+                ("alpha_min", ctypes.c_double), ("beta", ctypes.c_double), ("levels", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +58,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_destroy.argtypes = [vp]
         L.oracle_key.restype = ctypes.c_int
         L.oracle_key.argtypes = [ctypes.POINTER(_Config), vp, ctypes.POINTER(u64)]
+        L.oracle_key_at.restype = ctypes.c_int
+        L.oracle_key_at.argtypes = [ctypes.POINTER(_Config), vp, u32, ctypes.POINTER(u64)]
         L.oracle_insert.restype = u32
         L.oracle_insert.argtypes = [vp, vp, u64]
         L.oracle_insert_progressive.restype = u32
@@ -66,6 +69,7 @@ def lib() -> ctypes.CDLL:
         L.oracle_reset.argtypes = [vp]
         L.oracle_query_cv.argtypes = [vp, vp, u32, u32, vp]
         L.oracle_lookup.argtypes = [vp, vp, u64, vp]
+        L.oracle_lookup_paths.argtypes = [vp, vp, u32, u32, vp]
         L.oracle_query_biased.argtypes = [vp, vp, u32, u32, ctypes.c_double, u32, u32, vp]
         L.oracle_size.restype = u64
         L.oracle_size.argtypes = [vp]
@@ -79,9 +83,9 @@ def lib() -> ctypes.CDLL:
 
 def make_config(pos_bits: int = 4, dir_bits: int = 2, use_normal: bool = True, frac_bits: int = 24,
                 blend_mode: int = 0, cv_max_depth: int = 0xFFFFFFFF, alpha_min: float = 0.1,
-                beta: float = 1.0) -> _Config:
+                beta: float = 1.0, levels: int = 1) -> _Config:
     return _Config(pos_bits, dir_bits, int(bool(use_normal)), frac_bits, blend_mode, cv_max_depth,
-                   float(alpha_min), float(beta))
+                   float(alpha_min), float(beta), levels, 0)
 
 
 def _verts(v: np.ndarray) -> np.ndarray:
@@ -91,11 +95,15 @@ def _verts(v: np.ndarray) -> np.ndarray:
     return v
 
 
-def vertex_key(cfg: _Config, v16) -> int | None:
-    """Packed cell key of one vertex record, or None if the vertex has no valid cell."""
+def vertex_key(cfg: _Config, v16, level: int = 0) -> int | None:
+    """Packed cell key of one vertex record at a hierarchy level, or None if the vertex has
+    no valid cell."""
     v = np.ascontiguousarray(v16, dtype=np.float32).reshape(16)
     out = ctypes.c_uint64()
-    ok = lib().oracle_key(ctypes.byref(cfg), v.ctypes.data, ctypes.byref(out))
+    if level == 0:
+        ok = lib().oracle_key(ctypes.byref(cfg), v.ctypes.data, ctypes.byref(out))
+    else:
+        ok = lib().oracle_key_at(ctypes.byref(cfg), v.ctypes.data, level, ctypes.byref(out))
     return int(out.value) if ok else None
 
 
@@ -148,11 +156,15 @@ class Oracle:
         lib().oracle_query_biased(self._h, v.ctypes.data, P, D, float(gamma), j_begin, j_end, out.ctypes.data)
         return out
 
-    def lookup(self, verts: np.ndarray) -> np.ndarray:
-        """(n, 3) approximant of each vertex's cell, 0 where the cell is absent."""
+    def lookup(self, verts: np.ndarray, P: int | None = None, D: int | None = None) -> np.ndarray:
+        """(n, 3) approximant of each vertex's cell, 0 where the cell is absent; given P and D
+        (depth-major paths) vertex j reads the level a query reads, min(j, levels - 1)."""
         v = _verts(verts)
         out = np.empty((v.shape[0], 3), dtype=np.float64)
-        lib().oracle_lookup(self._h, v.ctypes.data, v.shape[0], out.ctypes.data)
+        if P is None:
+            lib().oracle_lookup(self._h, v.ctypes.data, v.shape[0], out.ctypes.data)
+        else:
+            lib().oracle_lookup_paths(self._h, v.ctypes.data, P, D, out.ctypes.data)
         return out
 
     def __len__(self) -> int:

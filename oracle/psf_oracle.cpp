@@ -22,7 +22,10 @@
 //     estimator-value form out = L - beta * (t * C_next) + beta * C_self;
 //   * biased query: Section "Biased estimation", equation BiasedEstimator,
 //     out = gamma * (L - t * C_next) + C_self;
-//   * progressive update values: Section "Progressive solver", eq. (9), Alg. 1 and 2.
+//   * progressive update values: Section "Progressive solver", eq. (9), Alg. 1 and 2;
+//   * hierarchy levels: Section "Progressive hierarchical solver" (cells 2^l times wider at
+//     level l; the level a vertex reads follows its path depth -- a reading, the paper's
+//     footprint heuristic is only cited).
 //
 // Precision: the decisions that produce integers (cell indices, direction bins,
 // fixed-point codes) are taken in FP32 with one correctly rounded IEEE operation
@@ -56,6 +59,8 @@ struct Config {
     uint32_t cv_max_depth;
     double alpha_min;
     double beta;
+    uint32_t levels;      // hierarchy levels (Section "Progressive hierarchical solver"); 0 or 1 = flat
+    uint32_t pad;
 };
 
 // (level, normal bin, direction bin u, direction bin v, cell x, cell y, cell z);
@@ -127,8 +132,10 @@ bool direction_bins(float wx, float wy, float wz, uint32_t d, uint32_t* bu, uint
     return true;
 }
 
-// The basis function b_h a vertex lands on (a single cell: b_h is an indicator).
-bool vertex_cell(const Config& c, const float* v, CellKey* key) {
+// The basis function b_h a vertex lands on at hierarchy level `level` (a single cell: b_h is
+// an indicator).  Level l uses cells 2^l times wider: index floor(p * 2^(q - l)); a vertex
+// has a cell at every level exactly when it has one at level 0.
+bool vertex_cell(const Config& c, const float* v, CellKey* key, uint32_t level = 0) {
     const float* p = v;
     const float* n = v + 4;
     const float* d = v + 8;
@@ -137,12 +144,31 @@ bool vertex_cell(const Config& c, const float* v, CellKey* key) {
     if (!cell_index(p[0], c.pos_bits_q, &bx) || !cell_index(p[1], c.pos_bits_q, &by) ||
         !cell_index(p[2], c.pos_bits_q, &bz))
         return false;
+    if (level > 0) {
+        const int q = static_cast<int>(c.pos_bits_q) - static_cast<int>(level);
+        auto coarse = [q](float x) {
+            return static_cast<uint32_t>(static_cast<int64_t>(std::floor(static_cast<double>(x) * std::ldexp(1.0, q))) + 32768);
+        };
+        bx = coarse(p[0]);
+        by = coarse(p[1]);
+        bz = coarse(p[2]);
+    }
     uint32_t nb = c.use_normal ? normal_bin(n[0], n[1], n[2]) : 0u;
     uint32_t bu, bv;
     // omega_o = -d (Alg. 1: the outgoing direction is the reversed incoming ray)
     if (!direction_bins(-d[0], -d[1], -d[2], c.dir_bits_d, &bu, &bv)) return false;
-    *key = CellKey(0u, nb, bu, bv, bx, by, bz);
+    *key = CellKey(level, nb, bu, bv, bx, by, bz);
     return true;
+}
+
+uint32_t level_count(const Config& c) { return c.levels == 0 ? 1u : c.levels; }
+
+// The level a vertex at path depth j reads (Section "Progressive hierarchical solver": the
+// level follows the path's footprint).  Reading: the footprint widens with every bounce, so
+// vertex j reads level min(j, levels - 1); a flat table reads level 0.
+uint32_t read_level(const Config& c, int64_t j) {
+    const int64_t top = static_cast<int64_t>(level_count(c)) - 1;
+    return static_cast<uint32_t>(j < top ? j : top);
 }
 
 uint64_t pack_key(const Config& c, const CellKey& k) {
@@ -171,6 +197,8 @@ typedef struct {
     uint32_t cv_max_depth;
     double alpha_min;
     double beta;
+    uint32_t levels;
+    uint32_t pad;
 } oracle_config;
 
 typedef struct {
@@ -182,7 +210,8 @@ typedef struct {
 } oracle_record;
 
 void* oracle_create(const oracle_config* cfg) {
-    if (!cfg || cfg->dir_bits_d > 5 || cfg->pos_bits_q > 20 || cfg->frac_bits < 8 || cfg->frac_bits > 32)
+    if (!cfg || cfg->dir_bits_d > 5 || cfg->pos_bits_q > 20 || cfg->frac_bits < 8 || cfg->frac_bits > 32 ||
+        cfg->levels > 4)
         return nullptr;
     Oracle* o = new Oracle();
     std::memcpy(&o->cfg, cfg, sizeof(Config));
@@ -197,6 +226,16 @@ int oracle_key(const oracle_config* cfg, const float* v, uint64_t* key) {
     std::memcpy(&c, cfg, sizeof(Config));
     CellKey k;
     if (!vertex_cell(c, v, &k)) return 0;
+    *key = pack_key(c, k);
+    return 1;
+}
+
+// As oracle_key, for the vertex's cell at hierarchy level `level` (< 4).
+int oracle_key_at(const oracle_config* cfg, const float* v, uint32_t level, uint64_t* key) {
+    Config c;
+    std::memcpy(&c, cfg, sizeof(Config));
+    CellKey k;
+    if (level > 3 || !vertex_cell(c, v, &k, level)) return 0;
     *key = pack_key(c, k);
     return 1;
 }
@@ -228,9 +267,12 @@ uint32_t oracle_insert(void* h, const float* verts, uint64_t n) {
             o->zero_weight++;
             continue;
         }
-        Cell& cell = o->cells[key];
-        for (int ch = 0; ch < 3; ++ch) cell.sum[ch] += std::llrint(static_cast<double>(prod[ch]) * scale);
-        cell.c_new += cw;
+        for (uint32_t l = 0; l < level_count(c); ++l) {  // every level's cell receives the vertex
+            vertex_cell(c, v, &key, l);
+            Cell& cell = o->cells[key];
+            for (int ch = 0; ch < 3; ++ch) cell.sum[ch] += std::llrint(static_cast<double>(prod[ch]) * scale);
+            cell.c_new += cw;
+        }
     }
     return status;
 }
@@ -258,7 +300,7 @@ uint32_t oracle_insert_progressive(void* h, const float* verts, uint32_t P, uint
             const double t[3] = {v[7], v[11], v[15]};
             double C[3] = {0.0, 0.0, 0.0};
             CellKey key;
-            if (vertex_cell(c, v, &key)) {
+            if (vertex_cell(c, v, &key, read_level(c, j))) {
                 auto it = o->cells.find(key);
                 if (it != o->cells.end())
                     for (int ch = 0; ch < 3; ++ch) C[ch] = it->second.L[ch];
@@ -293,9 +335,12 @@ uint32_t oracle_insert_progressive(void* h, const float* verts, uint32_t P, uint
             o->zero_weight++;
             continue;
         }
-        Cell& cell = o->cells[key];
-        for (int ch = 0; ch < 3; ++ch) cell.sum[ch] += std::llrint(prod[ch] * scale);
-        cell.c_new += cw;
+        for (uint32_t l = 0; l < level_count(c); ++l) {
+            vertex_cell(c, v, &key, l);
+            Cell& cell = o->cells[key];
+            for (int ch = 0; ch < 3; ++ch) cell.sum[ch] += std::llrint(prod[ch] * scale);
+            cell.c_new += cw;
+        }
     }
     return status;
 }
@@ -347,7 +392,7 @@ void oracle_query_cv(void* h, const float* verts, uint32_t P, uint32_t D, double
             const float* v = verts + 16 * idx;
             double C[3] = {0.0, 0.0, 0.0};
             CellKey key;
-            if (vertex_cell(c, v, &key)) {
+            if (vertex_cell(c, v, &key, read_level(c, j))) {
                 auto it = o->cells.find(key);
                 if (it != o->cells.end())
                     for (int ch = 0; ch < 3; ++ch) C[ch] = it->second.L[ch];
@@ -379,7 +424,7 @@ void oracle_query_biased(void* h, const float* verts, uint32_t P, uint32_t D, do
             const float* v = verts + 16 * idx;
             double C[3] = {0.0, 0.0, 0.0};
             CellKey key;
-            if (vertex_cell(c, v, &key)) {
+            if (vertex_cell(c, v, &key, read_level(c, j))) {
                 auto it = o->cells.find(key);
                 if (it != o->cells.end())
                     for (int ch = 0; ch < 3; ++ch) C[ch] = it->second.L[ch];
@@ -409,6 +454,23 @@ void oracle_lookup(void* h, const float* verts, uint64_t n, double* C_out) {
         if (it != o->cells.end())
             for (int ch = 0; ch < 3; ++ch) C[ch] = it->second.L[ch];
     }
+}
+
+// As oracle_lookup for P paths of depth D (depth-major): vertex j reads its cell at the level
+// min(j, levels - 1), as the queries do.
+void oracle_lookup_paths(void* h, const float* verts, uint32_t P, uint32_t D, double* C_out) {
+    Oracle* o = static_cast<Oracle*>(h);
+    for (uint64_t j = 0; j < D; ++j)
+        for (uint64_t p = 0; p < P; ++p) {
+            const uint64_t i = j * P + p;
+            double* C = C_out + 3 * i;
+            C[0] = C[1] = C[2] = 0.0;
+            CellKey key;
+            if (!vertex_cell(o->cfg, verts + 16 * i, &key, read_level(o->cfg, static_cast<int64_t>(j)))) continue;
+            auto it = o->cells.find(key);
+            if (it != o->cells.end())
+                for (int ch = 0; ch < 3; ++ch) C[ch] = it->second.L[ch];
+        }
 }
 
 uint64_t oracle_size(void* h) { return static_cast<Oracle*>(h)->cells.size(); }

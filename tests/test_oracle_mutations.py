@@ -13,7 +13,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "psf_oracle.cpp")
-PINS = ["tests/test_oracle_keys.py", "tests/test_oracle_accumulate.py", "tests/test_oracle_cv.py"]
+PINS = ["tests/test_oracle_keys.py", "tests/test_oracle_accumulate.py", "tests/test_oracle_cv.py",
+        "tests/test_oracle_levels.py"]
 
 MUTANTS = {
     "cv_sign_of_control": ("L - c.beta * (t[ch] * C_next[ch]) + c.beta * C[ch]",
@@ -42,6 +43,15 @@ MUTANTS = {
     "packed_axes_swapped": ("(bx << 32) | (by << 16) | bz", "(bz << 32) | (by << 16) | bx"),
     "biased_gamma_on_approximant": ("gamma * (L - t[ch] * C_next[ch]) + C[ch]", "(L - t[ch] * C_next[ch]) + gamma * C[ch]"),
     "biased_corrector_sign": ("gamma * (L - t[ch] * C_next[ch]) + C[ch]", "gamma * (L + t[ch] * C_next[ch]) + C[ch]"),
+    "level_read_one_deeper": ("return static_cast<uint32_t>(j < top ? j : top);",
+                              "return static_cast<uint32_t>(j + 1 < top ? j + 1 : top);"),
+    "level_coarse_truncates": ("std::floor(static_cast<double>(x) * std::ldexp(1.0, q))",
+                               "std::trunc(static_cast<double>(x) * std::ldexp(1.0, q))"),
+    "level_coarse_finer": ("static_cast<int>(c.pos_bits_q) - static_cast<int>(level)",
+                           "static_cast<int>(c.pos_bits_q) + static_cast<int>(level)"),
+    "level_bits_dropped": ("*key = CellKey(level, nb,", "*key = CellKey(0u, nb,"),
+    "insert_level_zero_only": ("l < level_count(c); ++l) {  // every level's cell receives the vertex",
+                               "l < 1; ++l) {  // every level's cell receives the vertex"),
 }
 
 
