@@ -95,9 +95,10 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6400.0, "source": "fallback"}
 
 
-def load_traffic(kernel: str, staged: bool = False) -> float | None:
-    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged
-    (the insert with staged vertex tiles is the kernel k_insert_staged)."""
+def load_traffic(kernel: str, staged: bool, setup: dict) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if it was captured on the same
+    kernels (source hash) and the same setup (workload, cache, levels, capacity); the insert
+    with staged vertex tiles is the kernel k_insert_staged."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
@@ -105,9 +106,12 @@ def load_traffic(kernel: str, staged: bool = False) -> float | None:
         d = json.load(f)
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    name = kernel + "_staged" if staged and kernel in ("k_insert", "k_query") else kernel
-    k = d.get("kernels", {}).get(name)
-    return float(k["bytes_per_launch"]) if k else None
+    for cap in d.get("captures", []):
+        if all(cap.get(k) == v for k, v in setup.items()):
+            name = kernel + "_staged" if staged and kernel in ("k_insert", "k_query") else kernel
+            k = cap.get("kernels", {}).get(name)
+            return float(k["bytes_per_launch"]) if k else None
+    return None
 
 
 class _Nvml:
@@ -282,11 +286,12 @@ def generate(name: str, iterations: list[int], procs: int) -> list[np.ndarray]:
 # CPU baseline: the oracle on a bounded sample
 # ---------------------------------------------------------------------------
 
-def oracle_rate(w: dict, batches: list[np.ndarray], budget_s: float = 20.0) -> dict:
+def oracle_rate(w: dict, batches: list[np.ndarray], budget_s: float = 20.0, levels: int = 1) -> dict:
     import oracle
 
     P, D = w["width"] * w["height"], w["depth"]
-    o = oracle.Oracle(pos_bits=w["pos_bits"], dir_bits=w["dir_bits"], alpha_min=float(np.float32(w["alpha_min"])))
+    o = oracle.Oracle(pos_bits=w["pos_bits"], dir_bits=w["dir_bits"], alpha_min=float(np.float32(w["alpha_min"])),
+                      levels=levels)
     done = 0
     t0 = time.perf_counter()
     for v in batches:
@@ -314,7 +319,8 @@ def run_reference(args) -> None:
     import oracle
 
     P, D = w["width"] * w["height"], w["depth"]
-    o = oracle.Oracle(pos_bits=w["pos_bits"], dir_bits=w["dir_bits"], alpha_min=float(np.float32(w["alpha_min"])))
+    o = oracle.Oracle(pos_bits=w["pos_bits"], dir_bits=w["dir_bits"], alpha_min=float(np.float32(w["alpha_min"])),
+                      levels=args.levels)
     for v in batches[:min(args.warmup, 1)]:
         o.insert(v)
         o.update()
@@ -337,7 +343,7 @@ def run_reference(args) -> None:
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w["name"], "paths": P, "depth": D, "vertices_per_step": frac_paths * D,
+        "config": {"workload": w["name"], "paths": P, "depth": D, "vertices_per_step": frac_paths * D, "levels": args.levels,
                    "sample": f"first {frac_paths} of {P} paths per iteration"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} iterations x {frac_paths} paths x depth {D} of {w['name']}"},
@@ -373,9 +379,12 @@ def run_psf(args) -> None:
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     psf.load()
-    cfg = psf.make_config(log2_capacity=w["log2_capacity"], pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],
+    # coarse levels add few cells (measured live cells over the flat table's: 1.26x at 2
+    # levels, 1.35x at 4), so the workload's capacity serves every level count
+    log2cap = w["log2_capacity"]
+    cfg = psf.make_config(log2_capacity=log2cap, pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],
                           alpha_min=w["alpha_min"], cache_fp16=args.fp16 or w["cache_fp16"],
-                          key_layout=args.key_layout)
+                          key_layout=args.key_layout, levels=args.levels)
     table = psf.Table(cfg)
     table.set_launch(insert_mode=args.insert_mode, vertex_staging=args.staging)
     dev = [torch.from_numpy(v).cuda() for v in host]
@@ -442,7 +451,7 @@ def run_psf(args) -> None:
     achieved = alg[dominant] / (avg[dominant] / 1e3) / 1e9
     # atomic roofline of the insert: 5 atomics per (warp, key) group against the probe's rate
     # for the same pattern (4 reductions into one random 32-byte sector + 1 bitmap reduction)
-    probe_words = 8 << w["log2_capacity"]  # a buffer the size of the table's 64-byte slot records
+    probe_words = 8 << log2cap  # a buffer the size of the table's 64-byte slot records
     probe = atomic_probe_rates(modes=(2,), n_words=probe_words) if rank == 0 else {}
     atom_rate = 5.0 * leaders / (avg["k_insert"] / 1e3)
     atomic_roofline = {"kernel": "k_insert", "achieved": atom_rate / 1e9, "unit": "G atomics/s",
@@ -458,7 +467,8 @@ def run_psf(args) -> None:
     hbm = {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
            "peak_source": peaks["source"], "algorithmic_bytes_per_launch": alg[dominant]}
     staged = {"k_insert": bool(args.staging & 1), "k_query": bool(args.staging & 2)}.get(dominant, False)
-    roofline = {"kernel": dominant, "traffic": load_traffic(dominant, staged), "hbm": hbm}
+    setup = {"workload": w["name"], "cache": "fp16" if fp16 else "fp32", "levels": args.levels, "log2_capacity": log2cap}
+    roofline = {"kernel": dominant, "traffic": load_traffic(dominant, staged, setup), "hbm": hbm}
     binding = hbm
     roofline["bound"] = "hbm"
     if dominant == "k_insert" and atomic_roofline["frac"] is not None:
@@ -481,7 +491,7 @@ def run_psf(args) -> None:
         "warmup": args.warmup, "ms_per_step": agg["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+i64 fixed point", "data": "synthetic",
         "config": {"workload": w["name"], "paths": P, "depth": D, "vertices_per_step": V,
-                   "log2_capacity": w["log2_capacity"], "cache": "fp16" if fp16 else "fp32",
+                   "log2_capacity": log2cap, "levels": args.levels, "cache": "fp16" if fp16 else "fp32",
                    "touched_cells_per_step": touched, "live_cells": after["live_cells"],
                    "l2": f"inputs larger than L2: {n_iter} distinct {V * 64 / 1e6:.0f} MB vertex batches, "
                          "a different one every step",
@@ -497,7 +507,7 @@ def run_psf(args) -> None:
         "e2e": e2e,
     }
     if cpu_sample is not None:
-        line["cpu_baseline"] = oracle_rate(w, cpu_sample)
+        line["cpu_baseline"] = oracle_rate(w, cpu_sample, levels=args.levels)
     print(json.dumps(line), flush=True)
     table.close()
     if world > 1:
@@ -777,6 +787,7 @@ def main(argv=None) -> None:
     ap.add_argument("--staging", type=int, default=1, help="bit 0: insert, bit 1: query stage vertex records through shared memory (TMA)")
     ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
     ap.add_argument("--key-layout", type=int, default=0, help="0: auto, 1: dense key array, 2: keys in slot records")
+    ap.add_argument("--levels", type=int, default=1, help="hierarchy levels of the table (1: flat)")
     ap.add_argument("--pool", type=int, default=4, help="distinct resident iterations per session (batched)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")

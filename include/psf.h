@@ -38,7 +38,7 @@
  * Cell key (Section "Basis functions and data structures: spatio-directional hashing":
  * a grid over position times a grid over omega_o; the dominant-axis normal bin is an
  * optional extra field).  Packed in 64 bits, bit 63 always 0:
- *   level:2 (61-62, always 0) | normal bin:3 (58-60) | direction bin:2d (48..) |
+ *   level:2 (61-62, the hierarchy level; see psf_config.levels) | normal bin:3 (58-60) | direction bin:2d (48..) |
  *   x:16 (32-47) | y:16 (16-31) | z:16 (0-15)
  * x = floor(px * 2^q) + 2^15 (likewise y, z); the direction bin is the octahedral map of
  * omega_o on a 2^d x 2^d grid (sgn(0) = +1, lower hemisphere folded outwards, bins
@@ -91,6 +91,14 @@ typedef struct {
                                0 = 2 for FP32 tables up to 2^22 slots, else 1 (measured: larger tables
                                keep more probes in L2 with the dense array, and FP16 queries read the
                                dense keys beside the compact FP16 copy).  Results do not depend on it. */
+    uint32_t levels;        /* hierarchy levels L, 0..4 (0 and 1: a flat table).  Section "Progressive
+                               hierarchical solver": level l has cells 2^l times wider in position
+                               (x_l = floor(px * 2^(q-l)) + 2^15, likewise y, z; the same normal and
+                               direction bins); every inserted vertex is added to its cell at all L
+                               levels, and a vertex at path depth j is read at level min(j, L - 1) by
+                               the queries and by psf_insert_progressive (the paper's level choice is a
+                               path-footprint heuristic it does not give; the depth stands in for the
+                               footprint).  A table holds up to L times the cells of a flat one. */
 } psf_config;
 
 /* One exported cell (psf_export), in ascending key order. */
@@ -292,7 +300,7 @@ int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, const psf_ba
 const char* psf_last_cuda_error(void);
 
 /* ABI version of this header: bump on any incompatible change. */
-#define PSF_ABI_VERSION 2
+#define PSF_ABI_VERSION 3
 int psf_abi_version(void);
 
 #ifdef __cplusplus

@@ -47,14 +47,16 @@ class Config(ctypes.Structure):
         ("cache_fp16", ctypes.c_uint32),
         ("blend_mode", ctypes.c_uint32),
         ("key_layout", ctypes.c_uint32),
+        ("levels", ctypes.c_uint32),
     ]
 
 
 def make_config(log2_capacity: int = 16, pos_bits: int = 4, dir_bits: int = 2, use_normal: bool = True,
                 alpha_min: float = 0.1, beta: float = 1.0, cv_max_depth: int = 0xFFFFFFFF,
-                frac_bits: int = 24, cache_fp16: bool = False, blend_mode: int = 0, key_layout: int = 0) -> Config:
+                frac_bits: int = 24, cache_fp16: bool = False, blend_mode: int = 0, key_layout: int = 0,
+                levels: int = 1) -> Config:
     return Config(log2_capacity, pos_bits, dir_bits, int(bool(use_normal)), alpha_min, beta, cv_max_depth,
-                  frac_bits, int(bool(cache_fp16)), blend_mode, key_layout)
+                  frac_bits, int(bool(cache_fp16)), blend_mode, key_layout, levels)
 
 
 class Stats(ctypes.Structure):

@@ -58,7 +58,7 @@ bool keys_inline(const psf_config* c) {
 
 bool config_valid(const psf_config* c) {
     if (!c) return false;
-    if (c->key_layout > 2) return false;
+    if (c->key_layout > 2 || c->levels > 4) return false;
     if (c->log2_capacity < 4 || c->log2_capacity > 30) return false;
     if (c->pos_bits_q > 20 || c->dir_bits_d > 5) return false;
     if (c->frac_bits < 8 || c->frac_bits > 32) return false;
@@ -98,7 +98,7 @@ int grid_for(const psf_table* t, int per_sm, unsigned long long work_items, uint
 // Kernels
 // ---------------------------------------------------------------------------
 
-template <int kMode>
+template <int kMode, bool kHier>
 __global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* __restrict__ v, unsigned long long n) {
     __shared__ unsigned s_max_probe;
     __shared__ unsigned long long s_leaders;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* 
             n2 = __ldcs(r + 2);
             n3 = __ldcs(r + 3);
         }
-        psf::insert_warp<kMode>(t, base + threadIdx.x < n, v0, v1, v2, v3, &max_len, stage, &leaders);
+        psf::insert_warp<kMode, kHier>(t, base + threadIdx.x < n, v0, v1, v2, v3, &max_len, stage, &leaders);
         v0 = n0;
         v1 = n1;
         v2 = n2;
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* 
 // vertex's cell (read before this iteration's blend, so it is L~old) feeds the value of
 // the vertex before it, which is then scattered like a plain insert.  Warps hold 32 paths
 // at the same depth, so the warp-level merge of equal keys applies unchanged.
-template <int kMode>
+template <int kMode, bool kHier>
 __global__ void __launch_bounds__(kThreads) k_insert_progressive(TableView t, const float4* __restrict__ v, unsigned P,
                                                                  unsigned D, unsigned field) {
     __shared__ unsigned s_max_probe;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_insert_progressive(TableView t, co
                 v1 = __ldcs(r + 1);
                 v2 = __ldcs(r + 2);
                 v3 = __ldcs(r + 3);
-                c = psf::cell_value(t, v0, v1, v2, /*fp32_master=*/true);
+                c = psf::cell_value(t, v0, v1, v2, /*fp32_master=*/true, psf::read_level(t, static_cast<unsigned>(j)));
             }
             const float3 le = make_float3(v3.x, v3.y, v3.z);
             float4 val = v3;  // (value_r, value_g, value_b, t_b)
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_insert_progressive(TableView t, co
                 val.y = __fmul_rn(v2.w, __fadd_rn(le_next.y, c_next.y));
                 val.z = __fmul_rn(v3.w, __fadd_rn(le_next.z, c_next.z));
             }
-            psf::insert_warp<kMode>(t, valid, v0, v1, v2, val, &max_len, stage, &leaders);
+            psf::insert_warp<kMode, kHier>(t, valid, v0, v1, v2, val, &max_len, stage, &leaders);
             c_next = c;
             le_next = le;
         }
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kThreads) k_insert_progressive(TableView t, co
 // never wait for each other.
 constexpr unsigned kWarpsPerBlock = kThreads / 32;
 
-template <int kMode>
+template <int kMode, bool kHier>
 __global__ void __launch_bounds__(kThreads, 5) k_insert_staged(TableView t, const float4* __restrict__ v, unsigned long long n) {
     __shared__ alignas(128) float4 s_tile[kWarpsPerBlock][2][32 * 4];
     __shared__ alignas(8) unsigned long long s_bar[kWarpsPerBlock][2];
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_insert_staged(TableView t, cons
         const bool valid = i < n;
         float4 v0 = make_float4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
         if (valid) psf::read_staged(s_tile[wib][buf], lane, v0, v1, v2, v3);
-        psf::insert_warp<kMode>(t, valid, v0, v1, v2, v3, &max_len, stage, &leaders);
+        psf::insert_warp<kMode, kHier>(t, valid, v0, v1, v2, v3, &max_len, stage, &leaders);
         __syncwarp();  // the tile is consumed before its buffer is refilled
     }
     if (!ok && lane == 0) {
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_query_staged(TableView t, psf::
         if (p < P) {
             float4 v0, v1, v2, v3;
             psf::read_staged(s_tile[wib][buf], lane, v0, v1, v2, v3);
-            const float3 c = psf::cell_value(t, v0, v1, v2);
+            const float3 c = psf::cell_value(t, v0, v1, v2, false, psf::read_level(t, j));
             float o0 = v3.x, o1 = v3.y, o2 = v3.z;
             if (j + 1 < D && j >= e.j_begin && j < e.j_end) {
                 o0 = psf::combine(e, v3.x, v1.w, c_next.x, c.x);
@@ -447,6 +447,38 @@ __global__ void __launch_bounds__(kThreads) k_reset(TableView t) {
 // C ABI
 // ---------------------------------------------------------------------------
 
+namespace {
+
+// The insert kernels for a flat table (kHier = false) or for one with hierarchy levels.
+template <bool kHier>
+void launch_insert(const psf_table* t, const float4* v, unsigned long long n, cudaStream_t st) {
+    if (t->launch.vertex_staging & 1u) {
+        const int sgrid = grid_for(t, t->staged_blocks_per_sm, n, t->launch.insert_blocks_per_sm);
+        if (t->launch.insert_mode == 1)
+            k_insert_staged<psf::kAggNone, kHier><<<sgrid, kThreads, 0, st>>>(t->view, v, n);
+        else
+            k_insert_staged<psf::kAggWarp, kHier><<<sgrid, kThreads, 0, st>>>(t->view, v, n);
+        return;
+    }
+    const int grid = grid_for(t, t->insert_blocks_per_sm, n, t->launch.insert_blocks_per_sm);
+    if (t->launch.insert_mode == 1)
+        k_insert<psf::kAggNone, kHier><<<grid, kThreads, 0, st>>>(t->view, v, n);
+    else
+        k_insert<psf::kAggWarp, kHier><<<grid, kThreads, 0, st>>>(t->view, v, n);
+}
+
+template <bool kHier>
+void launch_insert_progressive(const psf_table* t, const float4* v, uint32_t P, uint32_t D, uint32_t field,
+                               cudaStream_t st) {
+    const int grid = grid_for(t, t->insert_blocks_per_sm, P, t->launch.insert_blocks_per_sm);
+    if (t->launch.insert_mode == 1)
+        k_insert_progressive<psf::kAggNone, kHier><<<grid, kThreads, 0, st>>>(t->view, v, P, D, field);
+    else
+        k_insert_progressive<psf::kAggWarp, kHier><<<grid, kThreads, 0, st>>>(t->view, v, P, D, field);
+}
+
+}  // namespace
+
 extern "C" {
 
 int psf_abi_version(void) { return PSF_ABI_VERSION; }
@@ -473,11 +505,11 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     t->bytes = bytes;
     if (!cuda_ok(cudaGetDevice(&t->device), "cudaGetDevice") ||
         !cuda_ok(cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device), "cudaDeviceGetAttribute") ||
-        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->insert_blocks_per_sm, k_insert<psf::kAggWarp>, kThreads, 0),
+        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->insert_blocks_per_sm, k_insert<psf::kAggWarp, false>, kThreads, 0),
                  "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->update_blocks_per_sm, k_update, kThreads, 0), "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->query_blocks_per_sm, k_query, kThreads, 0), "occupancy") ||
-        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->staged_blocks_per_sm, k_insert_staged<psf::kAggWarp>,
+        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->staged_blocks_per_sm, k_insert_staged<psf::kAggWarp, false>,
                                                                kThreads, 0),
                  "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->staged_query_blocks_per_sm, k_query_staged, kThreads, 0),
@@ -520,6 +552,7 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     v.blend_mode = cfg->blend_mode;
     v.alpha_min = cfg->alpha_min;
     v.beta = cfg->beta;
+    v.levels = cfg->levels == 0 ? 1u : cfg->levels;
 
     const size_t cap = size_t{1} << cfg->log2_capacity;
     bool ok = cuda_ok(cudaMemsetAsync(base, 0, L.total, st), "cudaMemsetAsync");
@@ -542,20 +575,12 @@ int psf_insert(psf_table* t, const float* d_vertices, uint64_t n, void* stream) 
     if (!t) return PSF_ERR_INVALID_ARG;
     if (n == 0) return PSF_OK;
     if (!d_vertices || (reinterpret_cast<uintptr_t>(d_vertices) & 15u)) return PSF_ERR_INVALID_ARG;
-    const int grid = grid_for(t, t->insert_blocks_per_sm, n, t->launch.insert_blocks_per_sm);
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->launch.vertex_staging & 1u) {
-        const int sgrid = grid_for(t, t->staged_blocks_per_sm, n, t->launch.insert_blocks_per_sm);
-        if (t->launch.insert_mode == 1)
-            k_insert_staged<psf::kAggNone><<<sgrid, kThreads, 0, st>>>(t->view, v, n);
-        else
-            k_insert_staged<psf::kAggWarp><<<sgrid, kThreads, 0, st>>>(t->view, v, n);
-    } else if (t->launch.insert_mode == 1) {
-        k_insert<psf::kAggNone><<<grid, kThreads, 0, st>>>(t->view, v, n);
-    } else {
-        k_insert<psf::kAggWarp><<<grid, kThreads, 0, st>>>(t->view, v, n);
-    }
+    if (t->view.levels > 1)
+        launch_insert<true>(t, v, n, st);
+    else
+        launch_insert<false>(t, v, n, st);
     return cuda_ok(cudaGetLastError(), "k_insert") ? PSF_OK : PSF_ERR_CUDA;
 }
 
@@ -563,13 +588,12 @@ int psf_insert_progressive(psf_table* t, const float* d_vertices, uint32_t P, ui
     if (!t || field > 1) return PSF_ERR_INVALID_ARG;
     if (P == 0 || D == 0) return PSF_OK;
     if (!d_vertices || (reinterpret_cast<uintptr_t>(d_vertices) & 15u)) return PSF_ERR_INVALID_ARG;
-    const int grid = grid_for(t, t->insert_blocks_per_sm, P, t->launch.insert_blocks_per_sm);
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->launch.insert_mode == 1)
-        k_insert_progressive<psf::kAggNone><<<grid, kThreads, 0, st>>>(t->view, v, P, D, field);
+    if (t->view.levels > 1)
+        launch_insert_progressive<true>(t, v, P, D, field, st);
     else
-        k_insert_progressive<psf::kAggWarp><<<grid, kThreads, 0, st>>>(t->view, v, P, D, field);
+        launch_insert_progressive<false>(t, v, P, D, field, st);
     return cuda_ok(cudaGetLastError(), "k_insert_progressive") ? PSF_OK : PSF_ERR_CUDA;
 }
 

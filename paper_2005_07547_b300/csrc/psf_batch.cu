@@ -140,7 +140,10 @@ __global__ void __launch_bounds__(kThreads)
             v3 = __ldcs(r + 3);
         }
         unsigned len = 0, leaders = 0;
-        psf::insert_warp<kMode>(b.t, valid, v0, v1, v2, v3, &len, stage, &leaders);
+        if (b.t.levels > 1)  // warp-uniform: a warp's 32 vertices belong to one item
+            psf::insert_warp<kMode, true>(b.t, valid, v0, v1, v2, v3, &len, stage, &leaders);
+        else
+            psf::insert_warp<kMode, false>(b.t, valid, v0, v1, v2, v3, &len, stage, &leaders);
         if (len > 16u) atomicMax(&b.t.hdr->max_probe, len);  // only long probes are recorded here
     }
     if (!grid_barrier(ctl, h, items)) return;

@@ -74,6 +74,7 @@ struct TableView {
     uint32_t blend_mode;
     float alpha_min;
     float beta;
+    uint32_t levels;  // hierarchy levels, 1..4 (1: a flat table)
 };
 
 __device__ __forceinline__ unsigned long long global_timer_ns() {
@@ -240,6 +241,27 @@ __device__ __forceinline__ bool cell_key(const TableView& t, const float4& v0, c
     return true;
 }
 
+// The key of the same vertex at hierarchy level l (Section "Progressive hierarchical
+// solver"): cells 2^l times wider, so each signed position index is floor-divided by 2^l
+// (an arithmetic shift) and the level goes into bits 61-62; the normal and direction bins
+// (bits 48-60) are kept.  floor(floor(p 2^q) / 2^l) = floor(p 2^(q-l)).
+__device__ __forceinline__ unsigned long long level_key(unsigned long long k0, unsigned l) {
+    if (l == 0) return k0;
+    auto axis = [l](unsigned long long k, int shift) {
+        const int i = static_cast<int>((k >> shift) & 0xFFFFull) - 32768;
+        return static_cast<unsigned long long>((i >> l) + 32768) << shift;
+    };
+    return (static_cast<unsigned long long>(l) << 61) | (k0 & 0x1FFF000000000000ull) | axis(k0, 32) | axis(k0, 16) |
+           axis(k0, 0);
+}
+
+// The level a vertex at path depth j reads: min(j, levels - 1).  The paper picks the level
+// by a path-footprint heuristic it does not spell out; a path's footprint widens with every
+// bounce, and this rule takes the depth as that footprint's measure.
+__device__ __forceinline__ unsigned read_level(const TableView& t, unsigned j) {
+    return j < t.levels - 1u ? j : t.levels - 1u;
+}
+
 // Fixed-point contributions of an accepted vertex (eq. 5-6): round(fl32(w L_c) 2^F), round(w 2^F).
 // Returns 1 = accepted, 2 = range rule, 3 = zero fixed-point weight.
 __device__ __forceinline__ int vertex_values(const TableView& t, const float4& v0, const float4& v3,
@@ -327,20 +349,22 @@ struct alignas(16) LaneSums {
 // match_any; a group's lowest lane (its leader) adds the other members' sums, read from
 // the warp's shared-memory staging area, then probes once and adds.  A warp whose keys
 // are all distinct (the common case after the first bounce) skips the merge.  Integer
-// sums are exact, so every mode gives bit-identical tables.
-template <int kMode>
+// sums are exact, so every mode gives bit-identical tables.  With kHier the vertex is
+// added to its cell at every hierarchy level (t.levels of them); coarser levels merge
+// more lanes.
+template <int kMode, bool kHier = false>
 __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, const float4& v0, const float4& v1,
                                             const float4& v2, const float4& v3, unsigned* max_len,
                                             LaneSums* stage, unsigned* leaders) {
     const unsigned lane = threadIdx.x & 31u;
-    unsigned long long key = 0;
-    long long sums[4] = {0, 0, 0, 0};
+    unsigned long long key0 = 0;
+    long long own[4] = {0, 0, 0, 0};
     int cls = 0;
     if (valid) {
-        if (!cell_key(t, v0, v1, v2, &key))
+        if (!cell_key(t, v0, v1, v2, &key0))
             cls = 2;
         else
-            cls = vertex_values(t, v0, v3, sums, &sums[3]);
+            cls = vertex_values(t, v0, v3, own, &own[3]);
     }
     const unsigned accepted = __ballot_sync(kFull, cls == 1);
     const unsigned ranged = __ballot_sync(kFull, cls == 2);
@@ -352,32 +376,42 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
         }
         if (zero_w) atomicAdd(&t.hdr->zero_weight, static_cast<unsigned long long>(__popc(zero_w)));
     }
+    const unsigned nlevels = kHier ? t.levels : 1u;
     if (kMode == kAggNone) {
-        if (cls == 1) scatter_group(t, key, 1u << lane, sums, max_len);
-        *leaders += __popc(accepted);
+        for (unsigned l = 0; l < nlevels; ++l)
+            if (cls == 1) scatter_group(t, kHier ? level_key(key0, l) : key0, 1u << lane, own, max_len);
+        *leaders += nlevels * __popc(accepted);
         return;
     }
-    unsigned group = 0;
-    if (cls == 1) group = __match_any_sync(accepted, key);
-    const bool donor = cls == 1 && (group & ((1u << lane) - 1u)) != 0u;
-    if (__any_sync(kFull, donor)) {
-        if (donor) stage[lane] = LaneSums{{sums[0], sums[1], sums[2], sums[3]}};
-        __syncwarp();
-        if (cls == 1 && !donor) {
-            unsigned rest = group & ~(1u << lane);
-            while (rest) {
-                const LaneSums m = stage[__ffs(rest) - 1];
-                rest &= rest - 1u;
-                sums[0] += m.v[0];
-                sums[1] += m.v[1];
-                sums[2] += m.v[2];
-                sums[3] += m.v[3];
+    bool staged = false;
+    for (unsigned l = 0; l < nlevels; ++l) {
+        const unsigned long long key = kHier ? level_key(key0, l) : key0;
+        long long sums[4] = {own[0], own[1], own[2], own[3]};
+        unsigned group = 0;
+        if (cls == 1) group = __match_any_sync(accepted, key);
+        const bool donor = cls == 1 && (group & ((1u << lane) - 1u)) != 0u;
+        if (__any_sync(kFull, donor)) {
+            // the lanes' own sums are the same at every level, so they are staged once (by
+            // every accepted lane when a coarser level may make a leader a donor)
+            if (!staged && cls == 1 && (kHier || donor)) stage[lane] = LaneSums{{own[0], own[1], own[2], own[3]}};
+            staged = true;
+            __syncwarp();
+            if (cls == 1 && !donor) {
+                unsigned rest = group & ~(1u << lane);
+                while (rest) {
+                    const LaneSums m = stage[__ffs(rest) - 1];
+                    rest &= rest - 1u;
+                    sums[0] += m.v[0];
+                    sums[1] += m.v[1];
+                    sums[2] += m.v[2];
+                    sums[3] += m.v[3];
+                }
             }
+            __syncwarp();
         }
-        __syncwarp();
+        if (cls == 1 && !donor) scatter_group(t, key, group, sums, max_len);
+        *leaders += __popc(__ballot_sync(kFull, cls == 1 && !donor));
     }
-    if (cls == 1 && !donor) scatter_group(t, key, group, sums, max_len);
-    *leaders += __popc(__ballot_sync(kFull, cls == 1 && !donor));
 }
 
 // ---------------------------------------------------------------------------
@@ -509,14 +543,16 @@ __device__ __forceinline__ float3 value_at(const TableView& t, unsigned long lon
     return make_float3(L.x, L.y, L.z);
 }
 
-// The approximant of the vertex's cell, 0 if the cell is absent.  The value at the home
+// The approximant of the vertex's cell at hierarchy level `level`, 0 if the cell is
+// absent.  The value at the home
 // slot is loaded together with its key, so the common case (key found at its home slot)
 // costs one round trip instead of two.
 __device__ __forceinline__ float3 cell_value(const TableView& t, const float4& v0, const float4& v1,
-                                             const float4& v2, bool fp32_master = false) {
+                                             const float4& v2, bool fp32_master = false, unsigned level = 0) {
     const float3 zero = make_float3(0.0f, 0.0f, 0.0f);
     unsigned long long key;
     if (!cell_key(t, v0, v1, v2, &key)) return zero;
+    key = level_key(key, level);
     const unsigned long long mask = (1ull << t.log2cap) - 1ull;
     const unsigned long long keep = policy_evict_last();
     unsigned long long s = home_slot(t, key);
@@ -561,7 +597,7 @@ __device__ __forceinline__ void query_path(const TableView& t, const Estimator& 
         const unsigned long long i = static_cast<unsigned long long>(j) * P + p;
         const float4* r = v + 4 * i;  // streamed once: evict-first
         const float4 v0 = __ldcs(r), v1 = __ldcs(r + 1), v2 = __ldcs(r + 2), v3 = __ldcs(r + 3);
-        const float3 c = cell_value(t, v0, v1, v2);
+        const float3 c = cell_value(t, v0, v1, v2, false, read_level(t, static_cast<unsigned>(j)));
         float o0 = v3.x, o1 = v3.y, o2 = v3.z;
         if (j + 1 < static_cast<int>(D) && static_cast<unsigned>(j) >= e.j_begin && static_cast<unsigned>(j) < e.j_end) {
             o0 = combine(e, v3.x, v1.w, c_next.x, c.x);

@@ -20,10 +20,11 @@ def _session(k, w, d):
     h = int(round(9 * w / 16))
     v = w * h * d
     log2cap = int(math.ceil(math.log2(v))) + 1
-    return dict(name=f"s{k}", width=w, height=h, depth=d, log2_capacity=log2cap,
+    levels = 3 if k % 4 == 1 else 1  # some tables have hierarchy levels (more cells: more capacity)
+    return dict(name=f"s{k}", width=w, height=h, depth=d, log2_capacity=log2cap + (2 if levels > 1 else 0),
                 pos_bits=config4_q_bits(log2cap, 3), dir_bits=3, alpha_min=0.1, radiance="glossy",
                 seed=4000 + k, camera_step=0.0, camera_x0=0.5, cache_fp16=bool(k % 2),
-                key_layout=2 if k % 3 == 2 else 0)  # some tables keep their keys in the slot records
+                key_layout=2 if k % 3 == 2 else 0, levels=levels)  # some keep their keys in the slot records
 
 
 def _data(sessions, iterations):
@@ -35,7 +36,7 @@ def _data(sessions, iterations):
 def _table(psf, s):
     return psf.Table(psf.make_config(log2_capacity=s["log2_capacity"], pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
                                       alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"],
-                                      key_layout=s.get("key_layout", 0)))
+                                      key_layout=s.get("key_layout", 0), levels=s.get("levels", 1)))
 
 
 @pytest.mark.parametrize("insert_mode", [0, 1])
@@ -47,7 +48,7 @@ def test_batch_matches_alone_and_oracle(psf_mod, oracle_mod, insert_mode):
     alone = [_table(psf_mod, s) for s in sessions]
     mixed = [_table(psf_mod, s) for s in sessions]
     oracles = [oracle_mod.Oracle(pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
-                                 alpha_min=float(np.float32(s["alpha_min"]))) for s in sessions]
+                                 alpha_min=float(np.float32(s["alpha_min"])), levels=s["levels"]) for s in sessions]
     batch = psf_mod.Batch(len(sessions), insert_mode=insert_mode)
     for it in range(3):
         dev = [torch.from_numpy(data[k][it]).cuda() for k in range(len(sessions))]
@@ -64,7 +65,7 @@ def test_batch_matches_alone_and_oracle(psf_mod, oracle_mod, insert_mode):
             o.insert(data[k][it])
             o.update()
             check_after_update(rb, o.export(), fp16=s["cache_fp16"])
-            check_cv(outs_b[k].cpu().numpy(), o.query_cv(data[k][it], P, D), data[k][it], o.lookup(data[k][it]), P, D,
+            check_cv(outs_b[k].cpu().numpy(), o.query_cv(data[k][it], P, D), data[k][it], o.lookup(data[k][it], P, D), P, D,
                      1.0, 0xFFFFFFFF, o.export()["L"], fp16=s["cache_fp16"])
     assert batch.status() == 0
     for k, t in enumerate(mixed):

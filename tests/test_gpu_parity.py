@@ -18,7 +18,8 @@ pytestmark = pytest.mark.gpu
 def _oracle_for(oracle_mod, cfg):
     return oracle_mod.Oracle(pos_bits=cfg.pos_bits_q, dir_bits=cfg.dir_bits_d, use_normal=bool(cfg.use_normal),
                              frac_bits=cfg.frac_bits, blend_mode=cfg.blend_mode, cv_max_depth=cfg.cv_max_depth,
-                             alpha_min=float(np.float32(cfg.alpha_min)), beta=float(np.float32(cfg.beta)))
+                             alpha_min=float(np.float32(cfg.alpha_min)), beta=float(np.float32(cfg.beta)),
+                             levels=cfg.levels)
 
 
 def _run_and_compare(psf, oracle_mod, cfg, batches, P, D, *, check_insert=True, use_step=False):
@@ -44,7 +45,7 @@ def _run_and_compare(psf, oracle_mod, cfg, batches, P, D, *, check_insert=True, 
         worst["L32"] = max(worst["L32"], r32)
         worst["L16"] = max(worst["L16"], r16 or 0.0)
         ref = ora.query_cv(v, P, D)
-        worst["cv"] = max(worst["cv"], check_cv(out.cpu().numpy(), ref, v, ora.lookup(v), P, D, float(cfg.beta),
+        worst["cv"] = max(worst["cv"], check_cv(out.cpu().numpy(), ref, v, ora.lookup(v, P, D), P, D, float(cfg.beta),
                                                 cfg.cv_max_depth, ora.export()["L"], fp16=bool(cfg.cache_fp16)))
         stats = table.stats()
         dropped, zero_w = ora.counters()
