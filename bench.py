@@ -225,7 +225,7 @@ class ClockSampler:
                 "power_w_max": max(s[2] for s in self.samples), "source": "NVML (libnvidia-ml), 1 ms"}
 
 
-def atomic_probe_rates(modes=(0, 1, 2, 3), n_words: int = 1 << 25, reps: int = 3) -> dict:
+def atomic_probe_rates(modes=(0, 1, 2, 3, 4), n_words: int = 1 << 25, reps: int = 3) -> dict:
     """Measured L2 64-bit atomic throughput (ops/s) on this GPU, per probe mode, on a buffer of
     n_words 64-bit words (2^25 words = 256 MB, larger than L2, like a 2^22-slot table)."""
     import ctypes
@@ -243,10 +243,11 @@ def atomic_probe_rates(modes=(0, 1, 2, 3), n_words: int = 1 << 25, reps: int = 3
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     stream = torch.cuda.current_stream()
     out = {}
-    names = {0: "red_random_u64", 1: "atom_random_u64", 2: "insert_pattern_4red_1or", 3: "red_warp_contended_u64"}
+    names = {0: "red_random_u64", 1: "atom_random_u64", 2: "insert_pattern_4red_1or", 3: "red_warp_contended_u64",
+             4: "insert_pattern_bulk32_1or"}
     for mode in modes:
-        groups = (1 << 24) if mode == 2 else (1 << 26)
-        ops_per_group = 5 if mode == 2 else 1
+        groups = (1 << 24) if mode in (2, 4) else (1 << 26)
+        ops_per_group = 5 if mode in (2, 4) else 1
         args = (buf.data_ptr(), n_words, groups, mode, sms * 8, stream.cuda_stream)
         if lib.atomic_probe(*args) != 0:
             raise RuntimeError("atomic probe failed")
@@ -386,7 +387,7 @@ def run_psf(args) -> None:
                           alpha_min=w["alpha_min"], cache_fp16=args.fp16 or w["cache_fp16"],
                           key_layout=args.key_layout, levels=args.levels)
     table = psf.Table(cfg)
-    table.set_launch(insert_mode=args.insert_mode, vertex_staging=args.staging)
+    table.set_launch(insert_mode=args.insert_mode, vertex_staging=args.staging, sum_reduction=args.sum_reduction)
     dev = [torch.from_numpy(v).cuda() for v in host]
     out = torch.empty((V, 3), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -449,16 +450,20 @@ def run_psf(args) -> None:
     avg = {k: sum(v) / len(v) for k, v in kt.items()}
     dominant = max(avg, key=avg.get)
     achieved = alg[dominant] / (avg[dominant] / 1e3) / 1e9
-    # atomic roofline of the insert: 5 atomics per (warp, key) group against the probe's rate
-    # for the same pattern (4 reductions into one random 32-byte sector + 1 bitmap reduction)
-    probe_words = 8 << log2cap  # a buffer the size of the table's 64-byte slot records
-    probe = atomic_probe_rates(modes=(2,), n_words=probe_words) if rank == 0 else {}
-    atom_rate = 5.0 * leaders / (avg["k_insert"] / 1e3)
-    atomic_roofline = {"kernel": "k_insert", "achieved": atom_rate / 1e9, "unit": "G atomics/s",
-                       "peak": probe.get("insert_pattern_4red_1or", float("nan")) / 1e9,
-                       "frac": atom_rate / probe["insert_pattern_4red_1or"] if probe else None,
-                       "atomics_per_launch": 5.0 * leaders, "leader_groups_per_launch": leaders,
-                       "peak_source": f"live probe: 4 x red.add.u64 into one random 32-B sector + red.or, "
+    # atomic roofline of the insert: one update of a random 32-byte sector per (warp, key)
+    # group plus one bitmap reduction, against the probe's rate for the same pattern on a
+    # buffer the size of the table's slot records (mode 4: the sums as one bulk reduction,
+    # the default; mode 2: as four 64-bit reductions)
+    probe_words = 8 << log2cap
+    mode = 4 if args.sum_reduction == 0 else 2
+    pname = {4: "insert_pattern_bulk32_1or", 2: "insert_pattern_4red_1or"}[mode]
+    probe = atomic_probe_rates(modes=(mode,), n_words=probe_words) if rank == 0 else {}
+    peak_groups = probe[pname] / 5.0 if probe else float("nan")
+    group_rate = leaders / (avg["k_insert"] / 1e3)
+    atomic_roofline = {"kernel": "k_insert", "achieved": group_rate / 1e9, "unit": "G groups/s",
+                       "peak": peak_groups / 1e9, "frac": group_rate / peak_groups if probe else None,
+                       "leader_groups_per_launch": leaders,
+                       "peak_source": f"live probe: random 32-B sector, {'one bulk (TMA) reduction' if mode == 4 else '4 x red.add.u64'} + red.or, "
                                       f"{probe_words * 8 / 1e6:.0f} MB (the slot records)"}
     kernels = {k: {"avg_ms": avg[k], "share": avg[k] / sum(avg.values()),
                    "algorithmic_GBps": alg[k] / (avg[k] / 1e3) / 1e9,
@@ -496,6 +501,7 @@ def run_psf(args) -> None:
                    "l2": f"inputs larger than L2: {n_iter} distinct {V * 64 / 1e6:.0f} MB vertex batches, "
                          "a different one every step",
                    "insert_mode": args.insert_mode, "vertex_staging": args.staging,
+                   "sum_reduction": {0: "bulk (TMA) 32-B reduction", 1: "4 x red.add.u64"}[args.sum_reduction],
                    "key_layout": {0: "auto", 1: "dense key array", 2: "keys in slot records"}[args.key_layout],
                    "parallelism": f"sessions x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -788,6 +794,7 @@ def main(argv=None) -> None:
     ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
     ap.add_argument("--key-layout", type=int, default=0, help="0: auto, 1: dense key array, 2: keys in slot records")
     ap.add_argument("--levels", type=int, default=1, help="hierarchy levels of the table (1: flat)")
+    ap.add_argument("--sum-reduction", type=int, default=0, help="0: one bulk (TMA) reduction per group, 1: four red.add")
     ap.add_argument("--pool", type=int, default=4, help="distinct resident iterations per session (batched)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")

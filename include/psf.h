@@ -204,8 +204,9 @@ int psf_destroy(psf_table* t);
 
 /* Launch knobs of a table's kernels (the autotuner's search space).  Results do not
  * depend on them: the integer sums are order-independent.  psf_create starts from
- * {0, 0, 0, 0, 1} (warp merge, occupancy-limited grids, insert tiles staged); a zero
- * grid cap means the occupancy limit. */
+ * {0, 0, 0, 0, 1, 0} (warp merge, occupancy-limited grids, insert tiles staged, bulk sums);
+ * a zero grid cap means the occupancy limit.  A batch (psf_batch_set) copies each table's
+ * sum_reduction when its descriptors are set. */
 typedef struct {
     uint32_t insert_mode;          /* 0: lanes of a warp holding the same key are merged (match_any)
                                       and one leader probes and adds; 1: every vertex adds on its own */
@@ -215,6 +216,9 @@ typedef struct {
     uint32_t vertex_staging;       /* bit 0: psf_insert, bit 1: psf_query_cv/_biased stage the vertex
                                       records through shared memory with bulk (TMA) copies, per warp;
                                       a clear bit means direct 16-byte loads */
+    uint32_t sum_reduction;        /* how an insert adds a group's three sums and counter to its cell:
+                                      0 = one 32-byte bulk reduction from shared memory (TMA),
+                                      1 = four 64-bit atomic reductions */
 } psf_launch_config;
 
 /* Set / read the launch knobs of a table (host-side only; affects later calls). */
@@ -300,7 +304,7 @@ int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, const psf_ba
 const char* psf_last_cuda_error(void);
 
 /* ABI version of this header: bump on any incompatible change. */
-#define PSF_ABI_VERSION 3
+#define PSF_ABI_VERSION 4
 int psf_abi_version(void);
 
 #ifdef __cplusplus

@@ -22,6 +22,7 @@ from .table import Table
 
 TABLE_SPACE = {
     "vertex_staging": (0, 1, 2, 3),
+    "sum_reduction": (0, 1),
     "insert_mode": (0, 1),
     "insert_blocks_per_sm": (0, 4, 2),
     "query_blocks_per_sm": (0, 4),

@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* 
         v2 = n2;
         v3 = n3;
     }
+    psf::bulk_wait_done();  // this thread's sums have landed before the kernel ends
     if (max_len) atomicMax(&s_max_probe, max_len);
     if ((threadIdx.x & 31u) == 0 && leaders) atomicAdd(&s_leaders, static_cast<unsigned long long>(leaders));
     __syncthreads();
@@ -197,6 +198,7 @@ __global__ void __launch_bounds__(kThreads) k_insert_progressive(TableView t, co
             le_next = le;
         }
     }
+    psf::bulk_wait_done();  // this thread's sums have landed before the kernel ends
     if (max_len) atomicMax(&s_max_probe, max_len);
     if ((threadIdx.x & 31u) == 0 && leaders) atomicAdd(&s_leaders, static_cast<unsigned long long>(leaders));
     __syncthreads();
@@ -267,6 +269,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_insert_staged(TableView t, cons
         // let a copy still in flight land before the warp leaves (bounded)
         if (pending_other) psf::mbar_wait(&s_bar[wib][(k & 1u) ^ 1u], ((k + 1) >> 1) & 1u);
     }
+    psf::bulk_wait_done();  // this thread's sums have landed before the kernel ends
     if (max_len) atomicMax(&s_max_probe, max_len);
     if (lane == 0 && leaders) atomicAdd(&s_leaders, static_cast<unsigned long long>(leaders));
     __syncthreads();
@@ -520,7 +523,8 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
         return PSF_ERR_CUDA;
     }
     *t->h_status = 0;
-    t->launch = psf_launch_config{0u, 0u, 0u, 0u, 1u};  // insert stages its vertex tiles
+    t->launch = psf_launch_config{0u, 0u, 0u, 0u, 1u, 0u};  // insert stages its vertex tiles, bulk sums
+    t->view.sum_path = psf::kSumsBulk;
     char* base = static_cast<char*>(d_mem);
     TableView& v = t->view;
     v.hdr = reinterpret_cast<DevHeader*>(base + L.hdr);
@@ -656,8 +660,9 @@ int psf_reset(psf_table* t, void* stream) {
 }
 
 int psf_set_launch_config(psf_table* t, const psf_launch_config* c) {
-    if (!t || !c || c->insert_mode > 1 || c->vertex_staging > 3) return PSF_ERR_INVALID_ARG;
+    if (!t || !c || c->insert_mode > 1 || c->vertex_staging > 3 || c->sum_reduction > 1) return PSF_ERR_INVALID_ARG;
     t->launch = *c;
+    t->view.sum_path = c->sum_reduction;
     return PSF_OK;
 }
 

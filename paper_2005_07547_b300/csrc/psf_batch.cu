@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(kThreads)
             psf::insert_warp<kMode, false>(b.t, valid, v0, v1, v2, v3, &len, stage, &leaders);
         if (len > 16u) atomicMax(&b.t.hdr->max_probe, len);  // only long probes are recorded here
     }
+    psf::bulk_wait_done();  // this thread's bulk sums have landed before the barrier publishes them
     if (!grid_barrier(ctl, h, items)) return;
 
     // phase 2: blend every table's touched cells

@@ -74,8 +74,12 @@ struct TableView {
     uint32_t blend_mode;
     float alpha_min;
     float beta;
-    uint32_t levels;  // hierarchy levels, 1..4 (1: a flat table)
+    uint32_t levels;    // hierarchy levels, 1..4 (1: a flat table)
+    uint32_t sum_path;  // how a group's sums reach its slot: kSumsBulk or kSumsRed
 };
+
+constexpr uint32_t kSumsBulk = 0;  // one 32-byte bulk reduction from shared memory (TMA)
+constexpr uint32_t kSumsRed = 1;   // four 64-bit reductions
 
 __device__ __forceinline__ unsigned long long global_timer_ns() {
     unsigned long long t;
@@ -318,11 +322,40 @@ __device__ __forceinline__ long long probe_claim(const TableView& t, unsigned lo
     return -1;
 }
 
+// Per-warp staging of the lanes' sums (32 B per lane): donors' sums for the merge, and each
+// leader's merged sums as the source of its bulk reduction.
+struct alignas(16) LaneSums {
+    long long v[4];
+};
+
+// Before a lane rewrites its LaneSums slot: its earlier bulk reductions have read it.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// Before the sums are read by other threads (kernel end, grid barrier): this thread's bulk
+// reductions have been performed, and they are ordered before its later generic accesses.
+__device__ __forceinline__ void bulk_wait_done() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Add the four 64-bit sums at `src` (shared memory) into the first sector of slot `dst` with
+// one bulk reduction (cp.reduce.async.bulk .add.u64): each element is added atomically, and
+// the L2 takes one 32-byte operation instead of four.  Measured on the B300 (random sectors,
+// plus the dirty-bit reduction): 29 vs 21 G groups/s on 256 MB, 24 vs 11 on 1 GB.
+__device__ __forceinline__ void bulk_add_sums(Slot* dst, const LaneSums* src) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // src's generic writes first
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_u32(src)), "r"(32u)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
 // Leader of a group of lanes holding the same key: probe once, add the group's sums.
-// Every atomic is a reduction whose result is not read (fire and forget); the touched
-// bit is set unconditionally, so no warp waits on an atomic round trip.
+// Every update is a reduction whose result is not read (fire and forget); the touched bit
+// is set unconditionally, so no warp waits on an atomic round trip.  `src` is this lane's
+// LaneSums slot (the bulk reduction's source).
 __device__ __forceinline__ void scatter_group(const TableView& t, unsigned long long key, unsigned members,
-                                              const long long sums[4], unsigned* max_len) {
+                                              const long long sums[4], unsigned* max_len, LaneSums* src) {
     unsigned len = 0;
     const long long slot = probe_claim(t, key, &len);
     *max_len = len > *max_len ? len : *max_len;
@@ -332,17 +365,18 @@ __device__ __forceinline__ void scatter_group(const TableView& t, unsigned long 
         return;
     }
     Slot* a = t.slots + slot;
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[0]), static_cast<unsigned long long>(sums[0]));
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[1]), static_cast<unsigned long long>(sums[1]));
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[2]), static_cast<unsigned long long>(sums[2]));
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a->c), static_cast<unsigned long long>(sums[3]));
+    if (t.sum_path == kSumsBulk) {
+        bulk_wait_read();
+        *src = LaneSums{{sums[0], sums[1], sums[2], sums[3]}};
+        bulk_add_sums(a, src);
+    } else {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[0]), static_cast<unsigned long long>(sums[0]));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[1]), static_cast<unsigned long long>(sums[1]));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[2]), static_cast<unsigned long long>(sums[2]));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a->c), static_cast<unsigned long long>(sums[3]));
+    }
     atomicOr(t.dirty + (slot >> 5), 1u << (slot & 31));
 }
-
-// Per-warp staging of the lanes' sums for the donor merge (32 B per lane).
-struct alignas(16) LaneSums {
-    long long v[4];
-};
 
 // One warp's worth of vertices (one per lane, `valid` lanes only): classify, then add each
 // accepted vertex to its cell.  With kAggWarp, lanes holding the same key are found with
@@ -351,7 +385,9 @@ struct alignas(16) LaneSums {
 // are all distinct (the common case after the first bounce) skips the merge.  Integer
 // sums are exact, so every mode gives bit-identical tables.  With kHier the vertex is
 // added to its cell at every hierarchy level (t.levels of them); coarser levels merge
-// more lanes.
+// more lanes.  A lane's LaneSums slot holds its own sums while the group merges and then,
+// for a leader, the merged sums its bulk reduction reads; every write to the slot waits
+// for the lane's earlier bulk reductions to have read it.
 template <int kMode, bool kHier = false>
 __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, const float4& v0, const float4& v1,
                                             const float4& v2, const float4& v3, unsigned* max_len,
@@ -379,11 +415,10 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
     const unsigned nlevels = kHier ? t.levels : 1u;
     if (kMode == kAggNone) {
         for (unsigned l = 0; l < nlevels; ++l)
-            if (cls == 1) scatter_group(t, kHier ? level_key(key0, l) : key0, 1u << lane, own, max_len);
+            if (cls == 1) scatter_group(t, kHier ? level_key(key0, l) : key0, 1u << lane, own, max_len, stage + lane);
         *leaders += nlevels * __popc(accepted);
         return;
     }
-    bool staged = false;
     for (unsigned l = 0; l < nlevels; ++l) {
         const unsigned long long key = kHier ? level_key(key0, l) : key0;
         long long sums[4] = {own[0], own[1], own[2], own[3]};
@@ -391,10 +426,10 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
         if (cls == 1) group = __match_any_sync(accepted, key);
         const bool donor = cls == 1 && (group & ((1u << lane) - 1u)) != 0u;
         if (__any_sync(kFull, donor)) {
-            // the lanes' own sums are the same at every level, so they are staged once (by
-            // every accepted lane when a coarser level may make a leader a donor)
-            if (!staged && cls == 1 && (kHier || donor)) stage[lane] = LaneSums{{own[0], own[1], own[2], own[3]}};
-            staged = true;
+            if (donor) {
+                bulk_wait_read();
+                stage[lane] = LaneSums{{own[0], own[1], own[2], own[3]}};
+            }
             __syncwarp();
             if (cls == 1 && !donor) {
                 unsigned rest = group & ~(1u << lane);
@@ -409,7 +444,7 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
             }
             __syncwarp();
         }
-        if (cls == 1 && !donor) scatter_group(t, key, group, sums, max_len);
+        if (cls == 1 && !donor) scatter_group(t, key, group, sums, max_len, stage + lane);
         *leaders += __popc(__ballot_sync(kFull, cls == 1 && !donor));
     }
 }

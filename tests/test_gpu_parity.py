@@ -257,6 +257,7 @@ def test_1920x1080_depth5_full_size_fp32_and_fp16(psf_mod, oracle_mod):
 @pytest.mark.parametrize("knobs", [dict(insert_mode=1), dict(insert_blocks_per_sm=1, update_blocks_per_sm=1,
                                                               query_blocks_per_sm=1),
                                    dict(insert_mode=1, insert_blocks_per_sm=2), dict(vertex_staging=3),
+                                   dict(sum_reduction=1), dict(sum_reduction=1, insert_mode=1, vertex_staging=0),
                                    dict(vertex_staging=3, insert_mode=1, insert_blocks_per_sm=1, query_blocks_per_sm=1)])
 def test_launch_knobs_do_not_change_results(psf_mod, knobs):
     """Aggregation mode and grid shape change only the order of the integer additions."""
