@@ -225,9 +225,10 @@ class ClockSampler:
                 "power_w_max": max(s[2] for s in self.samples), "source": "NVML (libnvidia-ml), 1 ms"}
 
 
-def atomic_probe_rates(modes=(0, 1, 2, 3, 4), n_words: int = 1 << 25, reps: int = 3) -> dict:
+def atomic_probe_rates(modes=(0, 1, 2, 3, 4, 5), n_words: int = 1 << 25, reps: int = 3, n_distinct: int = 0) -> dict:
     """Measured L2 64-bit atomic throughput (ops/s) on this GPU, per probe mode, on a buffer of
-    n_words 64-bit words (2^25 words = 256 MB, larger than L2, like a 2^22-slot table)."""
+    n_words 64-bit words (2^25 words = 256 MB, larger than L2, like a 2^22-slot table).  With
+    n_distinct > 0 the sector patterns (modes 2, 4, 5) target that many fixed random sectors."""
     import ctypes
 
     import torch
@@ -237,18 +238,18 @@ def atomic_probe_rates(modes=(0, 1, 2, 3, 4), n_words: int = 1 << 25, reps: int 
     _b.build()
     lib = ctypes.CDLL(_b.PROBE_LIB)
     lib.atomic_probe.restype = ctypes.c_int
-    lib.atomic_probe.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
-                                 ctypes.c_void_p]
+    lib.atomic_probe.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_void_p]
     buf = torch.zeros(n_words * 8 + (n_words // 128) * 4, dtype=torch.uint8, device="cuda")
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     stream = torch.cuda.current_stream()
     out = {}
     names = {0: "red_random_u64", 1: "atom_random_u64", 2: "insert_pattern_4red_1or", 3: "red_warp_contended_u64",
-             4: "insert_pattern_bulk32_1or"}
+             4: "insert_pattern_bulk32_1or", 5: "bulk32_only"}
     for mode in modes:
-        groups = (1 << 24) if mode in (2, 4) else (1 << 26)
-        ops_per_group = 5 if mode in (2, 4) else 1
-        args = (buf.data_ptr(), n_words, groups, mode, sms * 8, stream.cuda_stream)
+        groups = (1 << 24) if mode in (2, 4, 5) else (1 << 26)
+        ops_per_group = 5 if mode in (2, 4, 5) else 1
+        args = (buf.data_ptr(), n_words, groups, n_distinct, mode, sms * 8, stream.cuda_stream)
         if lib.atomic_probe(*args) != 0:
             raise RuntimeError("atomic probe failed")
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -452,19 +453,20 @@ def run_psf(args) -> None:
     achieved = alg[dominant] / (avg[dominant] / 1e3) / 1e9
     # atomic roofline of the insert: one update of a random 32-byte sector per (warp, key)
     # group plus one bitmap reduction, against the probe's rate for the same pattern on a
-    # buffer the size of the table's slot records (mode 4: the sums as one bulk reduction,
-    # the default; mode 2: as four 64-bit reductions)
+    # buffer the size of the table's slot records with the insert's footprint (targets drawn
+    # from as many fixed random sectors as the insert touches cells); mode 4: the sums as one
+    # bulk reduction, the default; mode 2: as four 64-bit reductions
     probe_words = 8 << log2cap
     mode = 4 if args.sum_reduction == 0 else 2
     pname = {4: "insert_pattern_bulk32_1or", 2: "insert_pattern_4red_1or"}[mode]
-    probe = atomic_probe_rates(modes=(mode,), n_words=probe_words) if rank == 0 else {}
+    probe = atomic_probe_rates(modes=(mode,), n_words=probe_words, n_distinct=max(1, int(touched))) if rank == 0 else {}
     peak_groups = probe[pname] / 5.0 if probe else float("nan")
     group_rate = leaders / (avg["k_insert"] / 1e3)
     atomic_roofline = {"kernel": "k_insert", "achieved": group_rate / 1e9, "unit": "G groups/s",
                        "peak": peak_groups / 1e9, "frac": group_rate / peak_groups if probe else None,
                        "leader_groups_per_launch": leaders,
                        "peak_source": f"live probe: random 32-B sector, {'one bulk (TMA) reduction' if mode == 4 else '4 x red.add.u64'} + red.or, "
-                                      f"{probe_words * 8 / 1e6:.0f} MB (the slot records)"}
+                                      f"{int(touched)} distinct sectors of {probe_words * 8 / 1e6:.0f} MB (the touched cells of the slot records)"}
     kernels = {k: {"avg_ms": avg[k], "share": avg[k] / sum(avg.values()),
                    "algorithmic_GBps": alg[k] / (avg[k] / 1e3) / 1e9,
                    "frac_of_hbm": alg[k] / (avg[k] / 1e3) / 1e9 / peaks["hbm_gbs"]} for k in avg}
@@ -790,7 +792,7 @@ def main(argv=None) -> None:
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--insert-mode", type=int, default=0, help="0: warp aggregation of equal keys; 1: none")
-    ap.add_argument("--staging", type=int, default=1, help="bit 0: insert, bit 1: query stage vertex records through shared memory (TMA)")
+    ap.add_argument("--staging", type=int, default=0, help="bit 0: insert, bit 1: query stage vertex records through shared memory (TMA)")
     ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched workload")
     ap.add_argument("--key-layout", type=int, default=0, help="0: auto, 1: dense key array, 2: keys in slot records")
     ap.add_argument("--levels", type=int, default=1, help="hierarchy levels of the table (1: flat)")

@@ -204,7 +204,7 @@ int psf_destroy(psf_table* t);
 
 /* Launch knobs of a table's kernels (the autotuner's search space).  Results do not
  * depend on them: the integer sums are order-independent.  psf_create starts from
- * {0, 0, 0, 0, 1, 0} (warp merge, occupancy-limited grids, insert tiles staged, bulk sums);
+ * {0, 0, 0, 0, 0, 0} (warp merge, occupancy-limited grids, direct vertex loads, bulk sums);
  * a zero grid cap means the occupancy limit.  A batch (psf_batch_set) copies each table's
  * sum_reduction when its descriptors are set. */
 typedef struct {

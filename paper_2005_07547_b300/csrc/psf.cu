@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_query_staged(TableView t, psf::
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_update(TableView t) {
+__global__ void __launch_bounds__(kThreads, 4) k_update(TableView t) {
     __shared__ unsigned long long s_touched;
     if (threadIdx.x == 0) s_touched = 0;
     __syncthreads();
@@ -452,32 +452,52 @@ __global__ void __launch_bounds__(kThreads) k_reset(TableView t) {
 
 namespace {
 
+// Resident 256-thread blocks per SM of kernel `fn` on this table's device (queried once per
+// kernel and cached in the table; 1 if the query fails).
+int resident_blocks(const psf_table* t, const void* fn) {
+    for (int i = 0; i < t->occ_n; ++i)
+        if (t->occ_fn[i] == fn) return t->occ_blocks[i];
+    int blocks = 0;
+    if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, kThreads, 0), "occupancy") || blocks < 1)
+        blocks = 1;
+    if (t->occ_n < 16) {
+        t->occ_fn[t->occ_n] = fn;
+        t->occ_blocks[t->occ_n] = blocks;
+        ++t->occ_n;
+    }
+    return blocks;
+}
+
+template <typename Kernel, typename... Args>
+void launch_sized(const psf_table* t, Kernel kernel, unsigned long long work, cudaStream_t st, Args... args) {
+    const int grid = grid_for(t, resident_blocks(t, reinterpret_cast<const void*>(kernel)), work,
+                              t->launch.insert_blocks_per_sm);
+    kernel<<<grid, kThreads, 0, st>>>(args...);
+}
+
 // The insert kernels for a flat table (kHier = false) or for one with hierarchy levels.
 template <bool kHier>
 void launch_insert(const psf_table* t, const float4* v, unsigned long long n, cudaStream_t st) {
+    const bool none = t->launch.insert_mode == 1;
     if (t->launch.vertex_staging & 1u) {
-        const int sgrid = grid_for(t, t->staged_blocks_per_sm, n, t->launch.insert_blocks_per_sm);
-        if (t->launch.insert_mode == 1)
-            k_insert_staged<psf::kAggNone, kHier><<<sgrid, kThreads, 0, st>>>(t->view, v, n);
+        if (none)
+            launch_sized(t, k_insert_staged<psf::kAggNone, kHier>, n, st, t->view, v, n);
         else
-            k_insert_staged<psf::kAggWarp, kHier><<<sgrid, kThreads, 0, st>>>(t->view, v, n);
-        return;
+            launch_sized(t, k_insert_staged<psf::kAggWarp, kHier>, n, st, t->view, v, n);
+    } else if (none) {
+        launch_sized(t, k_insert<psf::kAggNone, kHier>, n, st, t->view, v, n);
+    } else {
+        launch_sized(t, k_insert<psf::kAggWarp, kHier>, n, st, t->view, v, n);
     }
-    const int grid = grid_for(t, t->insert_blocks_per_sm, n, t->launch.insert_blocks_per_sm);
-    if (t->launch.insert_mode == 1)
-        k_insert<psf::kAggNone, kHier><<<grid, kThreads, 0, st>>>(t->view, v, n);
-    else
-        k_insert<psf::kAggWarp, kHier><<<grid, kThreads, 0, st>>>(t->view, v, n);
 }
 
 template <bool kHier>
 void launch_insert_progressive(const psf_table* t, const float4* v, uint32_t P, uint32_t D, uint32_t field,
                                cudaStream_t st) {
-    const int grid = grid_for(t, t->insert_blocks_per_sm, P, t->launch.insert_blocks_per_sm);
     if (t->launch.insert_mode == 1)
-        k_insert_progressive<psf::kAggNone, kHier><<<grid, kThreads, 0, st>>>(t->view, v, P, D, field);
+        launch_sized(t, k_insert_progressive<psf::kAggNone, kHier>, P, st, t->view, v, P, D, field);
     else
-        k_insert_progressive<psf::kAggWarp, kHier><<<grid, kThreads, 0, st>>>(t->view, v, P, D, field);
+        launch_sized(t, k_insert_progressive<psf::kAggWarp, kHier>, P, st, t->view, v, P, D, field);
 }
 
 }  // namespace
@@ -508,13 +528,8 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     t->bytes = bytes;
     if (!cuda_ok(cudaGetDevice(&t->device), "cudaGetDevice") ||
         !cuda_ok(cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device), "cudaDeviceGetAttribute") ||
-        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->insert_blocks_per_sm, k_insert<psf::kAggWarp, false>, kThreads, 0),
-                 "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->update_blocks_per_sm, k_update, kThreads, 0), "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->query_blocks_per_sm, k_query, kThreads, 0), "occupancy") ||
-        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->staged_blocks_per_sm, k_insert_staged<psf::kAggWarp, false>,
-                                                               kThreads, 0),
-                 "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->staged_query_blocks_per_sm, k_query_staged, kThreads, 0),
                  "occupancy") ||
         !cuda_ok(cudaHostAlloc(reinterpret_cast<void**>(&t->h_status), sizeof(unsigned), cudaHostAllocMapped),
@@ -523,7 +538,9 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
         return PSF_ERR_CUDA;
     }
     *t->h_status = 0;
-    t->launch = psf_launch_config{0u, 0u, 0u, 0u, 1u, 0u};  // insert stages its vertex tiles, bulk sums
+    // direct vertex loads (measured: with bulk sums the TMA-staged tiles are slower, 133 vs
+    // 120 us on 1280x720x4, as both go through the TMA unit), bulk sums
+    t->launch = psf_launch_config{0u, 0u, 0u, 0u, 0u, 0u};
     t->view.sum_path = psf::kSumsBulk;
     char* base = static_cast<char*>(d_mem);
     TableView& v = t->view;

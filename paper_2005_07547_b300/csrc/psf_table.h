@@ -16,12 +16,16 @@ struct psf_table {
     unsigned* h_status;  // host-mapped pinned word written by the update
     int device;
     int sms;
-    int insert_blocks_per_sm;  // occupancy limits of the kernels
-    int update_blocks_per_sm;
+    int update_blocks_per_sm;  // occupancy limits of the kernels (the inserts: occ_* below)
     int query_blocks_per_sm;
-    int staged_blocks_per_sm;  // the shared-memory staged insert and query
-    int staged_query_blocks_per_sm;
+    int staged_query_blocks_per_sm;  // the shared-memory staged query
     psf_launch_config launch;  // tuning knobs (psf_set_launch_config)
+    // resident blocks per SM of each insert kernel variant launched so far (its grid is sized
+    // from its own register use: the variants differ, and a grid above the resident limit
+    // runs a partial second wave)
+    mutable const void* occ_fn[16];
+    mutable int occ_blocks[16];
+    mutable int occ_n;
 };
 
 // Records the CUDA error text for psf_last_cuda_error; true if e is cudaSuccess.

@@ -27,7 +27,7 @@ def test_levels_64x64_all_iterations(psf_mod, oracle_mod, levels, fp16):
     print("worst relative errors", worst)
 
 
-@pytest.mark.parametrize("knobs", [dict(vertex_staging=0), dict(insert_mode=1), dict(vertex_staging=3),
+@pytest.mark.parametrize("knobs", [dict(vertex_staging=1), dict(insert_mode=1), dict(vertex_staging=3),
                                    dict(vertex_staging=0, insert_mode=1, insert_blocks_per_sm=1), dict(sum_reduction=1),
                                    dict(sum_reduction=1, insert_mode=1)])
 def test_levels_launch_knobs_do_not_change_results(psf_mod, knobs):
