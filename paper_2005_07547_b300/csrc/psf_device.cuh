@@ -297,29 +297,40 @@ __device__ __forceinline__ unsigned long long home_slot(const TableView& t, unsi
     return fmix64(key) >> (64 - t.log2cap);
 }
 
-// Find or claim the slot of `key` (linear probing, claim by CAS on kEmpty).
-// Returns the slot, or -1 when max_probe slots were visited without success.
-__device__ __forceinline__ long long probe_claim(const TableView& t, unsigned long long key, unsigned* len) {
-    const unsigned long long mask = (1ull << t.log2cap) - 1ull;
+// Find or claim the slot of `key` for every lane with `need` set (linear probing from
+// fmix64(key), claim by CAS on kEmpty), the whole warp stepping together: one warp-uniform
+// loop whose trip count is the longest probe among the lanes, with no divergent exits to
+// reconverge.  Slot indices are 32-bit (capacity <= 2^30).  *slot receives the slot, or -1
+// when max_probe slots were visited without success; *len the slots visited.
+__device__ __forceinline__ void probe_warp(const TableView& t, bool need, unsigned long long key, long long* slot,
+                                           unsigned* len) {
+    const unsigned mask = (1u << t.log2cap) - 1u;
     const unsigned long long keep = policy_evict_last();
-    unsigned long long s = home_slot(t, key);
-    for (unsigned i = 0; i < t.max_probe; ++i) {
-        const unsigned long long k = load_key(key_ptr(t, s), keep);
-        if (k == key) {
-            *len = i + 1;
-            return static_cast<long long>(s);
-        }
-        if (k == kEmpty) {
-            const unsigned long long old = atomicCAS(key_ptr(t, s), kEmpty, key);
-            if (old == kEmpty || old == key) {
-                *len = i + 1;
-                return static_cast<long long>(s);
+    unsigned s = static_cast<unsigned>(home_slot(t, key));
+    unsigned n = 0;
+    long long found = -1;
+    while (__any_sync(kFull, need)) {
+        if (need) {
+            ++n;
+            unsigned long long* kp = t.keys + static_cast<unsigned long long>(s) * t.key_stride;
+            const unsigned long long k = load_key(kp, keep);
+            bool hit = k == key;
+            if (!hit && k == kEmpty) {
+                const unsigned long long old = atomicCAS(kp, kEmpty, key);
+                hit = old == kEmpty || old == key;
+            }
+            if (hit) {
+                found = s;
+                need = false;
+            } else if (n >= t.max_probe) {
+                need = false;
+            } else {
+                s = (s + 1) & mask;
             }
         }
-        s = (s + 1) & mask;
     }
-    *len = t.max_probe;
-    return -1;
+    *slot = found;
+    *len = n;
 }
 
 // Per-warp staging of the lanes' sums (32 B per lane): donors' sums for the merge, and each
@@ -350,15 +361,13 @@ __device__ __forceinline__ void bulk_add_sums(Slot* dst, const LaneSums* src) {
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-// Leader of a group of lanes holding the same key: probe once, add the group's sums.
-// Every update is a reduction whose result is not read (fire and forget); the touched bit
-// is set unconditionally, so no warp waits on an atomic round trip.  `src` is this lane's
-// LaneSums slot (the bulk reduction's source).
-__device__ __forceinline__ void scatter_group(const TableView& t, unsigned long long key, unsigned members,
-                                              const long long sums[4], unsigned* max_len, LaneSums* src) {
-    unsigned len = 0;
-    const long long slot = probe_claim(t, key, &len);
-    *max_len = len > *max_len ? len : *max_len;
+// A group's head adds the group's sums to its cell's slot (from probe_warp; -1: the
+// table is full and the group's vertices are dropped).  Every update is a reduction whose
+// result is not read (fire and forget); the touched bit is set unconditionally, so no warp
+// waits on an atomic round trip.  `src` is this lane's LaneSums slot (the bulk reduction's
+// source).
+__device__ __forceinline__ void add_group(const TableView& t, long long slot, unsigned members, const long long sums[4],
+                                          LaneSums* src) {
     if (slot < 0) {
         atomicOr(&t.hdr->status, kStatusTableFull);
         atomicAdd(&t.hdr->dropped, static_cast<unsigned long long>(__popc(members)));
@@ -376,6 +385,19 @@ __device__ __forceinline__ void scatter_group(const TableView& t, unsigned long 
         atomicAdd(reinterpret_cast<unsigned long long*>(&a->c), static_cast<unsigned long long>(sums[3]));
     }
     atomicOr(t.dirty + (slot >> 5), 1u << (slot & 31));
+}
+
+// Probe for every lane with `head` set (the whole warp calls this), then each head adds
+// its group's sums.
+__device__ __forceinline__ void scatter_heads(const TableView& t, bool head, unsigned long long key, unsigned members,
+                                              const long long sums[4], unsigned* max_len, LaneSums* src) {
+    long long slot;
+    unsigned len;
+    probe_warp(t, head, key, &slot, &len);
+    if (head) {
+        *max_len = len > *max_len ? len : *max_len;
+        add_group(t, slot, members, sums, src);
+    }
 }
 
 // The lanes after `lane` that continue its run (the consecutive set bits of `joined` from
@@ -422,7 +444,7 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
     const unsigned nlevels = kHier ? t.levels : 1u;
     if (kMode == kAggNone) {
         for (unsigned l = 0; l < nlevels; ++l)
-            if (cls == 1) scatter_group(t, kHier ? level_key(key0, l) : key0, 1u << lane, own, max_len, stage + lane);
+            scatter_heads(t, cls == 1, kHier ? level_key(key0, l) : key0, 1u << lane, own, max_len, stage + lane);
         *leaders += nlevels * __popc(accepted);
         return;
     }
@@ -452,7 +474,7 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
                 }
             }
             const bool head = cls == 1 && !joins;
-            if (head) scatter_group(t, key, (1u << lane) | heads_after(joined, lane), sums, max_len, stage + lane);
+            scatter_heads(t, head, key, (1u << lane) | heads_after(joined, lane), sums, max_len, stage + lane);
             *leaders += __popc(__ballot_sync(kFull, head));
         } else {
             // Every level: lanes on one key anywhere in the warp are found with match_any (the
@@ -481,7 +503,7 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
                 }
                 __syncwarp();
             }
-            if (cls == 1 && !donor) scatter_group(t, key, group, sums, max_len, stage + lane);
+            scatter_heads(t, cls == 1 && !donor, key, group, sums, max_len, stage + lane);
             *leaders += __popc(__ballot_sync(kFull, cls == 1 && !donor));
         }
     }
