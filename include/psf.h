@@ -17,7 +17,9 @@
  *     memory given to psf_create; the library owns only a small host-side header.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *     Calls enqueue work on it and return without waiting, except psf_export and
- *     psf_get_stats, which synchronise that stream.
+ *     psf_get_stats, which synchronise that stream.  psf_create and psf_destroy make no
+ *     allocation that synchronizes the device (the first psf_create of a process allocates
+ *     a slab of mapped status words).
  *   - Return value: PSF_OK (0) or a negative PSF_ERR_* code for errors detected on the
  *     host (nothing is enqueued then).  Conditions detected on the device set sticky
  *     bits (PSF_STATUS_*) in the table's device status word; psf_update returns them
@@ -199,7 +201,9 @@ int psf_export(psf_table* t, psf_cell_record* h_out, size_t cap, size_t* n_out, 
 int psf_get_stats(psf_table* t, psf_stats* out, void* stream);
 
 /* Release the host header (the caller frees d_mem).  All work enqueued on the table must
- * have completed (synchronise its stream first), as for freeing d_mem.  NULL is a no-op. */
+ * have completed (synchronise its stream first), as for freeing d_mem.  Makes no CUDA call
+ * (the table's mapped status word returns to a process-wide pool), so it never waits on the
+ * device.  NULL is a no-op. */
 int psf_destroy(psf_table* t);
 
 /* Launch knobs of a table's kernels (the autotuner's search space).  Results do not

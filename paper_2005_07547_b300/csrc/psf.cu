@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -40,6 +41,44 @@ bool psf_cuda_ok(cudaError_t e, const char* what) {
 namespace {
 
 bool cuda_ok(cudaError_t e, const char* what) { return psf_cuda_ok(e, what); }
+
+// Mapped pinned status words, one per table, handed out from slabs that live until the
+// process exits: creating and destroying a table (as a server does for every session) then
+// makes no pinned allocation or free, either of which can synchronize the device.
+struct StatusWord {
+    unsigned* host;
+    unsigned* dev;
+};
+
+std::mutex g_status_mu;
+std::vector<StatusWord> g_status_free;
+
+bool status_take(StatusWord* w) {
+    std::lock_guard<std::mutex> lock(g_status_mu);
+    if (g_status_free.empty()) {
+        constexpr unsigned kSlab = 4096;
+        unsigned* host = nullptr;
+        unsigned* dev = nullptr;
+        if (!cuda_ok(cudaHostAlloc(reinterpret_cast<void**>(&host), kSlab * sizeof(unsigned),
+                                   cudaHostAllocMapped | cudaHostAllocPortable),
+                     "cudaHostAlloc"))
+            return false;
+        if (!cuda_ok(cudaHostGetDevicePointer(reinterpret_cast<void**>(&dev), host, 0), "cudaHostGetDevicePointer")) {
+            cudaFreeHost(host);
+            return false;
+        }
+        g_status_free.reserve(g_status_free.size() + kSlab);
+        for (unsigned i = kSlab; i-- > 0;) g_status_free.push_back(StatusWord{host + i, dev + i});
+    }
+    *w = g_status_free.back();
+    g_status_free.pop_back();
+    return true;
+}
+
+void status_give(const StatusWord& w) {
+    std::lock_guard<std::mutex> lock(g_status_mu);
+    g_status_free.push_back(w);
+}
 
 struct Layout {
     size_t hdr, keys, slots, mirror, dirty, total;
@@ -531,12 +570,16 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->update_blocks_per_sm, k_update, kThreads, 0), "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->query_blocks_per_sm, k_query, kThreads, 0), "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->staged_query_blocks_per_sm, k_query_staged, kThreads, 0),
-                 "occupancy") ||
-        !cuda_ok(cudaHostAlloc(reinterpret_cast<void**>(&t->h_status), sizeof(unsigned), cudaHostAllocMapped),
-                 "cudaHostAlloc")) {
+                 "occupancy")) {
         delete t;
         return PSF_ERR_CUDA;
     }
+    StatusWord word;
+    if (!status_take(&word)) {
+        delete t;
+        return PSF_ERR_CUDA;
+    }
+    t->h_status = word.host;
     *t->h_status = 0;
     // direct vertex loads (measured: with bulk sums the TMA-staged tiles are slower, 133 vs
     // 120 us on 1280x720x4, as both go through the TMA unit), bulk sums
@@ -556,13 +599,8 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     v.slots = reinterpret_cast<Slot*>(base + L.slots);
     v.mirror = cfg->cache_fp16 ? reinterpret_cast<uint2*>(base + L.mirror) : nullptr;
     v.dirty = reinterpret_cast<unsigned*>(base + L.dirty);
-    unsigned* dev_status = nullptr;
-    if (!cuda_ok(cudaHostGetDevicePointer(reinterpret_cast<void**>(&dev_status), t->h_status, 0), "cudaHostGetDevicePointer")) {
-        cudaFreeHost(t->h_status);
-        delete t;
-        return PSF_ERR_CUDA;
-    }
-    v.h_status = dev_status;
+    v.h_status = word.dev;
+    t->d_status = word.dev;
     v.log2cap = cfg->log2_capacity;
     v.max_probe = std::min<uint32_t>(PSF_MAX_PROBE, 1u << std::min<uint32_t>(cfg->log2_capacity, 31u));
     v.q = cfg->pos_bits_q;
@@ -584,7 +622,7 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
         ok = cuda_ok(cudaGetLastError(), "k_init_keys");
     }
     if (!ok) {
-        cudaFreeHost(t->h_status);
+        status_give(word);
         delete t;
         return PSF_ERR_CUDA;
     }
@@ -765,7 +803,7 @@ int psf_get_stats(psf_table* t, psf_stats* out, void* stream) {
 
 int psf_destroy(psf_table* t) {
     if (!t) return PSF_OK;
-    cudaFreeHost(t->h_status);
+    status_give(StatusWord{t->h_status, t->d_status});  // no CUDA call: nothing here waits on the device
     delete t;
     return PSF_OK;
 }

@@ -13,7 +13,8 @@ struct psf_table {
     psf::TableView view;
     void* mem;
     size_t bytes;
-    unsigned* h_status;  // host-mapped pinned word written by the update
+    unsigned* h_status;  // host-mapped pinned word written by the update (from a process-wide pool)
+    unsigned* d_status;  // its device address
     int device;
     int sms;
     int update_blocks_per_sm;  // occupancy limits of the kernels (the inserts: occ_* below)

@@ -10,12 +10,17 @@ time.  Each server tick:
      persistent kernel for all of them (captured once in a CUDA graph and replayed;
      joins and leaves only rewrite the device descriptors), in "plain" mode one
      psf_step per session, back to back;
-  3. retires sessions that reached their iteration count and frees their tables.
+  3. retires sessions that reached their iteration count.
 
-Sessions are closed loops: a session's next iteration starts when its previous one has
-completed.  Per-iteration latency is the time from the start of a tick to the
-completion of that session's iteration; admission delay is the time from arrival to
-admission.  Every session's results are independent of who else is in the batch.
+Ticks are pipelined one deep in both modes: the host prepares and enqueues tick k+1 while
+the device runs tick k, and waits only for tick k-1's completion event, so the device does
+not idle while the host builds descriptors, admits or retires.  A retired session's table
+is freed once the tick holding its last iteration has completed (psf_destroy makes no CUDA
+call, so freeing never waits on the device); its memory counts against the budget until
+then.  A session's iterations are ordered on the one stream.  Per-iteration latency is the
+device time from the start of a tick to the completion of that session's iteration;
+admission delay is the time from arrival to admission.  Every session's results are
+independent of who else is in the batch.
 """
 
 from __future__ import annotations
@@ -77,6 +82,7 @@ class Server:
         self.vertices = 0
         self.admission_ms: list[float] = []
         self.on_retire = on_retire
+        self._inflight: deque = deque()  # (start event, end event(s), sessions, retiring sessions)
 
     # -- membership ---------------------------------------------------------------------
     def _admit(self, queue: deque, now: float) -> bool:
@@ -98,64 +104,70 @@ class Server:
             changed = True
         return changed
 
-    def _retire(self) -> bool:
-        keep, changed = [], False
+    def _retire(self) -> list:
+        """Sessions that have had their last iteration enqueued leave the live set (their
+        tables are freed once that iteration has completed)."""
+        keep, done = [], []
         for s in self.live:
-            if s.done >= s.request["iterations"]:
+            (done if s.done >= s.request["iterations"] else keep).append(s)
+        self.live = keep
+        return done
+
+    def _complete(self, keep: int) -> None:
+        """Wait for all but the newest `keep` ticks; record their latencies and free the
+        tables of the sessions they retired."""
+        while len(self._inflight) > keep:
+            start, ends, sessions, retiring = self._inflight.popleft()
+            ends[-1].synchronize()
+            for s, e in zip(sessions, ends if len(ends) == len(sessions) else [ends[-1]] * len(sessions)):
+                s.latencies_ms.append(start.elapsed_time(e))
+            for s in retiring:
                 if self.on_retire is not None:
                     self.on_retire(s)
                 self.used -= s.table.nbytes
-                s.table.close()
+                s.table.close(synchronize=False)  # its last iteration has completed
                 s.out = None
                 self.finished.append(s)
-                changed = True
-            else:
-                keep.append(s)
-        self.live = keep
-        return changed
 
     # -- one iteration of every live session ---------------------------------------------
     def _entries(self):
         return [(s.table, self.source(s.request, s.done), s.out, s.P, s.D) for s in self.live]
 
-    def _tick(self, membership_changed: bool) -> None:
+    def _tick(self) -> None:
         import torch
 
         start = torch.cuda.Event(enable_timing=True)
+        sessions = list(self.live)
         if self.mode == "batched":
             end = torch.cuda.Event(enable_timing=True)
-            # the descriptors point at each session's input of its current iteration
+            # the descriptors point at each session's input of its current iteration (the copy
+            # is ordered after the previous tick's kernel on the stream)
             self.batch.set(self._entries())
+            if self.use_graph and self.graph is None:
+                self.graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self.graph):
+                    self.batch.launch()
             start.record()
             if self.use_graph:
-                if self.graph is None:
-                    self.graph = torch.cuda.CUDAGraph()
-                    with torch.cuda.graph(self.graph):
-                        self.batch.launch()
-                    start.record()
                 self.graph.replay()
             else:
                 self.batch.launch()
             end.record()
-            end.synchronize()
-            ms = start.elapsed_time(end)
-            for s in self.live:
-                s.latencies_ms.append(ms)
+            ends = [end]
         else:
-            evs = []
+            ends = []
             start.record()
-            for s in self.live:
+            for s in sessions:
                 s.table.step(self.source(s.request, s.done), s.P, s.D, out=s.out)
                 e = torch.cuda.Event(enable_timing=True)
                 e.record()
-                evs.append(e)
-            evs[-1].synchronize()
-            for s, e in zip(self.live, evs):
-                s.latencies_ms.append(start.elapsed_time(e))
-        for s in self.live:
+                ends.append(e)
+        for s in sessions:
             s.done += 1
             self.vertices += s.P * s.D
         self.ticks += 1
+        self._inflight.append((start, ends, sessions, self._retire()))
+        self._complete(keep=1)
 
     # -- driver ---------------------------------------------------------------------------
     def run(self, requests: list[dict], duration_s: float, drain: bool = False) -> dict:
@@ -164,22 +176,22 @@ class Server:
         pending = deque(sorted(requests, key=lambda r: r["arrival_s"]))
         queue: deque = deque()
         t0 = time.perf_counter()
-        changed = True
         while True:
             now = time.perf_counter() - t0
             while pending and pending[0]["arrival_s"] <= now:
                 queue.append(pending.popleft())
             if now < duration_s:
-                changed |= self._admit(queue, now)
+                self._admit(queue, now)
             elif not drain or not self.live:
                 break
             if not self.live:
+                self._complete(keep=0)
                 if not pending:
                     break
                 time.sleep(max(0.0, min(pending[0]["arrival_s"] - now, 0.01)))
                 continue
-            self._tick(changed)
-            changed = self._retire()
+            self._tick()
+        self._complete(keep=0)
         wall = time.perf_counter() - t0
         lat = [x for s in self.finished + self.live for x in s.latencies_ms]
         report = {
@@ -196,6 +208,7 @@ class Server:
         return report
 
     def close(self) -> None:
+        self._complete(keep=0)
         for s in self.live:
             s.table.close()
         self.live = []

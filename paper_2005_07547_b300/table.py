@@ -140,12 +140,15 @@ class Table:
         _abi.check(_abi.load().psf_get_launch_config(self._h, ctypes.byref(lc)), "psf_get_launch_config")
         return {name: getattr(lc, name) for name, _ in lc._fields_}
 
-    def close(self) -> None:
-        """Wait for the table's work, then release it."""
+    def close(self, synchronize: bool = True) -> None:
+        """Release the table: first wait for the device, unless the caller already knows
+        that every kernel enqueued on the table has completed (synchronize=False; then
+        nothing here waits on the device)."""
         import torch
 
         if getattr(self, "_h", None) is not None and self._h.value:
-            torch.cuda.synchronize(self.device)
+            if synchronize:
+                torch.cuda.synchronize(self.device)
             _abi.load().psf_destroy(self._h)
             self._h = ctypes.c_void_p()
         self.mem = None

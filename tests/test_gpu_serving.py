@@ -86,9 +86,9 @@ def test_admission_respects_the_memory_budget(psf_mod):
     peak = []
 
     class Tracking(Server):
-        def _tick(self, changed):
+        def _tick(self):
             peak.append((len(self.live), self.used))
-            super()._tick(changed)
+            super()._tick()
 
     srv = Tracking(src, budget_bytes=budget, mode="batched")
     rep = srv.run(reqs, duration_s=30.0, drain=True)
