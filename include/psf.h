@@ -125,7 +125,9 @@ typedef struct {
     uint64_t table_bytes;          /* psf_table_bytes of the configuration */
     uint64_t touched_cells;        /* cells blended by all psf_update calls so far */
     uint64_t leader_groups;        /* (warp, key) groups that probed and added, all inserts so far
-                                      (each issues five atomics); not counted by batched launches */
+                                      (each issues one bulk reduction of its sums, or four 64-bit
+                                      reductions, plus one bitmap reduction); not counted by batched
+                                      launches */
 } psf_stats;
 
 /* Bytes of device memory a table with this configuration needs (0 if the
@@ -212,8 +214,9 @@ int psf_destroy(psf_table* t);
  * a zero grid cap means the occupancy limit.  A batch (psf_batch_set) copies each table's
  * sum_reduction when its descriptors are set. */
 typedef struct {
-    uint32_t insert_mode;          /* 0: lanes of a warp holding the same key are merged (match_any)
-                                      and one leader probes and adds; 1: every vertex adds on its own */
+    uint32_t insert_mode;          /* 0: lanes of a warp holding the same key are merged (runs of
+                                      adjacent lanes; any lanes, by match_any, with hierarchy levels)
+                                      and one head probes and adds; 1: every vertex adds on its own */
     uint32_t insert_blocks_per_sm; /* cap on resident 256-thread blocks per SM (0 = occupancy limit) */
     uint32_t update_blocks_per_sm;
     uint32_t query_blocks_per_sm;

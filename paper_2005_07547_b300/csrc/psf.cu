@@ -1,9 +1,10 @@
 // psf.cu -- kernels and C ABI of the progressive spatio-temporal filtering hot path.
 //
 // Per iteration (one table = one render session):
-//   k_insert  one thread per vertex, lanes with equal keys merged by match_any, one
-//             leader per key probes the open-addressing table and adds the group's
-//             64-bit fixed-point sums with four atomics (eq. 5-6, Alg. 1)
+//   k_insert  one thread per vertex, lanes of a warp on one key merged (adjacent runs,
+//             or match_any with hierarchy levels), one head per group probes the
+//             open-addressing table and adds the group's 64-bit fixed-point sums with one
+//             bulk (TMA) reduction (eq. 5-6, Alg. 1)
 //   k_update  one warp per 1024 slots of the dirty bitmap, set bits compacted across
 //             the warp, one lane per touched cell applies eq. (10)-(11)
 //   k_query   one thread per path, walking its vertices from the last to the first,

@@ -53,7 +53,7 @@ struct alignas(64) Slot {
 static_assert(sizeof(Slot) == 64, "one slot is one 64-byte block");
 
 // Insert aggregation modes (a launch-time choice, results are identical)
-constexpr int kAggWarp = 0;  // lanes with equal keys merged (match_any), one probe per key per warp
+constexpr int kAggWarp = 0;  // lanes of a warp on one key merged, one probe per group
 constexpr int kAggNone = 1;  // every vertex probes and adds on its own
 
 struct TableView {
