@@ -382,3 +382,34 @@ def test_key_layouts_give_identical_tables(psf_mod, fp16):
         runs.append((t.export().tobytes(), np.concatenate(outs).tobytes(), st["live_cells"], st["status"]))
         t.close()
     assert runs[0] == runs[1]
+
+
+def test_many_tables_reuse_pooled_status_words(psf_mod):
+    """Tables take their mapped status words from slabs of 4096: creating and freeing more
+    tables than a slab holds, some alive at once, leaves every table working."""
+    import torch
+
+    from helpers import random_vertices
+
+    rng = np.random.default_rng(5)
+    v = torch.from_numpy(random_vertices(rng, 96, q=2, cells_per_axis=3)).cuda()
+    cfg = psf_mod.make_config(log2_capacity=10, pos_bits=2, dir_bits=1)  # 96 crowded vertices fit easily
+    alive = []
+    for k in range(4500):
+        t = psf_mod.Table(cfg)
+        if k % 500 == 0:
+            t.insert(v)
+            assert t.update() >= 0
+            st = t.stats()
+            assert st["status"] == 0 and st["iterations"] == 1 and st["live_cells"] > 0
+        if k % 3 == 0:
+            alive.append(t)  # keep a third alive so that words are in use while others recycle
+        else:
+            torch.cuda.synchronize()
+            t.close(synchronize=False)
+    for t in alive[::97]:
+        t.insert(v)
+        t.update()
+        assert t.stats()["status"] == 0
+    for t in alive:
+        t.close()
