@@ -69,7 +69,7 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def algorithmic_bytes(V: int, touched: float, cache_fp16: bool) -> dict:
+def algorithmic_bytes(V: int, touched: float, cache_fp16: bool, slot_cache: bool = False) -> dict:
     """Bytes each kernel must move at minimum (per launch).
 
     insert: read the 64-B vertex record of every vertex; per touched cell read its
@@ -78,11 +78,13 @@ def algorithmic_bytes(V: int, touched: float, cache_fp16: bool) -> dict:
             approximant and the 8-B c_old, write the 8-B FP16 copy (112 or 120).
     query:  read the 64-B record and write the 12-B output of every vertex; per
             touched cell read its key and its approximant (8 + 16, or 8 + 8 for FP16).
+    With the slot cache the insert also writes, and the query reads, a 4-B slot per vertex.
     """
+    extra = 4.0 * V if slot_cache else 0.0
     return {
-        "k_insert": 64.0 * V + 72.0 * touched,
+        "k_insert": 64.0 * V + 72.0 * touched + extra,
         "k_update": (120.0 if cache_fp16 else 112.0) * touched,
-        "k_query": 76.0 * V + (16.0 if cache_fp16 else 24.0) * touched,
+        "k_query": 76.0 * V + (16.0 if cache_fp16 else 24.0) * touched + extra,
     }
 
 
@@ -393,10 +395,24 @@ def run_psf(args) -> None:
     out = torch.empty((V, 3), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    slots = torch.empty(V, dtype=torch.int32, device="cuda") if args.slot_cache else None
+
+    def insert(v):
+        if slots is not None:
+            table.insert_slots(v, P, D, slots=slots)
+        else:
+            table.insert(v)
+
+    def query(v):
+        if slots is not None:
+            table.query_cv_slots(v, slots, P, D, out=out)
+        else:
+            table.query_cv(v, P, D, out=out)
+
     for k in range(args.warmup):
-        table.insert(dev[k % n_iter])
+        insert(dev[k % n_iter])
         table.update()
-        table.query_cv(dev[k % n_iter], P, D, out=out)
+        query(dev[k % n_iter])
     torch.cuda.synchronize()
     before = table.stats()
 
@@ -411,11 +427,11 @@ def run_psf(args) -> None:
             v = dev[(args.warmup + k) % n_iter]
             e = ev[k]
             e[0].record(stream)
-            table.insert(v)
+            insert(v)
             e[1].record(stream)
             table.update()
             e[2].record(stream)
-            table.query_cv(v, P, D, out=out)
+            query(v)
             e[3].record(stream)
         end.record(stream)
         torch.cuda.synchronize()
@@ -443,11 +459,11 @@ def run_psf(args) -> None:
 
     # end to end through the public API: pinned host vertices in, host CV outputs back,
     # copies inside the timed region, H2D of step k+1 overlapped with compute of step k
-    e2e = run_e2e(psf, table, host, P, D, args.e2e_steps) if rank == 0 else None
+    e2e = run_e2e(psf, table, host, P, D, args.e2e_steps, bool(args.slot_cache)) if rank == 0 else None
 
     peaks = load_peaks()
     fp16 = bool(cfg.cache_fp16)
-    alg = algorithmic_bytes(V, touched, fp16)
+    alg = algorithmic_bytes(V, touched, fp16, bool(args.slot_cache))
     avg = {k: sum(v) / len(v) for k, v in kt.items()}
     dominant = max(avg, key=avg.get)
     achieved = alg[dominant] / (avg[dominant] / 1e3) / 1e9
@@ -474,7 +490,8 @@ def run_psf(args) -> None:
     hbm = {"achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
            "peak_source": peaks["source"], "algorithmic_bytes_per_launch": alg[dominant]}
     staged = {"k_insert": bool(args.staging & 1), "k_query": bool(args.staging & 2)}.get(dominant, False)
-    setup = {"workload": w["name"], "cache": "fp16" if fp16 else "fp32", "levels": args.levels, "log2_capacity": log2cap}
+    setup = {"workload": w["name"], "cache": "fp16" if fp16 else "fp32", "levels": args.levels, "log2_capacity": log2cap,
+             "slot_cache": bool(args.slot_cache)}
     roofline = {"kernel": dominant, "traffic": load_traffic(dominant, staged, setup), "hbm": hbm}
     binding = hbm
     roofline["bound"] = "hbm"
@@ -504,6 +521,7 @@ def run_psf(args) -> None:
                          "a different one every step",
                    "insert_mode": args.insert_mode, "vertex_staging": args.staging,
                    "sum_reduction": {0: "bulk (TMA) 32-B reduction", 1: "4 x red.add.u64"}[args.sum_reduction],
+                   "slot_cache": bool(args.slot_cache),
                    "key_layout": {0: "auto", 1: "dense key array", 2: "keys in slot records"}[args.key_layout],
                    "parallelism": f"sessions x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -522,9 +540,10 @@ def run_psf(args) -> None:
         dist.destroy_process_group()
 
 
-def run_e2e(psf, table, host: list[np.ndarray], P: int, D: int, steps: int) -> dict:
-    """Vertices/s through Table.insert/update/query_cv with host buffers: each step copies its
-    batch from pinned host memory and reads the CV outputs back into pinned host memory."""
+def run_e2e(psf, table, host: list[np.ndarray], P: int, D: int, steps: int, slot_cache: bool = True) -> dict:
+    """Vertices/s through Table.insert(_slots)/update/query_cv(_slots) with host buffers: each
+    step copies its batch from pinned host memory and reads the CV outputs back into pinned
+    host memory."""
     import torch
 
     V = P * D
@@ -533,6 +552,7 @@ def run_e2e(psf, table, host: list[np.ndarray], P: int, D: int, steps: int) -> d
     out_host = [torch.empty((V, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
     dev_in = [torch.empty((V, 16), dtype=torch.float32, device="cuda") for _ in range(2)]
     dev_out = [torch.empty((V, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    slots = torch.empty(V, dtype=torch.int32, device="cuda")  # used on the compute stream only
     compute = torch.cuda.current_stream()
     copy = torch.cuda.Stream()
     ready = [torch.cuda.Event() for _ in range(2)]
@@ -551,9 +571,14 @@ def run_e2e(psf, table, host: list[np.ndarray], P: int, D: int, steps: int) -> d
         if s >= 1:  # compute step s - 1
             pb = (s - 1) % 2
             compute.wait_event(ready[pb])
-            table.insert(dev_in[pb])
-            table.update()
-            table.query_cv(dev_in[pb], P, D, out=dev_out[pb])
+            if slot_cache:
+                table.insert_slots(dev_in[pb], P, D, slots=slots)
+                table.update()
+                table.query_cv_slots(dev_in[pb], slots, P, D, out=dev_out[pb])
+            else:
+                table.insert(dev_in[pb])
+                table.update()
+                table.query_cv(dev_in[pb], P, D, out=dev_out[pb])
             out_host[pb].copy_(dev_out[pb], non_blocking=True)
             free[pb].record(compute)
     end.record(compute)
@@ -797,6 +822,8 @@ def main(argv=None) -> None:
     ap.add_argument("--key-layout", type=int, default=0, help="0: auto, 1: dense key array, 2: keys in slot records")
     ap.add_argument("--levels", type=int, default=1, help="hierarchy levels of the table (1: flat)")
     ap.add_argument("--sum-reduction", type=int, default=0, help="0: one bulk (TMA) reduction per group, 1: four red.add")
+    ap.add_argument("--slot-cache", type=int, default=1,
+                    help="1: the insert notes each vertex's slot and the query reads it there; 0: the query probes")
     ap.add_argument("--pool", type=int, default=4, help="distinct resident iterations per session (batched)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")

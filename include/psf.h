@@ -186,6 +186,21 @@ int psf_query_cv(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, 
 int psf_query_biased(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float gamma, uint32_t j_begin,
                      uint32_t j_end, float* d_out_rgb, void* stream);
 
+/* The slot cache (an insert notes where each vertex's query will read):
+ * psf_insert_slots is psf_insert of D*P depth-major records (the same table afterwards) that
+ * also writes d_slots[i] = the slot of vertex i's cell at the level its query reads (level
+ * min(j, levels - 1) at depth j), or PSF_NO_SLOT when the vertex was not added (range rule,
+ * zero weight, full table).  psf_query_cv_slots is psf_query_cv over the same records (the
+ * same outputs, bit for bit) reading the approximant at d_slots[i] instead of hashing and
+ * probing, and probing as usual where d_slots[i] is PSF_NO_SLOT.  The slots stay valid for
+ * the table's lifetime (cells never move), so one insert's slots serve the query that
+ * follows its update.  d_slots: D*P uint32, caller-owned, 4-byte aligned.  The insert always
+ * loads its vertex records directly (vertex_staging bit 0 does not apply). */
+#define PSF_NO_SLOT 0xFFFFFFFFu
+int psf_insert_slots(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, uint32_t* d_slots, void* stream);
+int psf_query_cv_slots(psf_table* t, const float* d_vertices, const uint32_t* d_slots, uint32_t P, uint32_t D,
+                       float* d_out_rgb, void* stream);
+
 /* One whole iteration: psf_insert of the D*P vertices, psf_update, psf_query_cv. */
 int psf_step(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float* d_out_rgb,
              void* stream);
@@ -311,7 +326,7 @@ int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, const psf_ba
 const char* psf_last_cuda_error(void);
 
 /* ABI version of this header: bump on any incompatible change. */
-#define PSF_ABI_VERSION 4
+#define PSF_ABI_VERSION 5
 int psf_abi_version(void);
 
 #ifdef __cplusplus

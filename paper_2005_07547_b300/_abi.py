@@ -146,6 +146,8 @@ SIGNATURES = {
     "psf_batch_destroy": (_i, [_vp]),
     "psf_batch_step_noalloc": (_i, [ctypes.POINTER(BatchItem), _u32, ctypes.POINTER(BatchConfig), _vp]),
     "psf_get_launch_config": (_i, [_vp, ctypes.POINTER(LaunchConfig)]),
+    "psf_insert_slots": (_i, [_vp, _vp, _u32, _u32, _vp, _vp]),
+    "psf_query_cv_slots": (_i, [_vp, _vp, _vp, _u32, _u32, _vp, _vp]),
 }
 
 _lib = None

@@ -138,8 +138,11 @@ int grid_for(const psf_table* t, int per_sm, unsigned long long work_items, uint
 // Kernels
 // ---------------------------------------------------------------------------
 
-template <int kMode, bool kHier>
-__global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* __restrict__ v, unsigned long long n) {
+// With kSlots the kernel also notes each vertex's slot for the query (slots[i]; vertices
+// are depth-major records of P paths, so vertex i has depth i / P).
+template <int kMode, bool kHier, bool kSlots = false>
+__global__ void __launch_bounds__(kThreads, kHier ? 4 : 0) k_insert(TableView t, const float4* __restrict__ v, unsigned long long n,
+                                                     unsigned P = 0, unsigned* __restrict__ slots = nullptr) {
     __shared__ unsigned s_max_probe;
     __shared__ unsigned long long s_leaders;
     __shared__ psf::LaneSums s_stage[kThreads];
@@ -172,7 +175,14 @@ __global__ void __launch_bounds__(kThreads) k_insert(TableView t, const float4* 
             n2 = __ldcs(r + 2);
             n3 = __ldcs(r + 3);
         }
-        psf::insert_warp<kMode, kHier>(t, base + threadIdx.x < n, v0, v1, v2, v3, &max_len, stage, &leaders);
+        if constexpr (kSlots) {
+            const unsigned long long i = base + threadIdx.x;
+            psf::SlotNote note{kHier ? psf::read_level(t, static_cast<unsigned>(i / P)) : 0u, psf::kNoSlot};
+            psf::insert_warp<kMode, kHier, true>(t, i < n, v0, v1, v2, v3, &max_len, stage, &leaders, &note);
+            if (i < n) slots[i] = note.slot;
+        } else {
+            psf::insert_warp<kMode, kHier>(t, base + threadIdx.x < n, v0, v1, v2, v3, &max_len, stage, &leaders);
+        }
         v0 = n0;
         v1 = n1;
         v2 = n2;
@@ -408,12 +418,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_update(TableView t) {
     if (threadIdx.x == 0 && s_touched) atomicAdd(&t.hdr->touched, s_touched);
 }
 
+template <bool kSlots = false>
 __global__ void __launch_bounds__(kThreads) k_query(TableView t, psf::Estimator e, const float4* __restrict__ v,
-                                                    unsigned P, unsigned D, float* __restrict__ out) {
+                                                    unsigned P, unsigned D, float* __restrict__ out,
+                                                    const unsigned* __restrict__ slots = nullptr) {
     const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
     for (unsigned long long p = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < P;
          p += stride)
-        psf::query_path(t, e, v, P, D, p, out);
+        psf::query_path<kSlots>(t, e, v, P, D, p, out, slots);
 }
 
 __global__ void __launch_bounds__(kThreads) k_export(TableView t, unsigned long long s0, unsigned long long s1,
@@ -525,10 +537,19 @@ void launch_insert(const psf_table* t, const float4* v, unsigned long long n, cu
         else
             launch_sized(t, k_insert_staged<psf::kAggWarp, kHier>, n, st, t->view, v, n);
     } else if (none) {
-        launch_sized(t, k_insert<psf::kAggNone, kHier>, n, st, t->view, v, n);
+        launch_sized(t, k_insert<psf::kAggNone, kHier>, n, st, t->view, v, n, 0u, static_cast<unsigned*>(nullptr));
     } else {
-        launch_sized(t, k_insert<psf::kAggWarp, kHier>, n, st, t->view, v, n);
+        launch_sized(t, k_insert<psf::kAggWarp, kHier>, n, st, t->view, v, n, 0u, static_cast<unsigned*>(nullptr));
     }
+}
+
+template <bool kHier>
+void launch_insert_slots(const psf_table* t, const float4* v, uint32_t P, uint32_t D, unsigned* slots, cudaStream_t st) {
+    const unsigned long long n = static_cast<unsigned long long>(P) * D;
+    if (t->launch.insert_mode == 1)
+        launch_sized(t, k_insert<psf::kAggNone, kHier, true>, n, st, t->view, v, n, P, slots);
+    else
+        launch_sized(t, k_insert<psf::kAggWarp, kHier, true>, n, st, t->view, v, n, P, slots);
 }
 
 template <bool kHier>
@@ -569,7 +590,7 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     if (!cuda_ok(cudaGetDevice(&t->device), "cudaGetDevice") ||
         !cuda_ok(cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device), "cudaDeviceGetAttribute") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->update_blocks_per_sm, k_update, kThreads, 0), "occupancy") ||
-        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->query_blocks_per_sm, k_query, kThreads, 0), "occupancy") ||
+        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->query_blocks_per_sm, k_query<false>, kThreads, 0), "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->staged_query_blocks_per_sm, k_query_staged, kThreads, 0),
                  "occupancy")) {
         delete t;
@@ -682,7 +703,7 @@ int launch_query(psf_table* t, const psf::Estimator& e, const float* d_vertices,
         k_query_staged<<<grid, kThreads, 0, st>>>(t->view, e, v, P, D, d_out_rgb);
     } else {
         const int grid = grid_for(t, t->query_blocks_per_sm, P, t->launch.query_blocks_per_sm);
-        k_query<<<grid, kThreads, 0, st>>>(t->view, e, v, P, D, d_out_rgb);
+        k_query<false><<<grid, kThreads, 0, st>>>(t->view, e, v, P, D, d_out_rgb);
     }
     return cuda_ok(cudaGetLastError(), "k_query") ? PSF_OK : PSF_ERR_CUDA;
 }
@@ -698,6 +719,37 @@ int psf_query_biased(psf_table* t, const float* d_vertices, uint32_t P, uint32_t
                      uint32_t j_end, float* d_out_rgb, void* stream) {
     if (!t || !(gamma == gamma)) return PSF_ERR_INVALID_ARG;
     return launch_query(t, psf::Estimator{gamma, gamma, 1.0f, j_begin, j_end}, d_vertices, P, D, d_out_rgb, stream);
+}
+
+int psf_insert_slots(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, uint32_t* d_slots, void* stream) {
+    if (!t) return PSF_ERR_INVALID_ARG;
+    const unsigned long long n = static_cast<unsigned long long>(P) * D;
+    if (n == 0) return PSF_OK;
+    if (!d_vertices || !d_slots || (reinterpret_cast<uintptr_t>(d_vertices) & 15u) ||
+        (reinterpret_cast<uintptr_t>(d_slots) & 3u))
+        return PSF_ERR_INVALID_ARG;
+    const float4* v = reinterpret_cast<const float4*>(d_vertices);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (t->view.levels > 1)
+        launch_insert_slots<true>(t, v, P, D, d_slots, st);
+    else
+        launch_insert_slots<false>(t, v, P, D, d_slots, st);
+    return cuda_ok(cudaGetLastError(), "k_insert") ? PSF_OK : PSF_ERR_CUDA;
+}
+
+int psf_query_cv_slots(psf_table* t, const float* d_vertices, const uint32_t* d_slots, uint32_t P, uint32_t D,
+                       float* d_out_rgb, void* stream) {
+    if (!t) return PSF_ERR_INVALID_ARG;
+    if (P == 0 || D == 0) return PSF_OK;
+    if (!d_vertices || !d_slots || !d_out_rgb || (reinterpret_cast<uintptr_t>(d_vertices) & 15u) ||
+        (reinterpret_cast<uintptr_t>(d_slots) & 3u) || (reinterpret_cast<uintptr_t>(d_out_rgb) & 3u))
+        return PSF_ERR_INVALID_ARG;
+    const float4* v = reinterpret_cast<const float4*>(d_vertices);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int grid = grid_for(t, resident_blocks(t, reinterpret_cast<const void*>(k_query<true>)), P,
+                              t->launch.query_blocks_per_sm);
+    k_query<true><<<grid, kThreads, 0, st>>>(t->view, psf::cv_estimator(t->view), v, P, D, d_out_rgb, d_slots);
+    return cuda_ok(cudaGetLastError(), "k_query") ? PSF_OK : PSF_ERR_CUDA;
 }
 
 int psf_step(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, float* d_out_rgb, void* stream) {

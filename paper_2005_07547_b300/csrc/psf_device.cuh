@@ -388,9 +388,10 @@ __device__ __forceinline__ void add_group(const TableView& t, long long slot, un
 }
 
 // Probe for every lane with `head` set (the whole warp calls this), then each head adds
-// its group's sums.
-__device__ __forceinline__ void scatter_heads(const TableView& t, bool head, unsigned long long key, unsigned members,
-                                              const long long sums[4], unsigned* max_len, LaneSums* src) {
+// its group's sums.  Returns the head's slot (-1 for other lanes or a full table).
+__device__ __forceinline__ long long scatter_heads(const TableView& t, bool head, unsigned long long key,
+                                                   unsigned members, const long long sums[4], unsigned* max_len,
+                                                   LaneSums* src) {
     long long slot;
     unsigned len;
     probe_warp(t, head, key, &slot, &len);
@@ -398,7 +399,18 @@ __device__ __forceinline__ void scatter_heads(const TableView& t, bool head, uns
         *max_len = len > *max_len ? len : *max_len;
         add_group(t, slot, members, sums, src);
     }
+    return head ? slot : -1;
 }
+
+// The slot cache: an insert can note, for each vertex, the slot of the cell its query will
+// read (the level min(j, levels - 1) for path depth j), so that the query reads the
+// approximant there without hashing or probing.  kNoSlot: the vertex was not added (range
+// rule, zero weight, full table); its query probes as usual.
+constexpr unsigned kNoSlot = 0xffffffffu;
+struct SlotNote {
+    unsigned level;  // in: the hierarchy level whose slot to note
+    unsigned slot;   // out: that slot, or kNoSlot
+};
 
 // The lanes after `lane` that continue its run (the consecutive set bits of `joined` from
 // lane + 1 on), which a run's head reports as its members.
@@ -417,10 +429,10 @@ __device__ __forceinline__ unsigned heads_after(unsigned joined, unsigned lane) 
 // them).  A lane's LaneSums slot holds its own sums while a kHier group merges and the sums
 // its bulk reduction reads; every write to the slot waits for the lane's earlier bulk
 // reductions to have read it.
-template <int kMode, bool kHier = false>
+template <int kMode, bool kHier = false, bool kSlots = false>
 __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, const float4& v0, const float4& v1,
                                             const float4& v2, const float4& v3, unsigned* max_len,
-                                            LaneSums* stage, unsigned* leaders) {
+                                            LaneSums* stage, unsigned* leaders, SlotNote* note = nullptr) {
     const unsigned lane = threadIdx.x & 31u;
     unsigned long long key0 = 0;
     long long own[4] = {0, 0, 0, 0};
@@ -442,9 +454,14 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
         if (zero_w) atomicAdd(&t.hdr->zero_weight, static_cast<unsigned long long>(__popc(zero_w)));
     }
     const unsigned nlevels = kHier ? t.levels : 1u;
+    if constexpr (kSlots) note->slot = kNoSlot;
     if (kMode == kAggNone) {
-        for (unsigned l = 0; l < nlevels; ++l)
-            scatter_heads(t, cls == 1, kHier ? level_key(key0, l) : key0, 1u << lane, own, max_len, stage + lane);
+        for (unsigned l = 0; l < nlevels; ++l) {
+            const long long hs =
+                scatter_heads(t, cls == 1, kHier ? level_key(key0, l) : key0, 1u << lane, own, max_len, stage + lane);
+            if constexpr (kSlots)
+                if (l == note->level && hs >= 0) note->slot = static_cast<unsigned>(hs);
+        }
         *leaders += nlevels * __popc(accepted);
         return;
     }
@@ -474,8 +491,15 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
                 }
             }
             const bool head = cls == 1 && !joins;
-            scatter_heads(t, head, key, (1u << lane) | heads_after(joined, lane), sums, max_len, stage + lane);
+            const long long hs =
+                scatter_heads(t, head, key, (1u << lane) | heads_after(joined, lane), sums, max_len, stage + lane);
             *leaders += __popc(__ballot_sync(kFull, head));
+            if constexpr (kSlots) {
+                // a lane's head: the last lane at or before it that does not continue a run
+                const unsigned upto = lane == 31 ? kFull : ((2u << lane) - 1u);
+                const long long s = __shfl_sync(kFull, hs, 31 - __clz(~joined & upto));
+                if (cls == 1 && l == note->level && s >= 0) note->slot = static_cast<unsigned>(s);
+            }
         } else {
             // Every level: lanes on one key anywhere in the warp are found with match_any (the
             // coarser levels repeat keys across the warp); a group's lowest lane adds the other
@@ -503,8 +527,12 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
                 }
                 __syncwarp();
             }
-            scatter_heads(t, cls == 1 && !donor, key, group, sums, max_len, stage + lane);
+            const long long hs = scatter_heads(t, cls == 1 && !donor, key, group, sums, max_len, stage + lane);
             *leaders += __popc(__ballot_sync(kFull, cls == 1 && !donor));
+            if constexpr (kSlots) {
+                const long long s = __shfl_sync(kFull, hs, cls == 1 ? __ffs(group) - 1 : static_cast<int>(lane));
+                if (cls == 1 && l == note->level && s >= 0) note->slot = static_cast<unsigned>(s);
+            }
         }
     }
 }
@@ -677,15 +705,24 @@ __device__ __forceinline__ float combine(const Estimator& e, float L, float tj, 
 }
 
 // All vertices of path p (depth-major records j*P + p), last to first so that each vertex
-// is probed once: its cell value serves as C_j here and as C_{j+1} for vertex j - 1.
+// is probed once: its cell value serves as C_j here and as C_{j+1} for vertex j - 1.  With
+// kSlots a vertex whose slot the insert noted reads the approximant there directly.
+template <bool kSlots = false>
 __device__ __forceinline__ void query_path(const TableView& t, const Estimator& e, const float4* __restrict__ v,
-                                           unsigned P, unsigned D, unsigned long long p, float* __restrict__ out) {
+                                           unsigned P, unsigned D, unsigned long long p, float* __restrict__ out,
+                                           const unsigned* __restrict__ slots = nullptr) {
     float3 c_next = make_float3(0.0f, 0.0f, 0.0f);
     for (int j = static_cast<int>(D) - 1; j >= 0; --j) {
         const unsigned long long i = static_cast<unsigned long long>(j) * P + p;
         const float4* r = v + 4 * i;  // streamed once: evict-first
         const float4 v0 = __ldcs(r), v1 = __ldcs(r + 1), v2 = __ldcs(r + 2), v3 = __ldcs(r + 3);
-        const float3 c = cell_value(t, v0, v1, v2, false, read_level(t, static_cast<unsigned>(j)));
+        float3 c;
+        if constexpr (kSlots) {
+            const unsigned sl = __ldcs(slots + i);
+            c = sl != kNoSlot ? value_at(t, sl) : cell_value(t, v0, v1, v2, false, read_level(t, static_cast<unsigned>(j)));
+        } else {
+            c = cell_value(t, v0, v1, v2, false, read_level(t, static_cast<unsigned>(j)));
+        }
         float o0 = v3.x, o1 = v3.y, o2 = v3.z;
         if (j + 1 < static_cast<int>(D) && static_cast<unsigned>(j) >= e.j_begin && static_cast<unsigned>(j) < e.j_end) {
             o0 = combine(e, v3.x, v1.w, c_next.x, c.x);

@@ -65,6 +65,22 @@ class Table:
         _abi.check(_abi.load().psf_insert_progressive(self._h, verts.data_ptr(), P, D, field, _stream_handle(stream)),
                    "psf_insert_progressive")
 
+    def insert_slots(self, verts, P: int, D: int, slots=None, stream=None):
+        """psf_insert of D*P depth-major records that also notes, per vertex, the slot its
+        query will read (int32 view of uint32; -1 is PSF_NO_SLOT).  Returns the slots."""
+        import torch
+
+        _check_vertices(verts, "insert_slots")
+        if verts.shape[0] != P * D:
+            raise ValueError("insert_slots: vertex count must be P*D")
+        if slots is None:
+            slots = torch.empty(P * D, dtype=torch.int32, device=verts.device)
+        if slots.dtype != torch.int32 or slots.numel() != P * D or not slots.is_contiguous():
+            raise ValueError("insert_slots: slots must be a contiguous int32 tensor of P*D")
+        _abi.check(_abi.load().psf_insert_slots(self._h, verts.data_ptr(), P, D, slots.data_ptr(),
+                                                _stream_handle(stream)), "psf_insert_slots")
+        return slots
+
     def update(self, stream=None) -> int:
         return _abi.check(_abi.load().psf_update(self._h, _stream_handle(stream)), "psf_update")
 
@@ -78,6 +94,19 @@ class Table:
             out = torch.empty((P * D, 3), dtype=torch.float32, device=verts.device)
         _abi.check(_abi.load().psf_query_cv(self._h, verts.data_ptr(), P, D, out.data_ptr(),
                                             _stream_handle(stream)), "psf_query_cv")
+        return out
+
+    def query_cv_slots(self, verts, slots, P: int, D: int, out=None, stream=None):
+        """query_cv reading each vertex's approximant at the slot insert_slots noted."""
+        import torch
+
+        _check_vertices(verts, "query_cv_slots")
+        if verts.shape[0] != P * D or slots.numel() != P * D or slots.dtype != torch.int32:
+            raise ValueError("query_cv_slots: P*D vertices and P*D int32 slots")
+        if out is None:
+            out = torch.empty((P * D, 3), dtype=torch.float32, device=verts.device)
+        _abi.check(_abi.load().psf_query_cv_slots(self._h, verts.data_ptr(), slots.data_ptr(), P, D, out.data_ptr(),
+                                                  _stream_handle(stream)), "psf_query_cv_slots")
         return out
 
     def query_biased(self, verts, P: int, D: int, gamma: float, j_begin: int = 0, j_end: int = 0xFFFFFFFF, out=None,
