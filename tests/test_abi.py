@@ -114,6 +114,8 @@ def test_host_detected_argument_errors(lib):
     assert lib.psf_update(None, None) == _abi.PSF_ERR_INVALID_ARG
     assert lib.psf_query_cv(None, None, 1, 1, None, None) == _abi.PSF_ERR_INVALID_ARG
     assert lib.psf_reset(None, None) == _abi.PSF_ERR_INVALID_ARG
+    assert lib.psf_insert_slots(None, None, 1, 1, None, None) == _abi.PSF_ERR_INVALID_ARG
+    assert lib.psf_query_cv_slots(None, None, None, 1, 1, None, None) == _abi.PSF_ERR_INVALID_ARG
     assert lib.psf_destroy(None) == _abi.PSF_OK
     assert lib.psf_abi_version() == 5
 

@@ -1,0 +1,37 @@
+"""Host-side bookkeeping of the benchmark: the algorithmic bytes that the roofline divides by,
+and the committed DRAM traffic, which applies only to the setup it was captured on."""
+
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def test_algorithmic_bytes_per_launch():
+    V, C = 1000, 300
+    a = bench.algorithmic_bytes(V, C, cache_fp16=False)
+    assert a == {"k_insert": 64 * V + 72 * C, "k_update": 112 * C, "k_query": 76 * V + 24 * C}
+    b = bench.algorithmic_bytes(V, C, cache_fp16=True, slot_cache=True)
+    assert b == {"k_insert": 64 * V + 72 * C + 4 * V, "k_update": 120 * C, "k_query": 76 * V + 16 * C + 4 * V}
+
+
+def test_committed_traffic_applies_to_its_own_setup_only():
+    path = os.path.join(bench.ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        pytest.skip("no committed DRAM traffic")
+    with open(path) as f:
+        d = json.load(f)
+    if d["kernel_source_hash"] != bench.kernel_source_hash():
+        assert bench.load_traffic("k_insert", False, {}) is None  # stale counters are never used
+        return
+    cap = d["captures"][0]
+    setup = {k: cap[k] for k in ("workload", "cache", "levels", "log2_capacity", "slot_cache")}
+    got = bench.load_traffic("k_insert", False, setup)
+    assert got == cap["kernels"]["k_insert"]["bytes_per_launch"] and got > 0
+    for key, other in (("workload", "1920x1080_d5"), ("cache", "other"), ("levels", 7), ("log2_capacity", 3),
+                       ("slot_cache", not setup["slot_cache"])):
+        assert bench.load_traffic("k_insert", False, dict(setup, **{key: other})) is None, key
+    # the staged insert is a different kernel: only its own capture counts
+    assert bench.load_traffic("k_insert", True, setup) == cap["kernels"].get("k_insert_staged", {}).get("bytes_per_launch")
