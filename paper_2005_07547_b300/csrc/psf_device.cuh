@@ -9,11 +9,10 @@
 //                                   64-byte block per cell
 //   mirror uint2[cap] (8 B)         FP16 copy of L~ read by queries (cache_fp16 = 1)
 //   dirty  u32[cap/32]              one bit per slot: touched this iteration
-// Inserts read keys and add into the first 32-byte sector of a slot (one bulk reduction
-// per group); the blend reads and writes exactly one 64-byte block per touched cell, the
-// DRAM access granularity, so scattered cells cost no partial bursts; queries read keys +
-// the second sector of the slot (FP32) or the compact 8-byte FP16 copy (with the slot
-// cache, no keys: the slot noted by the insert).
+// Inserts touch keys + the first 32-byte sector of a slot (atomics); the blend reads and
+// writes exactly one 64-byte block per touched cell, the DRAM access granularity, so
+// scattered cells cost no partial bursts; queries read keys + the second sector of the
+// slot (FP32) or the compact 8-byte FP16 copy.
 
 #pragma once
 
