@@ -318,7 +318,8 @@ def run_reference(args) -> None:
     from synth.scene import workload
 
     w = workload(args.workload)
-    batches = generate(args.workload, list(range(args.warmup + args.steps)), os.cpu_count() or 1)
+    n_iter = min(args.warmup + args.steps, POOL)  # distinct iterations, cycled like the GPU arm's
+    batches = generate(args.workload, list(range(n_iter)), os.cpu_count() or 1)
     # warm-up steps: untimed oracle iterations (bounded)
     import oracle
 
@@ -329,11 +330,13 @@ def run_reference(args) -> None:
         o.insert(v)
         o.update()
         o.query_cv(v, P, D)
-    # each timed step is a bounded sample: the first 1/8 of the paths of that iteration
-    frac_paths = max(1, P // 8)
+    # each timed step is a bounded sample of that iteration's paths: 1/8 of them for up to 30
+    # steps, proportionally fewer for more steps, so the whole run stays within a minute or so
+    frac_paths = max(1, (P // 8) * min(30, args.steps) // max(args.steps, 1))
     times = []
     done = 0
-    for v in batches[args.warmup:args.warmup + args.steps]:
+    for k in range(args.steps):
+        v = batches[(args.warmup + k) % n_iter]
         sample = v.reshape(D, P, 16)[:, :frac_paths].reshape(-1, 16).copy()
         t0 = time.perf_counter()
         o.insert(sample)
@@ -809,7 +812,7 @@ def run_serving(args) -> None:
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--impl", default="psf", choices=["psf", "reference"])
