@@ -14,7 +14,9 @@
  * Conventions shared by every call
  *   - All pointers named d_* are device pointers on the current CUDA device; h_* are
  *     host pointers.  The caller owns every buffer it passes, including the table
- *     memory given to psf_create; the library owns only a small host-side header.
+ *     memory given to psf_create; the library owns only a small host-side header per
+ *     table (and its mapped status word, from a process-wide pool), each batch's
+ *     descriptor buffers, and the fixed array of psf_batch_step_noalloc.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *     Calls enqueue work on it and return without waiting, except psf_export and
  *     psf_get_stats, which synchronise that stream.  psf_create and psf_destroy make no
