@@ -628,10 +628,21 @@ def run_sessions(args) -> None:
                                alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"])
 
     outs = [torch.empty((d[0].shape[0], 3), device="cuda") for d in dev]
+    # the slot cache (the default): each session's insert notes its vertices' slots and its
+    # query reads them, in the fused kernel and in the plain loop alike
+    slots = [torch.empty(d[0].shape[0], dtype=torch.int32, device="cuda") if args.slot_cache else None for d in dev]
 
     def entries(tables, it):
-        return [(tables[k], dev[k][it % pool], outs[k], s["width"] * s["height"], s["depth"])
-                for k, s in enumerate(sessions)]
+        return [(tables[k], dev[k][it % pool], outs[k], s["width"] * s["height"], s["depth"]) +
+                ((slots[k],) if slots[k] is not None else ()) for k, s in enumerate(sessions)]
+
+    def plain_step(table, i, v, P, D):
+        if slots[i] is not None:
+            table.insert_slots(v, P, D, slots=slots[i])
+            table.update()
+            table.query_cv_slots(v, slots[i], P, D, out=outs[i])
+        else:
+            table.step(v, P, D, out=outs[i])
 
     tuned = autotune.tune_batch(lambda: entries([psf.Table(cfg_of(s)) for s in sessions], 0), len(sessions))
     knobs = tuned["best"]
@@ -668,7 +679,7 @@ def run_sessions(args) -> None:
 
     def plain(k):
         for i, s in enumerate(sessions):
-            plain_tables[i].step(dev[i][k % pool], s["width"] * s["height"], s["depth"], out=outs[i])
+            plain_step(plain_tables[i], i, dev[i][k % pool], s["width"] * s["height"], s["depth"])
 
     t_plain, per_plain = timed(plain, args.warmup, args.steps)
     graph_tables = [psf.Table(cfg_of(s)) for s in sessions]
@@ -677,7 +688,7 @@ def run_sessions(args) -> None:
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             for i, s in enumerate(sessions):
-                graph_tables[i].step(dev[i][it], s["width"] * s["height"], s["depth"], out=outs[i])
+                plain_step(graph_tables[i], i, dev[i][it], s["width"] * s["height"], s["depth"])
         plain_graphs.append(g)
     t_pgraph, per_pgraph = timed(lambda k: plain_graphs[k % pool].replay(), args.warmup, args.steps)
     # the batched tables equal the plain ones bit for bit (same iterations, order-free sums)
@@ -692,6 +703,7 @@ def run_sessions(args) -> None:
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 fixed point", "data": "synthetic",
         "config": {"workload": f"{len(sessions)} sessions, width log-uniform 128..1280, 16:9, depth U{{2..6}}",
                    "vertices_per_step": V, "pool": pool, "fp16_cache": True, "batch_knobs": knobs,
+                   "slot_cache": bool(args.slot_cache),
                    "l2": f"inputs larger than L2: {pool} distinct iterations of {V * 64 / 1e9:.1f} GB"},
         "latency_ms": {"p50": float(np.percentile(per_batch, 50)), "p99": float(np.percentile(per_batch, 99))},
         "plain_loop": {"value": rate(t_plain), "ms_per_step": t_plain / args.steps, "launches_per_step": 3 * len(sessions),

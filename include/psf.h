@@ -270,6 +270,9 @@ typedef struct {
     float* d_out_rgb;        /* D*P*3 float32 */
     uint32_t P;
     uint32_t D;
+    uint32_t* d_slots;       /* optional slot cache (D*P uint32, 4-byte aligned): the item's insert
+                                notes each vertex's slot there and its query reads it, as
+                                psf_insert_slots / psf_query_cv_slots do; NULL = probe */
 } psf_batch_item;
 
 typedef struct {
@@ -328,7 +331,7 @@ int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, const psf_ba
 const char* psf_last_cuda_error(void);
 
 /* ABI version of this header: bump on any incompatible change. */
-#define PSF_ABI_VERSION 5
+#define PSF_ABI_VERSION 6
 int psf_abi_version(void);
 
 #ifdef __cplusplus

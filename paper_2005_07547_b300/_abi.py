@@ -101,6 +101,7 @@ class BatchItem(ctypes.Structure):
         ("d_out_rgb", ctypes.c_void_p),
         ("P", ctypes.c_uint32),
         ("D", ctypes.c_uint32),
+        ("d_slots", ctypes.c_void_p),
     ]
 
 

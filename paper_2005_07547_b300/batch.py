@@ -25,18 +25,27 @@ class Batch:
 
     @staticmethod
     def _items(entries):
-        """entries: iterable of (Table, vertices (P*D, 16) cuda tensor, out (P*D, 3) cuda tensor, P, D)."""
+        """entries: iterable of (Table, vertices (P*D, 16) cuda tensor, out (P*D, 3) cuda tensor, P, D)
+        or the same with a sixth element, a (P*D,) int32 cuda tensor: the item's slot cache."""
+        import torch
+
         entries = list(entries)
         arr = (_abi.BatchItem * max(1, len(entries)))()
         keep = []
-        for i, (table, verts, out, P, D) in enumerate(entries):
+        for i, entry in enumerate(entries):
+            table, verts, out, P, D = entry[:5]
+            slots = entry[5] if len(entry) > 5 else None
             if P * D:
                 _check_vertices(verts, "batch")
                 if verts.shape[0] != P * D or tuple(out.shape) != (P * D, 3) or not out.is_contiguous():
                     raise ValueError("batch: vertices must be (P*D, 16) and outputs (P*D, 3)")
+                if slots is not None and (slots.dtype != torch.int32 or slots.numel() != P * D or
+                                          not slots.is_contiguous()):
+                    raise ValueError("batch: slots must be a contiguous int32 tensor of P*D")
             arr[i] = _abi.BatchItem(table.handle, verts.data_ptr() if P * D else None,
-                                    out.data_ptr() if P * D else None, P, D)
-            keep.append((table, verts, out))
+                                    out.data_ptr() if P * D else None, P, D,
+                                    slots.data_ptr() if (slots is not None and P * D) else None)
+            keep.append((table, verts, out, slots))
         return arr, len(entries), keep
 
     def set(self, entries, stream=None) -> None:

@@ -28,6 +28,7 @@ struct BatchItemDev {
     TableView t;
     const float4* v;
     float* out;
+    unsigned* slots;  // the item's slot cache (D*P), or nullptr
     unsigned P;
     unsigned D;
     unsigned long long nverts;
@@ -140,10 +141,18 @@ __global__ void __launch_bounds__(kThreads)
             v3 = __ldcs(r + 3);
         }
         unsigned len = 0, leaders = 0;
-        if (b.t.levels > 1)  // warp-uniform: a warp's 32 vertices belong to one item
+        if (b.slots) {  // warp-uniform, like the level test: a warp's 32 vertices belong to one item
+            psf::SlotNote note{b.t.levels > 1 ? psf::read_level(b.t, static_cast<unsigned>(i / b.P)) : 0u, psf::kNoSlot};
+            if (b.t.levels > 1)
+                psf::insert_warp<kMode, true, true>(b.t, valid, v0, v1, v2, v3, &len, stage, &leaders, &note);
+            else
+                psf::insert_warp<kMode, false, true>(b.t, valid, v0, v1, v2, v3, &len, stage, &leaders, &note);
+            if (valid) b.slots[i] = note.slot;
+        } else if (b.t.levels > 1) {
             psf::insert_warp<kMode, true>(b.t, valid, v0, v1, v2, v3, &len, stage, &leaders);
-        else
+        } else {
             psf::insert_warp<kMode, false>(b.t, valid, v0, v1, v2, v3, &len, stage, &leaders);
+        }
         if (len > 16u) atomicMax(&b.t.hdr->max_probe, len);  // only long probes are recorded here
     }
     psf::bulk_wait_done();  // this thread's bulk sums have landed before the barrier publishes them
@@ -171,7 +180,12 @@ __global__ void __launch_bounds__(kThreads)
         const unsigned it = find_item(s_begin, n, u);
         const BatchItemDev& b = items[it];
         const unsigned long long p = (u - s_begin[it]) * 32ull + lane;
-        if (p < b.P) psf::query_path(b.t, psf::cv_estimator(b.t), b.v, b.P, b.D, p, b.out);
+        if (p < b.P) {
+            if (b.slots)
+                psf::query_path<true>(b.t, psf::cv_estimator(b.t), b.v, b.P, b.D, p, b.out, b.slots);
+            else
+                psf::query_path(b.t, psf::cv_estimator(b.t), b.v, b.P, b.D, p, b.out);
+        }
     }
 }
 
@@ -245,7 +259,7 @@ int psf_batch_set(psf_batch* b, const psf_batch_item* items, uint32_t n, void* s
         if (!it.table) return PSF_ERR_INVALID_ARG;
         const unsigned long long nv = static_cast<unsigned long long>(it.P) * it.D;
         if (nv && (!it.d_vertices || !it.d_out_rgb || (reinterpret_cast<uintptr_t>(it.d_vertices) & 15u) ||
-                   (reinterpret_cast<uintptr_t>(it.d_out_rgb) & 3u)))
+                   (reinterpret_cast<uintptr_t>(it.d_out_rgb) & 3u) || (reinterpret_cast<uintptr_t>(it.d_slots) & 3u)))
             return PSF_ERR_INVALID_ARG;
     }
     // the staging buffer may still feed the previous copy
@@ -263,6 +277,7 @@ int psf_batch_set(psf_batch* b, const psf_batch_item* items, uint32_t n, void* s
         d.t = it.table->view;
         d.v = reinterpret_cast<const float4*>(it.d_vertices);
         d.out = it.d_out_rgb;
+        d.slots = it.d_slots;
         d.P = it.P;
         d.D = it.D;
         d.nverts = static_cast<unsigned long long>(it.P) * it.D;
@@ -395,7 +410,7 @@ extern "C" int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, c
         if (!it.table) return PSF_ERR_INVALID_ARG;
         const unsigned long long nv = static_cast<unsigned long long>(it.P) * it.D;
         if (nv && (!it.d_vertices || !it.d_out_rgb || (reinterpret_cast<uintptr_t>(it.d_vertices) & 15u) ||
-                   (reinterpret_cast<uintptr_t>(it.d_out_rgb) & 3u)))
+                   (reinterpret_cast<uintptr_t>(it.d_out_rgb) & 3u) || (reinterpret_cast<uintptr_t>(it.d_slots) & 3u)))
             return PSF_ERR_INVALID_ARG;
     }
     int dev = 0;
@@ -420,6 +435,7 @@ extern "C" int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, c
         d.t = it.table->view;
         d.v = reinterpret_cast<const float4*>(it.d_vertices);
         d.out = it.d_out_rgb;
+        d.slots = it.d_slots;
         d.P = it.P;
         d.D = it.D;
         d.nverts = static_cast<unsigned long long>(it.P) * it.D;

@@ -117,7 +117,7 @@ def test_host_detected_argument_errors(lib):
     assert lib.psf_insert_slots(None, None, 1, 1, None, None) == _abi.PSF_ERR_INVALID_ARG
     assert lib.psf_query_cv_slots(None, None, None, 1, 1, None, None) == _abi.PSF_ERR_INVALID_ARG
     assert lib.psf_destroy(None) == _abi.PSF_OK
-    assert lib.psf_abi_version() == 5
+    assert lib.psf_abi_version() == 6
 
 
 def test_product_package_does_not_touch_the_oracle():

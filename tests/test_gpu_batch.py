@@ -50,11 +50,14 @@ def test_batch_matches_alone_and_oracle(psf_mod, oracle_mod, insert_mode):
     oracles = [oracle_mod.Oracle(pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
                                  alpha_min=float(np.float32(s["alpha_min"])), levels=s["levels"]) for s in sessions]
     batch = psf_mod.Batch(len(sessions), insert_mode=insert_mode)
+    # every other session carries a slot cache: the batched kernel notes and reads its slots
+    slots = [torch.empty(s["width"] * s["height"] * s["depth"], dtype=torch.int32, device="cuda") if k % 2 == 0
+             else None for k, s in enumerate(sessions)]
     for it in range(3):
         dev = [torch.from_numpy(data[k][it]).cuda() for k in range(len(sessions))]
         outs_b = [torch.empty((d.shape[0], 3), device="cuda") for d in dev]
-        batch.step([(mixed[k], dev[k], outs_b[k], s["width"] * s["height"], s["depth"])
-                    for k, s in enumerate(sessions)])
+        batch.step([(mixed[k], dev[k], outs_b[k], s["width"] * s["height"], s["depth"]) +
+                    ((slots[k],) if slots[k] is not None else ()) for k, s in enumerate(sessions)])
         for k, s in enumerate(sessions):
             P, D = s["width"] * s["height"], s["depth"]
             out_a = alone[k].step(dev[k], P, D)
