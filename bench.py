@@ -798,7 +798,7 @@ def run_serving(args) -> None:
     reqs = [src.fit(r) for r in reqs]
     reports = {}
     for mode in ("batched", "plain"):
-        srv = Server(src, budget_bytes=args.budget_gb * 1e9, mode=mode)
+        srv = Server(src, budget_bytes=args.budget_gb * 1e9, mode=mode, slot_cache=bool(args.slot_cache))
         with ClockSampler(local) as clocks:
             rep = srv.run(reqs, args.duration)
         rep["clocks"] = clocks.summary()

@@ -45,6 +45,7 @@ class Session:
     D: int
     arrival: float
     admitted: float
+    slots: object = None  # the session's slot cache (int32, P*D), or None
     done: int = 0
     latencies_ms: list = field(default_factory=list)
 
@@ -63,9 +64,11 @@ def table_bytes(req: dict) -> int:
 class Server:
     def __init__(self, vertex_source, budget_bytes: float = 60e9, max_live: int = _abi.MAX_BATCH,
                  mode: str = "batched", use_graph: bool = True, batch_knobs: dict | None = None,
-                 on_retire=None):
+                 on_retire=None, slot_cache: bool = True):
         """vertex_source(request, iteration) -> (P*D, 16) float32 CUDA tensor of that iteration;
-        on_retire(session), if given, sees each session (table still open) before it is freed."""
+        on_retire(session), if given, sees each session (table still open) before it is freed;
+        slot_cache: each session's insert notes its vertices' slots and its query reads them
+        (psf_insert_slots / psf_query_cv_slots, or the batch item's slots), in both modes."""
         if mode not in ("batched", "plain"):
             raise ValueError("mode must be 'batched' or 'plain'")
         self.source = vertex_source
@@ -82,6 +85,7 @@ class Server:
         self.vertices = 0
         self.admission_ms: list[float] = []
         self.on_retire = on_retire
+        self.slot_cache = slot_cache
         self._inflight: deque = deque()  # (start event, end event(s), sessions, retiring sessions)
 
     # -- membership ---------------------------------------------------------------------
@@ -98,7 +102,8 @@ class Server:
             P, D = req["width"] * req["height"], req["depth"]
             t = Table(table_config(req))
             out = torch.empty((P * D, 3), dtype=torch.float32, device="cuda")
-            self.live.append(Session(req, t, out, P, D, req["arrival_s"], now))
+            slots = torch.empty(P * D, dtype=torch.int32, device="cuda") if self.slot_cache else None
+            self.live.append(Session(req, t, out, P, D, req["arrival_s"], now, slots))
             self.used += t.nbytes
             self.admission_ms.append(1e3 * (now - req["arrival_s"]))
             changed = True
@@ -127,11 +132,13 @@ class Server:
                 self.used -= s.table.nbytes
                 s.table.close(synchronize=False)  # its last iteration has completed
                 s.out = None
+                s.slots = None
                 self.finished.append(s)
 
     # -- one iteration of every live session ---------------------------------------------
     def _entries(self):
-        return [(s.table, self.source(s.request, s.done), s.out, s.P, s.D) for s in self.live]
+        return [(s.table, self.source(s.request, s.done), s.out, s.P, s.D) + ((s.slots,) if s.slots is not None else ())
+                for s in self.live]
 
     def _tick(self) -> None:
         import torch
@@ -158,7 +165,13 @@ class Server:
             ends = []
             start.record()
             for s in sessions:
-                s.table.step(self.source(s.request, s.done), s.P, s.D, out=s.out)
+                v = self.source(s.request, s.done)
+                if s.slots is not None:
+                    s.table.insert_slots(v, s.P, s.D, slots=s.slots)
+                    s.table.update()
+                    s.table.query_cv_slots(v, s.slots, s.P, s.D, out=s.out)
+                else:
+                    s.table.step(v, s.P, s.D, out=s.out)
                 e = torch.cuda.Event(enable_timing=True)
                 e.record()
                 ends.append(e)

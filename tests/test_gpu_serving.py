@@ -42,8 +42,9 @@ class _Source:
         return self.data[req["name"]][iteration % 2]
 
 
-@pytest.mark.parametrize("mode,graph", [("batched", True), ("batched", False), ("plain", False)])
-def test_served_sessions_equal_alone(psf_mod, mode, graph):
+@pytest.mark.parametrize("mode,graph,slots", [("batched", True, True), ("batched", False, False), ("plain", False, True),
+                                              ("plain", False, False)])
+def test_served_sessions_equal_alone(psf_mod, mode, graph, slots):
     import torch
 
     from paper_2005_07547_b300.serve import Server, table_bytes
@@ -57,7 +58,7 @@ def test_served_sessions_equal_alone(psf_mod, mode, graph):
     def keep(sess):
         results[sess.request["name"]] = (sess.table.export().tobytes(), sess.out.cpu().numpy().copy(), sess.done)
 
-    srv = Server(src, budget_bytes=budget, mode=mode, use_graph=graph, on_retire=keep)
+    srv = Server(src, budget_bytes=budget, mode=mode, use_graph=graph, on_retire=keep, slot_cache=slots)
     rep = srv.run(reqs, duration_s=30.0, drain=True)
     srv.close()
     assert rep["sessions_finished"] == len(reqs) and rep["requests_waiting_at_end"] == 0
