@@ -14,7 +14,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "psf_oracle.cpp")
 PINS = ["tests/test_oracle_keys.py", "tests/test_oracle_accumulate.py", "tests/test_oracle_cv.py",
-        "tests/test_oracle_levels.py"]
+        "tests/test_oracle_levels.py", "tests/test_oracle_progressive.py"]
+PROG = "value[3 * idx + ch] = field == 0 ? Le + t[ch] * C_next[ch] : t[ch] * (Le_next[ch] + C_next[ch]);"
 
 MUTANTS = {
     "cv_sign_of_control": ("L - c.beta * (t[ch] * C_next[ch]) + c.beta * C[ch]",
@@ -52,6 +53,12 @@ MUTANTS = {
     "level_bits_dropped": ("*key = CellKey(level, nb,", "*key = CellKey(0u, nb,"),
     "insert_level_zero_only": ("l < level_count(c); ++l) {  // every level's cell receives the vertex",
                                "l < 1; ++l) {  // every level's cell receives the vertex"),
+    "progressive_alg1_without_emission": (PROG, PROG.replace("? Le + t[ch] * C_next[ch]", "? t[ch] * C_next[ch]")),
+    "progressive_alg1_own_cell": (PROG, PROG.replace("? Le + t[ch] * C_next[ch]", "? Le + t[ch] * C[ch]")),
+    "progressive_alg1_without_throughput": (PROG, PROG.replace("? Le + t[ch] * C_next[ch]", "? Le + C_next[ch]")),
+    "progressive_alg2_own_emission": (PROG, PROG.replace("(Le_next[ch] + C_next[ch])", "(Le + C_next[ch])")),
+    "progressive_alg2_without_throughput": (PROG, PROG.replace("t[ch] * (Le_next[ch] + C_next[ch])",
+                                                               "(Le_next[ch] + C_next[ch])")),
 }
 
 
