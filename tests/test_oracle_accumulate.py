@@ -197,6 +197,32 @@ def test_untouched_cells_keep_their_state(oracle_mod):
     assert rb0.tobytes() == rb1.tobytes()
 
 
+def test_reset_clears_counters_only(oracle_mod):
+    """The global counter reset (Section "Temporal averaging"): c_old := 0 everywhere, the
+    approximant kept -- a query before the next update reads the same values, an untouched
+    cell keeps its approximant, and a touched one takes alpha = 1 (its new mean)."""
+    o = oracle_mod.Oracle(pos_bits=4, dir_bits=2)
+    a = vertex((0.1, 0.1, 0.1), L=(1.0, 2.0, 4.0))
+    b = vertex((0.9, 0.9, 0.9), L=(3.0, 5.0, 7.0))
+    path = stack([a, b])  # one path of depth 2: a's CV reads b's cell
+    for _ in range(3):
+        o.insert(path)
+        o.update()
+    before = o.export()
+    q0 = o.query_cv(path, 1, 2)
+    o.reset()
+    mid = o.export()
+    assert np.array_equal(mid["L"], before["L"]) and not np.any(mid["c_old"])
+    assert np.array_equal(o.query_cv(path, 1, 2), q0)
+    o.insert(stack([vertex((0.1, 0.1, 0.1), L=(8.0, 8.0, 8.0))]))
+    o.update()
+    after = o.export()
+    kb = oracle_mod.vertex_key(o.cfg, b)
+    assert np.array_equal(after[after["key"] == kb]["L"], before[before["key"] == kb]["L"])
+    ka = oracle_mod.vertex_key(o.cfg, a)
+    assert np.array_equal(after[after["key"] == ka]["L"][0], [8.0, 8.0, 8.0])
+
+
 def test_counter_saturates(oracle_mod):
     o = oracle_mod.Oracle(pos_bits=4, dir_bits=2)
     v = vertex((0.5, 0.5, 0.5))

@@ -53,6 +53,11 @@ MUTANTS = {
     "level_bits_dropped": ("*key = CellKey(level, nb,", "*key = CellKey(0u, nb,"),
     "insert_level_zero_only": ("l < level_count(c); ++l) {  // every level's cell receives the vertex",
                                "l < 1; ++l) {  // every level's cell receives the vertex"),
+    "reset_also_clears_the_approximant": ("for (auto& kv : o->cells) kv.second.c_old = 0;",
+                                          "for (auto& kv : o->cells) { kv.second.c_old = 0; kv.second.L[0] = 0.0; }"),
+    "counter_does_not_saturate": ("if (a > INT64_MAX - b) return INT64_MAX;", "if (a < 0) return INT64_MAX;"),
+    "zero_weight_vertex_inserted": ("const int64_t cw = std::llrint(static_cast<double>(w) * scale);\n        if (cw == 0) {",
+                                    "const int64_t cw = std::llrint(static_cast<double>(w) * scale);\n        if (cw < 0) {"),
     "progressive_alg1_without_emission": (PROG, PROG.replace("? Le + t[ch] * C_next[ch]", "? t[ch] * C_next[ch]")),
     "progressive_alg1_own_cell": (PROG, PROG.replace("? Le + t[ch] * C_next[ch]", "? Le + t[ch] * C[ch]")),
     "progressive_alg1_without_throughput": (PROG, PROG.replace("? Le + t[ch] * C_next[ch]", "? Le + C_next[ch]")),
