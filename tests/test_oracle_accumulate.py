@@ -16,7 +16,7 @@ from helpers import fixed, random_vertices, stack, vertex
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_blend.json")
 
 
-def _brute_force(oracle_mod, cfg, verts):
+def _brute_force(oracle_mod, cfg, verts, frac_bits=24):
     """Group by full key with pairwise compares; returns {key: [sr, sg, sb, c]}."""
     groups = []  # list of (key, sums)
     for v in verts:
@@ -25,10 +25,10 @@ def _brute_force(oracle_mod, cfg, verts):
         prods = [np.float32(w * np.float32(v[12 + c])) for c in range(3)]
         if key is None or not (0.0 <= w <= 32768.0) or any((not np.isfinite(x)) or abs(x) > 32768.0 for x in prods):
             continue
-        cw = int(fixed(w))
+        cw = int(fixed(w, frac_bits))
         if cw == 0:
             continue
-        add = [int(fixed(x)) for x in prods] + [cw]
+        add = [int(fixed(x, frac_bits)) for x in prods] + [cw]
         for gk, gs in groups:
             if gk == key:
                 for i in range(4):
@@ -39,16 +39,16 @@ def _brute_force(oracle_mod, cfg, verts):
     return dict(groups)
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_brute_force_matches_map(oracle_mod, seed):
+@pytest.mark.parametrize("seed,frac_bits", [(0, 24), (1, 24), (2, 24), (3, 8), (4, 16), (5, 32)])
+def test_brute_force_matches_map(oracle_mod, seed, frac_bits):
     rng = np.random.default_rng(seed)
     q, d = 2, 1
     verts = random_vertices(rng, 200, q=q, cells_per_axis=2, zero_weight_fraction=0.05)
-    cfg = oracle_mod.make_config(pos_bits=q, dir_bits=d)
+    cfg = oracle_mod.make_config(pos_bits=q, dir_bits=d, frac_bits=frac_bits)
     o = oracle_mod.Oracle(cfg)
     assert o.insert(verts) == 0
     rec = o.export()
-    bf = _brute_force(oracle_mod, cfg, verts)
+    bf = _brute_force(oracle_mod, cfg, verts, frac_bits)
     assert len(rec) == len(bf) and len(bf) < 120  # many vertices share a cell
     for r in rec:
         assert [int(r["sum"][0]), int(r["sum"][1]), int(r["sum"][2]), int(r["c_new"])] == bf[int(r["key"])]

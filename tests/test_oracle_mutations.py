@@ -15,6 +15,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "psf_oracle.cpp")
 PINS = ["tests/test_oracle_keys.py", "tests/test_oracle_accumulate.py", "tests/test_oracle_cv.py",
         "tests/test_oracle_levels.py", "tests/test_oracle_progressive.py"]
+INSERT_SCALE = ("uint32_t oracle_insert(void* h, const float* verts, uint64_t n) {\n    Oracle* o = static_cast<Oracle*>(h);\n"
+                "    const Config& c = o->cfg;\n    const double scale = std::ldexp(1.0, static_cast<int>(c.frac_bits));")
 PROG = "value[3 * idx + ch] = field == 0 ? Le + t[ch] * C_next[ch] : t[ch] * (Le_next[ch] + C_next[ch]);"
 
 MUTANTS = {
@@ -53,6 +55,7 @@ MUTANTS = {
     "level_bits_dropped": ("*key = CellKey(level, nb,", "*key = CellKey(0u, nb,"),
     "insert_level_zero_only": ("l < level_count(c); ++l) {  // every level's cell receives the vertex",
                                "l < 1; ++l) {  // every level's cell receives the vertex"),
+    "fixed_point_ignores_frac_bits": (INSERT_SCALE, INSERT_SCALE.replace("static_cast<int>(c.frac_bits)", "24")),
     "reset_also_clears_the_approximant": ("for (auto& kv : o->cells) kv.second.c_old = 0;",
                                           "for (auto& kv : o->cells) { kv.second.c_old = 0; kv.second.L[0] = 0.0; }"),
     "counter_does_not_saturate": ("if (a > INT64_MAX - b) return INT64_MAX;", "if (a < 0) return INT64_MAX;"),
