@@ -133,3 +133,16 @@ def test_key_order_matches_tuple_order(oracle_mod):
     assert sorted(range(200), key=lambda i: keys[i]) == sorted(range(200), key=lambda i: (tup[i], keys[i]))
     assert all(k < (1 << 63) for k in keys)
     assert not math.isnan(sum(keys))
+
+
+def test_cell_index_range_edges(oracle_mod):
+    """The index range is [-2^15, 2^15): at q = 0 the cell of x is floor(x) (float32 holds
+    these values exactly), so 32767.5 and -32768.0 have cells and 32768.0 and -32768.5 do not;
+    an accepted index is stored biased by 2^15 in 16 bits."""
+    cfg = oracle_mod.make_config(pos_bits=0, dir_bits=1)
+    inside = {32767.5: 65535, -32768.0: 0, 0.25: 32768, -0.25: 32767}
+    for x, biased in inside.items():
+        k = oracle_mod.vertex_key(cfg, vertex((x, 0.0, 0.0)))
+        assert k is not None and (k >> 32) & 0xFFFF == biased, x
+    for x in (32768.0, -32768.5):
+        assert oracle_mod.vertex_key(cfg, vertex((x, 0.0, 0.0))) is None, x

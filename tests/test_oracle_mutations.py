@@ -56,6 +56,9 @@ MUTANTS = {
     "insert_level_zero_only": ("l < level_count(c); ++l) {  // every level's cell receives the vertex",
                                "l < 1; ++l) {  // every level's cell receives the vertex"),
     "fixed_point_ignores_frac_bits": (INSERT_SCALE, INSERT_SCALE.replace("static_cast<int>(c.frac_bits)", "24")),
+    "cell_index_upper_edge_excluded": ("if (t < -32768.0 || t > 32767.0) return false;",
+                                       "if (t < -32768.0 || t >= 32767.0) return false;"),
+    "progressive_weight_bound_exclusive": ("(w <= 32768.0)", "(w < 32768.0)"),
     "reset_also_clears_the_approximant": ("for (auto& kv : o->cells) kv.second.c_old = 0;",
                                           "for (auto& kv : o->cells) { kv.second.c_old = 0; kv.second.L[0] = 0.0; }"),
     "counter_does_not_saturate": ("if (a > INT64_MAX - b) return INT64_MAX;", "if (a < 0) return INT64_MAX;"),

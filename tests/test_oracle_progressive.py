@@ -102,3 +102,20 @@ def test_progressive_counters_match_plain_insert(oracle_mod):
     assert np.array_equal(ra["key"], rb["key"]) and np.array_equal(ra["c_new"], rb["c_new"])
     # with an empty table the Alg. 1 value of every vertex is its own L_e
     np.testing.assert_allclose(rb["sum"], ra["sum"], rtol=0, atol=1)
+
+
+def test_progressive_weight_range_edges(oracle_mod):
+    """The progressive insert applies the range rule to w and to w * value: w = 2^15 with a
+    value of 1 is accepted, w just above 2^15 is dropped (a one-vertex path: the Alg. 1 value
+    is the vertex's own emission)."""
+    for w, accepted in ((32768.0, True), (32768.0078125, False), (0.0, True)):
+        o = oracle_mod.Oracle(pos_bits=4, dir_bits=2)
+        v = vertex((0.3, 0.3, 0.3), w=w, L=(1.0, 1.0, 1.0))[None, :]
+        status = o.insert_progressive(v, 1, 1, field=0)
+        dropped, zero_w = o.counters()
+        if accepted and w > 0:
+            assert status == 0 and len(o) == 1 and int(o.export()[0]["c_new"]) == int(w * 2 ** 24)
+        elif accepted:
+            assert status == 0 and zero_w == 1 and len(o) == 0
+        else:
+            assert status != 0 and dropped == 1 and len(o) == 0
