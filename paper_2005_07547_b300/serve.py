@@ -101,13 +101,19 @@ class Server:
             queue.popleft()
             P, D = req["width"] * req["height"], req["depth"]
             t = Table(table_config(req))
-            out = torch.empty((P * D, 3), dtype=torch.float32, device="cuda")
-            slots = torch.empty(P * D, dtype=torch.int32, device="cuda") if self.slot_cache else None
+            out = self._empty((P * D, 3), torch.float32)
+            slots = self._empty((P * D,), torch.int32) if self.slot_cache else None
             self.live.append(Session(req, t, out, P, D, req["arrival_s"], now, slots))
             self.used += t.nbytes
             self.admission_ms.append(1e3 * (now - req["arrival_s"]))
             changed = True
         return changed
+
+    def _empty(self, shape, dtype):
+        """A session's device buffer (outputs, slot cache)."""
+        import torch
+
+        return torch.empty(shape, dtype=dtype, device="cuda")
 
     def _retire(self) -> list:
         """Sessions that have had their last iteration enqueued leave the live set (their
