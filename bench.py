@@ -2,12 +2,17 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl psf|reference]
 
-One step is one whole iteration of the hot path (psf_insert, psf_update,
-psf_query_cv) over one batch of synthetic path vertices shaped like a 1280x720,
-1-spp, depth-4 path tracer's output (3,686,400 vertices; each step gets a fresh
-236 MB batch, larger than the 126 MB L2).  Under torchrun every rank runs its own
-render session on its own GPU (weak scaling, no collective on the data path); the
-step time is the maximum over ranks.
+One step is one whole iteration of the hot path (insert, update, control-variate
+query) over one batch of synthetic path vertices shaped like a 1920x1080, 1-spp,
+depth-5 path tracer's output (10,368,000 vertices, 2^24-slot table, camera moving
+1% of the scene per frame; each step gets a fresh 664 MB batch, larger than the
+126 MB L2).  The line is timed with the workload's FP16 query copy of the
+approximant; the same steps with the FP32 copy, each cache's error against the FP64
+oracle, and the 64-session batched form (one fused persistent launch per iteration
+against the plain per-session loop, with its own roofline) are extra keys of the
+same line.  Under torchrun every rank runs its own render session on its own GPU
+(weak scaling, no collective on the data path); the step time is the maximum over
+ranks.
 
 --impl reference times the CPU oracle (test infrastructure: a single-threaded
 std::map implementation) on a bounded sample of the same workload.
@@ -33,7 +38,7 @@ if ROOT not in sys.path:
 
 METRIC = "path vertices filtered/sec (insert+update+query)"
 UNIT = "vertices/s"
-DEFAULT_WORKLOAD = "1280x720_d4"
+DEFAULT_WORKLOAD = "1920x1080_d5"
 POOL = 40  # distinct input batches kept resident; longer runs cycle through them
 KERNEL_SOURCES = ["paper_2005_07547_b300/csrc/psf.cu", "paper_2005_07547_b300/csrc/psf_device.cuh"]
 
@@ -290,27 +295,6 @@ def generate(name: str, iterations: list[int], procs: int) -> list[np.ndarray]:
 # CPU baseline: the oracle on a bounded sample
 # ---------------------------------------------------------------------------
 
-def oracle_rate(w: dict, batches: list[np.ndarray], budget_s: float = 20.0, levels: int = 1) -> dict:
-    import oracle
-
-    P, D = w["width"] * w["height"], w["depth"]
-    o = oracle.Oracle(pos_bits=w["pos_bits"], dir_bits=w["dir_bits"], alpha_min=float(np.float32(w["alpha_min"])),
-                      levels=levels)
-    done = 0
-    t0 = time.perf_counter()
-    for v in batches:
-        o.insert(v)
-        o.update()
-        o.query_cv(v, P, D)
-        done += v.shape[0]
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done // v.shape[0]} iterations ({done} vertices) of {w['name']}, std::map oracle, "
-                      f"insert+update+query, single thread, {dt:.1f} s"}
-
-
 def run_reference(args) -> None:
     rank, world, _ = dist_env()
     if rank != 0:
@@ -363,42 +347,107 @@ def run_reference(args) -> None:
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def run_psf(args) -> None:
-    rank, world, local = dist_env()
-    from synth.scene import workload
+def _oracle_leg(job: dict) -> dict:
+    """The oracle's share of the benchmark, run in a spawned process while the GPU arm runs:
+    iterations 0..k-1 of the workload (regenerated here from their seeds), the last one timed
+    as insert + update + query (the CPU baseline), then the table and the control-variate
+    outputs on every `stride`-th path, which the GPU arm's precision report compares with."""
+    import oracle
+    from synth.scene import iteration_vertices, make_scene, workload
 
-    w = workload(args.workload)
+    w = workload(job["name"])
+    scene = make_scene(w["seed"])
     P, D = w["width"] * w["height"], w["depth"]
-    V = P * D
-    off = rank_seed_offset(rank)
-    n_iter = min(args.warmup + args.steps, POOL)
-    host = generate(args.workload, [off + i for i in range(n_iter)], os.cpu_count() or 1)
-    cpu_sample = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_sample = host[:3]
+    o = oracle.Oracle(pos_bits=w["pos_bits"], dir_bits=w["dir_bits"], alpha_min=float(np.float32(w["alpha_min"])),
+                      levels=job.get("levels", 1))
+    k, stride = job["iterations"], job["stride"]
+    for it in range(k):
+        v = iteration_vertices(w, it, scene)
+        if it < k - 1:
+            o.insert(v)
+            o.update()
+            continue
+        t0 = time.perf_counter()
+        o.insert(v)
+        o.update()
+        out = o.query_cv(v, P, D)
+        dt = time.perf_counter() - t0
+    vs = v.reshape(D, P, 16)[:, ::stride].reshape(-1, 16)
+    Ps = vs.shape[0] // D
+    rec = o.export()
+    return {
+        "cpu_baseline": {"value": v.shape[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"iteration {k - 1} of {w['name']} ({v.shape[0]} vertices, after {k - 1} untimed "
+                                   f"iterations), std::map oracle, insert+update+query, single thread, {dt:.1f} s"},
+        "key": rec["key"], "c_old": rec["c_old"], "L": rec["L"],
+        "out": out.reshape(D, P, 3)[:, ::stride].reshape(-1, 3), "C": o.lookup(vs, Ps, D), "stride": stride,
+        "iterations": k,
+    }
 
+
+def precision_report(psf, make_cfg, dev: list, P: int, D: int, leg: dict, slot_cache: bool) -> dict:
+    """Each query cache's error against the FP64 oracle after the oracle leg's iterations: fresh
+    tables run the same batches with the benchmark's calls; keys and counters must match
+    exactly; the approximant's worst relative error |x - ref| / max(|ref|, 2^-14 max|ref|) and
+    the control-variate outputs' worst error over the norm-wise bound (tolerance 1e-5 for the
+    FP32 copy, 2e-3 for the FP16 copy) on every stride-th path."""
+    import torch
+
+    k, stride = leg["iterations"], leg["stride"]
+    ref = leg["L"]
+    scale = np.maximum(np.abs(ref), 2.0 ** -14 * float(np.max(np.abs(ref))))
+    rep = {"oracle": "FP64 std::map", "iterations": k, "sampled_paths": f"every {stride}th path, all depths"}
+    for fp16 in (False, True):
+        t = psf.Table(make_cfg(fp16))
+        out = torch.empty((P * D, 3), dtype=torch.float32, device="cuda")
+        slots = torch.empty(P * D, dtype=torch.int32, device="cuda")
+        for it in range(k):
+            if slot_cache:
+                t.insert_slots(dev[it], P, D, slots=slots)
+                t.update()
+                t.query_cv_slots(dev[it], slots, P, D, out=out)
+            else:
+                t.step(dev[it], P, D, out=out)
+        g = t.export()
+        exact = bool(np.array_equal(g["key"], leg["key"]) and np.array_equal(g["c_old"], leg["c_old"]))
+        r = {"keys_and_counters_exact": exact}
+        if exact:
+            r["L_fp32_max_rel_err"] = float(np.max(np.abs(g["L"].astype(np.float64) - ref) / scale))
+            if fp16:
+                h = g["L_fp16"].astype(np.uint16).view(np.float16).astype(np.float64)
+                r["L_fp16_max_rel_err"] = float(np.max(np.abs(h - ref) / scale))
+        vs = dev[k - 1].view(D, P, 16)[:, ::stride].reshape(-1, 16).cpu().numpy().astype(np.float64)
+        got = out.view(D, P, 3)[:, ::stride].reshape(-1, 3).cpu().numpy().astype(np.float64)
+        Ps = vs.shape[0] // D
+        C = leg["C"].reshape(D, Ps, 3)
+        Cn = np.zeros_like(C)
+        Cn[:-1] = C[1:]
+        on = (np.repeat(np.arange(D), Ps) + 1 < D)[:, None]
+        fl = 2.0 ** -14 * float(np.max(np.abs(ref)))
+        tj = vs[:, [7, 11, 15]]
+        norm = np.abs(vs[:, 12:15]) + on * (np.abs(tj) * (np.abs(Cn.reshape(-1, 3)) + fl) + np.abs(C.reshape(-1, 3)) + fl)
+        err = np.abs(got - leg["out"])
+        tol = 2e-3 if fp16 else 1e-5
+        r["cv_max_rel_err"] = float(np.max(err / norm))
+        r["cv_err_over_bound"] = float(np.max(err / (tol * norm)))
+        r["tolerance"] = tol
+        rep["fp16" if fp16 else "fp32"] = r
+        t.close()
+    return rep
+
+
+def time_single(psf, table, dev: list, P: int, D: int, steps: int, warmup: int, slot_cache: bool, local: int,
+                world: int) -> dict:
+    """Time `steps` whole iterations (insert, update, query) on one table, a different resident
+    batch each step, with CUDA events on the launching stream around every kernel."""
     import torch
     import torch.distributed as dist
 
-    import paper_2005_07547_b300 as psf
-
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    psf.load()
-    # coarse levels add few cells (measured live cells over the flat table's: 1.26x at 2
-    # levels, 1.35x at 4), so the workload's capacity serves every level count
-    log2cap = w["log2_capacity"]
-    cfg = psf.make_config(log2_capacity=log2cap, pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],
-                          alpha_min=w["alpha_min"], cache_fp16=args.fp16 or w["cache_fp16"],
-                          key_layout=args.key_layout, levels=args.levels)
-    table = psf.Table(cfg)
-    table.set_launch(insert_mode=args.insert_mode, vertex_staging=args.staging, sum_reduction=args.sum_reduction)
-    dev = [torch.from_numpy(v).cuda() for v in host]
+    V = P * D
+    n_iter = len(dev)
     out = torch.empty((V, 3), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-
-    slots = torch.empty(V, dtype=torch.int32, device="cuda") if args.slot_cache else None
+    slots = torch.empty(V, dtype=torch.int32, device="cuda") if slot_cache else None
 
     def insert(v):
         if slots is not None:
@@ -412,22 +461,21 @@ def run_psf(args) -> None:
         else:
             table.query_cv(v, P, D, out=out)
 
-    for k in range(args.warmup):
+    for k in range(warmup):
         insert(dev[k % n_iter])
         table.update()
         query(dev[k % n_iter])
     torch.cuda.synchronize()
     before = table.stats()
-
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
         start.record(stream)
-        for k in range(args.steps):
-            v = dev[(args.warmup + k) % n_iter]
+        for k in range(steps):
+            v = dev[(warmup + k) % n_iter]
             e = ev[k]
             e[0].record(stream)
             insert(v)
@@ -440,16 +488,70 @@ def run_psf(args) -> None:
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-    elapsed_ms = start.elapsed_time(end)
     after = table.stats()
     if after["status"] != 0:
         raise RuntimeError(f"device status {after['status']} during the benchmark")
-
     kt = {"k_insert": [e[0].elapsed_time(e[1]) for e in ev], "k_update": [e[1].elapsed_time(e[2]) for e in ev],
           "k_query": [e[2].elapsed_time(e[3]) for e in ev]}
-    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
-    touched = (after["touched_cells"] - before["touched_cells"]) / args.steps
-    leaders = (after["leader_groups"] - before["leader_groups"]) / args.steps
+    return {"elapsed_ms": start.elapsed_time(end), "kernel_ms": kt, "step_ms": [e[0].elapsed_time(e[3]) for e in ev],
+            "touched": (after["touched_cells"] - before["touched_cells"]) / steps,
+            "leaders": (after["leader_groups"] - before["leader_groups"]) / steps,
+            "live_cells": after["live_cells"], "clocks": clocks.summary()}
+
+
+def run_psf(args) -> None:
+    rank, world, local = dist_env()
+    from synth.scene import workload
+
+    w = workload(args.workload)
+    P, D = w["width"] * w["height"], w["depth"]
+    V = P * D
+    off = rank_seed_offset(rank)
+    n_iter = min(args.warmup + args.steps, POOL)
+    host = generate(args.workload, [off + i for i in range(n_iter)], os.cpu_count() or 1)
+    extras = rank == 0 and world == 1 and not args.no_cpu_baseline
+    sessions_host = None
+    if extras and args.batched_extra:
+        from synth.scene import session_workloads
+
+        sessions_host = generate_sessions(session_workloads(args.sessions), args.pool)
+    leg_proc = None
+    if extras:
+        # the oracle leg runs beside the GPU arm (spawned before any CUDA call)
+        ctx = mp.get_context("spawn")
+        leg_pool = ctx.Pool(1)
+        leg_proc = leg_pool.apply_async(_oracle_leg, ({"name": args.workload, "iterations": min(3, n_iter),
+                                                       "stride": 16, "levels": args.levels},))
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2005_07547_b300 as psf
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    psf.load()
+    # coarse levels add few cells (measured live cells over the flat table's: 1.26x at 2
+    # levels, 1.35x at 4), so the workload's capacity serves every level count
+    log2cap = w["log2_capacity"]
+    fp16 = bool(args.fp16 or w["cache_fp16"])
+
+    def make_cfg(cache_fp16):
+        return psf.make_config(log2_capacity=log2cap, pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],
+                               alpha_min=w["alpha_min"], cache_fp16=cache_fp16, key_layout=args.key_layout,
+                               levels=args.levels)
+
+    def new_table(cache_fp16):
+        t = psf.Table(make_cfg(cache_fp16))
+        t.set_launch(insert_mode=args.insert_mode, vertex_staging=args.staging, sum_reduction=args.sum_reduction)
+        return t
+
+    dev = [torch.from_numpy(v).cuda() for v in host]
+    table = new_table(fp16)
+    m = time_single(psf, table, dev, P, D, args.steps, args.warmup, bool(args.slot_cache), local, world)
+    table.close()
+    elapsed_ms, kt, step_ms, touched, leaders = m["elapsed_ms"], m["kernel_ms"], m["step_ms"], m["touched"], m["leaders"]
 
     if world > 1:
         t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
@@ -460,12 +562,25 @@ def run_psf(args) -> None:
         per_rank = [elapsed_ms]
     agg = aggregate(per_rank, V, args.steps, world)
 
+    other = None
+    if extras:  # the same steps with the other query cache
+        t2 = new_table(not fp16)
+        m2 = time_single(psf, t2, dev, P, D, args.steps, args.warmup, bool(args.slot_cache), local, 1)
+        t2.close()
+        other = {"value": V * args.steps / (m2["elapsed_ms"] / 1e3), "ms_per_step": m2["elapsed_ms"] / args.steps,
+                 "kernels_avg_ms": {k: sum(x) / len(x) for k, x in m2["kernel_ms"].items()},
+                 "p50": float(np.percentile(m2["step_ms"], 50)), "p99": float(np.percentile(m2["step_ms"], 99)),
+                 "clocks": m2["clocks"]}
+
     # end to end through the public API: pinned host vertices in, host CV outputs back,
     # copies inside the timed region, H2D of step k+1 overlapped with compute of step k
-    e2e = run_e2e(psf, table, host, P, D, args.e2e_steps, bool(args.slot_cache)) if rank == 0 else None
+    e2e = None
+    if rank == 0:
+        t3 = new_table(fp16)
+        e2e = run_e2e(psf, t3, host, P, D, args.e2e_steps, bool(args.slot_cache))
+        t3.close()
 
     peaks = load_peaks()
-    fp16 = bool(cfg.cache_fp16)
     alg = algorithmic_bytes(V, touched, fp16, bool(args.slot_cache))
     avg = {k: sum(v) / len(v) for k, v in kt.items()}
     dominant = max(avg, key=avg.get)
@@ -511,7 +626,6 @@ def run_psf(args) -> None:
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
-        table.close()
         return
     line = {
         "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -519,7 +633,8 @@ def run_psf(args) -> None:
         "vs_baseline": None, "dtype": "f32+i64 fixed point", "data": "synthetic",
         "config": {"workload": w["name"], "paths": P, "depth": D, "vertices_per_step": V,
                    "log2_capacity": log2cap, "levels": args.levels, "cache": "fp16" if fp16 else "fp32",
-                   "touched_cells_per_step": touched, "live_cells": after["live_cells"],
+                   "touched_cells_per_step": touched, "live_cells": m["live_cells"],
+                   "camera": f"x = {w['camera_x0']} + {w['camera_step']} * iteration",
                    "l2": f"inputs larger than L2: {n_iter} distinct {V * 64 / 1e6:.0f} MB vertex batches, "
                          "a different one every step",
                    "insert_mode": args.insert_mode, "vertex_staging": args.staging,
@@ -532,13 +647,20 @@ def run_psf(args) -> None:
         "roofline": roofline,
         "kernels": kernels,
         "gpu_launches": 3 * args.steps,
-        "clocks": clocks.summary(),
+        "clocks": m["clocks"],
         "e2e": e2e,
     }
-    if cpu_sample is not None:
-        line["cpu_baseline"] = oracle_rate(w, cpu_sample, levels=args.levels)
+    if other is not None:
+        line["fp32_cache" if fp16 else "fp16_cache"] = other
+    if sessions_host is not None:
+        line["batched_sessions"] = measure_sessions(args, sessions_host, local)
+    if leg_proc is not None:
+        leg = leg_proc.get()
+        leg_pool.close()
+        leg_pool.join()
+        line["cpu_baseline"] = leg["cpu_baseline"]
+        line["precision_vs_fp64_oracle"] = precision_report(psf, make_cfg, dev, P, D, leg, bool(args.slot_cache))
     print(json.dumps(line), flush=True)
-    table.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -599,29 +721,33 @@ def _gen_session(args):
     return iteration_vertices(s, iteration)
 
 
-def run_sessions(args) -> None:
-    """64 uneven render sessions: one fused persistent launch per iteration (graph-replayed)
-    against the plain per-session loop of psf_step calls, eager and graph-captured."""
-    rank, world, local = dist_env()
-    from synth.scene import session_workloads
-
-    sessions = session_workloads(args.sessions, first_session_seed=4000 + 1000 * rank)
-    pool = max(1, min(args.pool, args.warmup + args.steps))
+def generate_sessions(sessions: list[dict], pool: int) -> dict:
+    """Host vertex streams of every session for `pool` iterations (spawned workers, before any
+    CUDA call)."""
     jobs = [(s, it) for it in range(pool) for s in sessions]
     ctx = mp.get_context("spawn")
     with ctx.Pool(min(os.cpu_count() or 1, 32)) as p:
         flat = p.map(_gen_session, jobs, chunksize=1)
-    host = [[flat[it * len(sessions) + k] for it in range(pool)] for k in range(len(sessions))]
+    return {"sessions": sessions, "pool": pool,
+            "host": [[flat[it * len(sessions) + k] for it in range(pool)] for k in range(len(sessions))]}
 
+
+def measure_sessions(args, gen: dict, local: int) -> dict:
+    """Uneven render sessions: one fused persistent launch per iteration (graph-replayed)
+    against the plain per-session loop (three launches per session), eager and
+    graph-captured, on the same resident iterations.  The fused kernel's roofline: its
+    phases run back to back, so its floor is the sum of each phase's own floor over all
+    sessions (insert: the larger of its algorithmic bytes at the measured HBM rate and its
+    (warp, key) groups at the live bulk-reduction probe's rate on the sessions' footprint;
+    blend and query: their algorithmic bytes at the HBM rate), against the measured step."""
     import torch
 
     import paper_2005_07547_b300 as psf
     from paper_2005_07547_b300 import autotune
 
-    torch.cuda.set_device(local)
+    sessions, pool = gen["sessions"], gen["pool"]
     V = sum(s["width"] * s["height"] * s["depth"] for s in sessions)
-    dev = [[torch.from_numpy(v).cuda() for v in host[k]] for k in range(len(sessions))]
-    del host, flat
+    dev = [[torch.from_numpy(v).cuda() for v in gen["host"][k]] for k in range(len(sessions))]
 
     def cfg_of(s):
         return psf.make_config(log2_capacity=s["log2_capacity"], pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
@@ -694,26 +820,87 @@ def run_sessions(args) -> None:
     # the batched tables equal the plain ones bit for bit (same iterations, order-free sums)
     same = all(tables[i].export().tobytes() == plain_tables[i].export().tobytes() for i in range(len(sessions)))
 
+    # per-iteration work of every session, counted by the plain tables (the batched kernel
+    # does not count (warp, key) groups); every table ran warmup + steps identical iterations
+    peaks = load_peaks()
+    bytes_phase = {"k_insert": 0.0, "k_update": 0.0, "k_query": 0.0}
+    groups = touched_all = 0.0
+    slot_bytes = 0
+    for i, s in enumerate(sessions):
+        st = plain_tables[i].stats()
+        its = max(1, st["iterations"])
+        touched = st["touched_cells"] / its
+        groups += st["leader_groups"] / its
+        touched_all += touched
+        slot_bytes += 64 << s["log2_capacity"]
+        for k, b in algorithmic_bytes(s["width"] * s["height"] * s["depth"], touched, bool(s["cache_fp16"]),
+                                      bool(args.slot_cache)).items():
+            bytes_phase[k] += b
+    probe = atomic_probe_rates(modes=(4,), n_words=slot_bytes // 8, n_distinct=max(1, int(touched_all)))
+    group_peak = probe["insert_pattern_bulk32_1or"] / 5.0
+    hbm = peaks["hbm_gbs"] * 1e9
+    floor_s = {"k_insert": max(bytes_phase["k_insert"] / hbm, groups / group_peak),
+               "k_update": bytes_phase["k_update"] / hbm, "k_query": bytes_phase["k_query"] / hbm}
+    step_s = t_batch / args.steps / 1e3
+    total_bytes = sum(bytes_phase.values())
+    roofline = {"kernel": "k_batch", "bound": "hbm+l2_atomic (phase sum)",
+                "frac": sum(floor_s.values()) / step_s,
+                "floor_ms": {k: 1e3 * v for k, v in floor_s.items()},
+                "hbm": {"achieved": total_bytes / step_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": total_bytes / step_s / hbm, "algorithmic_bytes_per_step": total_bytes,
+                        "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"},
+                "l2_atomic": {"groups_per_step": groups, "probe_peak_G_groups_per_s": group_peak / 1e9,
+                              "peak_note": f"of measured (live probe: {int(touched_all)} distinct sectors of "
+                                           f"{slot_bytes / 1e9:.1f} GB)"}}
+
     def rate(ms):
         return V * args.steps / (ms / 1e3)
 
-    line = {
-        "metric": METRIC + ", 64 batched sessions", "value": rate(t_batch), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 fixed point", "data": "synthetic",
-        "config": {"workload": f"{len(sessions)} sessions, width log-uniform 128..1280, 16:9, depth U{{2..6}}",
-                   "vertices_per_step": V, "pool": pool, "fp16_cache": True, "batch_knobs": knobs,
-                   "slot_cache": bool(args.slot_cache),
-                   "l2": f"inputs larger than L2: {pool} distinct iterations of {V * 64 / 1e9:.1f} GB"},
+    res = {
+        "workload": f"{len(sessions)} sessions, width log-uniform 128..1280, 16:9, depth U{{2..6}}, FP16 cache",
+        "value": rate(t_batch), "unit": UNIT, "ms_per_step": t_batch / args.steps, "vertices_per_step": V,
+        "steps": args.steps, "warmup": args.warmup, "pool": pool, "batch_knobs": knobs,
+        "slot_cache": bool(args.slot_cache),
+        "l2": f"inputs larger than L2: {pool} distinct iterations of {V * 64 / 1e9:.1f} GB",
         "latency_ms": {"p50": float(np.percentile(per_batch, 50)), "p99": float(np.percentile(per_batch, 99))},
         "plain_loop": {"value": rate(t_plain), "ms_per_step": t_plain / args.steps, "launches_per_step": 3 * len(sessions),
                        "p50": float(np.percentile(per_plain, 50)), "p99": float(np.percentile(per_plain, 99))},
         "plain_graph": {"value": rate(t_pgraph), "ms_per_step": t_pgraph / args.steps,
                         "p50": float(np.percentile(per_pgraph, 50)), "p99": float(np.percentile(per_pgraph, 99))},
         "speedup_vs_plain_loop": t_plain / t_batch, "speedup_vs_plain_graph": t_pgraph / t_batch,
+        "roofline": roofline,
         "identical_to_plain": same, "status": status, "autotune": tuned["all"],
         "gpu_launches": args.steps, "clocks": clocks.summary(),
     }
+    for group in (tables, plain_tables, graph_tables):
+        for t in group:
+            t.close()
+    for b in batches:
+        b.close()
+    return res
+
+
+def run_sessions(args) -> None:
+    """64 uneven render sessions: the fused batched form against the plain per-session loop."""
+    rank, world, local = dist_env()
+    from synth.scene import session_workloads
+
+    gen = generate_sessions(session_workloads(args.sessions, first_session_seed=4000 + 1000 * rank),
+                            max(1, min(args.pool, args.warmup + args.steps)))
+    import torch
+
+    torch.cuda.set_device(local)
+    r = measure_sessions(args, gen, local)
+    line = {
+        "metric": METRIC + ", 64 batched sessions", "value": r["value"] * world, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 fixed point", "data": "synthetic",
+        "config": {"workload": r["workload"], "vertices_per_step": r["vertices_per_step"], "pool": r["pool"],
+                   "batch_knobs": r["batch_knobs"], "slot_cache": r["slot_cache"], "l2": r["l2"]},
+    }
+    line.update({k: r[k] for k in ("latency_ms", "plain_loop", "plain_graph", "speedup_vs_plain_loop",
+                                   "speedup_vs_plain_graph", "roofline", "identical_to_plain", "status", "autotune",
+                                   "gpu_launches", "clocks")})
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -843,6 +1030,8 @@ def main(argv=None) -> None:
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=60.0, help="serving: device memory for tables")
+    ap.add_argument("--batched-extra", type=int, default=1,
+                    help="single-session runs at N=1 also measure the 64-session batched form (extra key)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps are required")

@@ -1,0 +1,74 @@
+"""Full-size parity over camera-moving frames: the 1920x1080, depth-5 workload
+(10,368,000 vertices per frame, 2^24 slots, the camera translating 1% of the scene per
+frame), its first 16 frames, with the FP32 and the FP16 query copy of the approximant
+side by side against one FP64 oracle (the oracle has no cache precision), in the launch
+configuration the benchmark times (slot-cache insert, blend, slot-cache query).
+
+Every frame both tables are compared in full with the oracle after the blend (keys and
+counters exactly; the FP32 approximant within 1e-5, the FP16 copy within 2e-3 relative),
+after the insert (exact sums) on frames 0, 8 and 15, and their control-variate outputs
+on every 16th path, all depths (tolerance 1e-5 or 2e-3 norm-wise).  The moving camera
+keeps bringing new cells into the table while old ones age, so live and touched cells
+differ from frame to frame.
+"""
+
+import numpy as np
+import pytest
+
+import fullsize
+from parity import TOL_FP16, TOL_FP32, check_after_insert, check_after_update, check_cv
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+NAME, FRAMES, STRIDE = "1920x1080_d5", 16, 16
+
+
+def test_1920x1080_depth5_moving_camera_fp32_and_fp16(psf_mod, oracle_mod):
+    import torch
+
+    from synth.scene import workload
+
+    w = workload(NAME)
+    P, D = w["width"] * w["height"], w["depth"]
+    cfgs = {fp16: psf_mod.make_config(log2_capacity=w["log2_capacity"], pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],
+                                      alpha_min=w["alpha_min"], cache_fp16=fp16) for fp16 in (False, True)}
+    tables = {fp16: psf_mod.Table(c) for fp16, c in cfgs.items()}
+    ora = oracle_mod.Oracle(pos_bits=w["pos_bits"], dir_bits=w["dir_bits"], alpha_min=float(np.float32(w["alpha_min"])))
+    slots = {fp16: torch.empty(P * D, dtype=torch.int32, device="cuda") for fp16 in tables}
+    outs = {fp16: torch.empty((P * D, 3), dtype=torch.float32, device="cuda") for fp16 in tables}
+    live = []
+    for f, v in enumerate(fullsize.named_iterations(NAME, FRAMES)):
+        dv = torch.from_numpy(v).cuda()
+        for fp16, t in tables.items():
+            t.insert_slots(dv, P, D, slots=slots[fp16])
+        st = ora.insert(v)
+        if f in (0, 8, FRAMES - 1):
+            ref = ora.export()
+            for t in tables.values():
+                check_after_insert(t.export(), ref)
+        for t in tables.values():
+            t.update()
+        ora.update()
+        rec = ora.export()
+        vs, Ps = fullsize.sample_paths(v, P, D, STRIDE)
+        ref_out = ora.query_cv(vs, Ps, D)
+        C = ora.lookup(vs, Ps, D)
+        msg = [f"frame {f}: cells {len(rec)}"]
+        for fp16, t in tables.items():
+            rel32, rel16 = check_after_update(t.export(), rec, fp16=fp16)
+            t.query_cv_slots(dv, slots[fp16], P, D, out=outs[fp16])
+            ratio = check_cv(fullsize.sample_out(outs[fp16], P, D, STRIDE), ref_out, vs, C, Ps, D, 1.0, 0xFFFFFFFF,
+                             rec["L"], fp16=fp16)
+            stats = t.stats()
+            assert stats["status"] == st == 0
+            assert (stats["dropped_vertices"], stats["zero_weight_vertices"]) == ora.counters()
+            assert stats["live_cells"] == len(ora)
+            name = "fp16" if fp16 else "fp32"
+            msg.append(f"{name}: L32 err/bound {rel32 / TOL_FP32:.3g}"
+                       + (f", L16 err/bound {rel16 / TOL_FP16:.3g}" if fp16 else "") + f", cv err/bound {ratio:.3g}")
+        live.append(len(rec))
+        print("; ".join(msg))
+        del dv
+    assert live[-1] > live[0]  # the moving camera keeps adding cells
+    for t in tables.values():
+        t.close()

@@ -1,0 +1,73 @@
+"""Full-size parity of the batched form: the 64 uneven sessions of the batched workload
+(width log-uniform 128..1280, 16:9, depth 2..6, 2^(ceil(log2 V) + 1) slots each, FP16
+query copy; about 46 M vertices per iteration), 3 iterations of one fused persistent
+launch each, captured once in a CUDA graph and replayed with the descriptors re-set
+between iterations, with the autotuner's knobs and the slot cache -- the configuration
+the benchmark times.  After every iteration every session's table and the
+control-variate outputs of every 16th path are compared with that session's own oracle
+(spawned workers, one session each)."""
+
+import numpy as np
+import pytest
+
+import fullsize
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+ITERATIONS, STRIDE = 3, 16
+
+
+def test_64_batched_sessions_each_against_its_oracle(psf_mod, oracle_mod):
+    import multiprocessing as mp
+
+    import torch
+
+    from paper_2005_07547_b300 import autotune
+    from synth.scene import session_workloads
+
+    sessions = session_workloads(64)
+    shape = [(s["width"] * s["height"], s["depth"]) for s in sessions]
+
+    def cfg_of(s):
+        return psf_mod.make_config(log2_capacity=s["log2_capacity"], pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
+                                   alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"])
+
+    data = {0: [torch.from_numpy(v).cuda() for v in fullsize.session_iterations(sessions, 0)]}
+    outs = [torch.empty((P * D, 3), dtype=torch.float32, device="cuda") for P, D in shape]
+    slots = [torch.empty(P * D, dtype=torch.int32, device="cuda") for P, D in shape]
+
+    def entries(tables, it):
+        return [(tables[k], data[it][k], outs[k], P, D, slots[k]) for k, (P, D) in enumerate(shape)]
+
+    tuned = autotune.tune_batch(lambda: entries([psf_mod.Table(cfg_of(s)) for s in sessions], 0), len(sessions))
+    tables = [psf_mod.Table(cfg_of(s)) for s in sessions]
+    batch = psf_mod.Batch(len(sessions), **tuned["best"])
+    batch.set(entries(tables, 0))
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.launch()
+    gpu = [[] for _ in sessions]
+    for it in range(ITERATIONS):
+        if it > 0:
+            data[it] = [torch.from_numpy(v).cuda() for v in fullsize.session_iterations(sessions, it)]
+            data.pop(it - 1)
+            batch.set(entries(tables, it))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert batch.status() == 0
+        for k, (P, D) in enumerate(shape):
+            rec = tables[k].export()
+            assert not np.any(rec["sum"]) and not np.any(rec["c_new"])
+            gpu[k].append({"table": rec, "out": fullsize.sample_out(outs[k], P, D, STRIDE)})
+            assert tables[k].stats()["status"] == 0
+    ctx = mp.get_context("spawn")
+    jobs = [{"session": s, "gpu": gpu[k], "stride": STRIDE} for k, s in enumerate(sessions)]
+    with ctx.Pool(fullsize.procs(16)) as pool:
+        res = pool.map(fullsize.oracle_session_check, jobs, chunksize=1)
+    for r in res:
+        print(r)
+    print("autotuned knobs", tuned["best"], "worst err/bound", {k: max(r[k] for r in res) for k in ("L32", "L16", "cv")})
+    batch.close()
+    for t in tables:
+        t.close()

@@ -1,9 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
 
 Small workloads are compared in full every iteration (tables after insert and after
-update, CV outputs); the full-size 1280x720 and 1920x1080 workloads are compared in
-full for their first iterations, in the launch configuration the benchmark times
-(psf_step: insert, update, query on one stream).
+update, CV outputs).  The full-size workloads over their own iteration counts are in
+test_gpu_full_*.py.
 """
 
 import numpy as np
@@ -215,43 +214,6 @@ def test_deterministic_tables_and_outputs(psf_mod):
         table.close()
     assert exports[0] == exports[1]
     assert outs[0] == outs[1]
-
-
-@pytest.mark.slow
-def test_1280x720_depth4_full_size(psf_mod, oracle_mod):
-    w, batches = _workload_batches("1280x720_d4", 3)
-    worst = _run_and_compare(psf_mod, oracle_mod, _cfg_for(psf_mod, w), batches, w["width"] * w["height"],
-                             w["depth"], use_step=True)
-    print("worst relative errors", worst)
-
-
-@pytest.mark.slow
-def test_1920x1080_depth5_full_size_fp32_and_fp16(psf_mod, oracle_mod):
-    """Both caches against one FP64 oracle run (the oracle has no cache precision)."""
-    import torch
-
-    w, batches = _workload_batches("1920x1080_d5", 2)
-    P, D = w["width"] * w["height"], w["depth"]
-    tables = {fp16: psf_mod.Table(_cfg_for(psf_mod, w, cache_fp16=fp16)) for fp16 in (False, True)}
-    ora = _oracle_for(oracle_mod, _cfg_for(psf_mod, w))
-    errs = {}
-    for v in batches:
-        dv = torch.from_numpy(v).cuda()
-        outs = {fp16: t.step(dv, P, D) for fp16, t in tables.items()}
-        ora.insert(v)
-        ora.update()
-        ref_rec = ora.export()
-        ref = ora.query_cv(v, P, D)
-        C = ora.lookup(v)
-        for fp16, t in tables.items():
-            r32, r16 = check_after_update(t.export(), ref_rec, fp16=fp16)
-            rc = check_cv(outs[fp16].cpu().numpy(), ref, v, C, P, D, 1.0, 0xFFFFFFFF, ref_rec["L"], fp16=fp16)
-            errs[fp16] = (r32, r16, rc)
-        del dv, outs
-    for t in tables.values():
-        assert t.stats()["status"] == 0
-        t.close()
-    print("worst error/bound ratios (fp32 L, fp16 L, cv):", errs)
 
 
 @pytest.mark.parametrize("knobs", [dict(insert_mode=1), dict(insert_blocks_per_sm=1, update_blocks_per_sm=1,
