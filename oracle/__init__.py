@@ -23,6 +23,9 @@ STATUS_RANGE = 2
 
 RECORD_DTYPE = np.dtype([("key", "<u8"), ("sum", "<i8", (3,)), ("c_new", "<i8"), ("c_old", "<i8"),
                          ("L", "<f8", (3,))])
+# the YCoCg two-band SH payload: sums Y, Co, Cg, c_new, n(3), Y n(3), n n(xx, xy, xz, yy, yz, zz);
+# coefficients a, g_x, g_y, g_z, Co, Cg (luminance a + g . n)
+SH_RECORD_DTYPE = np.dtype([("key", "<u8"), ("sum", "<i8", (16,)), ("c_old", "<i8"), ("coef", "<f8", (6,))])
 
 
 class _Config(ctypes.Structure):
@@ -77,6 +80,21 @@ def lib() -> ctypes.CDLL:
         L.oracle_export.restype = u64
         L.oracle_export.argtypes = [vp, vp, u64]
         L.oracle_import.argtypes = [vp, vp, u64]
+        L.oracle_sh_create.restype = vp
+        L.oracle_sh_create.argtypes = [ctypes.POINTER(_Config), ctypes.c_double]
+        L.oracle_sh_destroy.argtypes = [vp]
+        L.oracle_sh_insert.restype = u32
+        L.oracle_sh_insert.argtypes = [vp, vp, u64]
+        L.oracle_sh_update.restype = u32
+        L.oracle_sh_update.argtypes = [vp]
+        L.oracle_sh_reset.argtypes = [vp]
+        L.oracle_sh_lookup.argtypes = [vp, vp, u64, vp]
+        L.oracle_sh_query_cv.argtypes = [vp, vp, u32, u32, vp]
+        L.oracle_sh_size.restype = u64
+        L.oracle_sh_size.argtypes = [vp]
+        L.oracle_sh_counters.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.oracle_sh_export.restype = u64
+        L.oracle_sh_export.argtypes = [vp, vp, u64]
         _lib = L
     return _lib
 
@@ -184,3 +202,60 @@ class Oracle:
     def import_records(self, recs: np.ndarray) -> None:
         r = np.ascontiguousarray(recs, dtype=RECORD_DTYPE)
         lib().oracle_import(self._h, r.ctypes.data, r.shape[0])
+
+
+class ShOracle:
+    """std::map-backed reference table with the YCoCg two-band SH payload: per cell, luminance
+    fitted over the normal (a + g . n, ridge on g) and constant chroma (see psf_oracle.cpp)."""
+
+    def __init__(self, cfg: _Config | None = None, ridge: float = 0.01, **kw):
+        self.cfg = cfg if cfg is not None else make_config(**kw)
+        self.ridge = float(ridge)
+        self._h = lib().oracle_sh_create(ctypes.byref(self.cfg), self.ridge)
+        if not self._h:
+            raise ValueError("invalid oracle configuration")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().oracle_sh_destroy(h)
+            self._h = None
+
+    def insert(self, verts: np.ndarray) -> int:
+        v = _verts(verts)
+        return int(lib().oracle_sh_insert(self._h, v.ctypes.data, v.shape[0]))
+
+    def update(self) -> int:
+        return int(lib().oracle_sh_update(self._h))
+
+    def reset(self) -> None:
+        lib().oracle_sh_reset(self._h)
+
+    def lookup(self, verts: np.ndarray) -> np.ndarray:
+        """(n, 3) RGB of each vertex's cell fit at the vertex's normal, 0 where absent."""
+        v = _verts(verts)
+        out = np.empty((v.shape[0], 3), dtype=np.float64)
+        lib().oracle_sh_lookup(self._h, v.ctypes.data, v.shape[0], out.ctypes.data)
+        return out
+
+    def query_cv(self, verts: np.ndarray, P: int, D: int) -> np.ndarray:
+        v = _verts(verts)
+        if v.shape[0] != P * D:
+            raise ValueError("vertex count must be P*D")
+        out = np.empty((P * D, 3), dtype=np.float64)
+        lib().oracle_sh_query_cv(self._h, v.ctypes.data, P, D, out.ctypes.data)
+        return out
+
+    def __len__(self) -> int:
+        return int(lib().oracle_sh_size(self._h))
+
+    def counters(self) -> tuple[int, int]:
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        lib().oracle_sh_counters(self._h, ctypes.byref(a), ctypes.byref(b))
+        return int(a.value), int(b.value)
+
+    def export(self) -> np.ndarray:
+        n = len(self)
+        out = np.zeros(n, dtype=SH_RECORD_DTYPE)
+        got = lib().oracle_sh_export(self._h, out.ctypes.data, n)
+        return out[:got]

@@ -520,6 +520,254 @@ void oracle_import(void* h, const oracle_record* recs, uint64_t n) {
     }
 }
 
+
+// ------------------------------------------------------------------------------------
+// YCoCg two-band spherical-harmonics payload (Section "Basis functions and data
+// structures: spatio-directional hashing", last paragraph: luminance in two SH bands over
+// the normal, chroma kept per cell, so that each cell's basis spans normal variation).
+//
+// Reading (the paper names the representation, not its estimator):
+//   * colour: Y = R/4 + G/2 + B/4, Co = R/2 - B/2, Cg = G/2 - R/4 - B/4 (Malvar and
+//     Sullivan's YCoCg), inverse R = Y + Co - Cg, G = Y + Cg, B = Y - Co - Cg;
+//   * per cell and iteration, luminance over the normal n is fitted by weighted least
+//     squares on the two SH bands, whose span is {1, n_x, n_y, n_z}: Y(n) ~ a + g . n
+//     (a = c00 Y00, g = sqrt(3 / 4 pi) (c11, c1-1, c10)), minimising
+//        sum_i w_i (Y_i - a - g . n_i)^2 + ridge * W * |g|^2,   W = sum_i w_i,
+//     whose band-0 part alone is eq. (6)'s weighted mean; chroma is the weighted mean;
+//   * in centred form: M = W sum w n n^T - (sum w n)(sum w n)^T and
+//     r = W sum w Y n - (sum w Y)(sum w n) are formed exactly from the integer sums
+//     (128-bit), then (M + ridge W^2 I) g = r and a = (sum w Y - g . sum w n) / W;
+//     if the regularised matrix is not positive definite band 1 is 0 for that iteration;
+//   * eq. (10)-(11) blend the six coefficients (a, g_x, g_y, g_z, Co, Cg) with the
+//     cell's alpha; the approximant at a vertex is the cell's fit evaluated at the vertex's
+//     own normal, turned back into RGB.
+// Fixed-point codes, in FP32 with one rounding per step in this order (the kernel takes
+// the same decisions): p_c = w L_c; wY = (p_r/4 + p_g/2) + p_b/4; wCo = p_r/2 - p_b/2;
+// wCg = (p_g/2 - p_r/4) - p_b/4; m_k = w n_k; Yn_k = wY n_k; nn_jk = m_j n_k; each
+// rounded to nearest even at 2^F.  Range rule: that of the RGB payload plus |n_k| <= 2.
+// ------------------------------------------------------------------------------------
+
+namespace {
+
+constexpr int SH_SUMS = 16;  // Y, Co, Cg, c_new, n(3), Y n(3), n n(xx, xy, xz, yy, yz, zz)
+
+struct ShCell {
+    int64_t s[SH_SUMS] = {};
+    int64_t c_old = 0;
+    double coef[6] = {0, 0, 0, 0, 0, 0};  // a, g_x, g_y, g_z, Co, Cg
+};
+
+struct ShOracle {
+    Config cfg;
+    double ridge;
+    std::map<CellKey, ShCell> cells;
+    uint64_t dropped = 0;
+    uint64_t zero_weight = 0;
+};
+
+// The cell fit's RGB at normal n.
+void sh_rgb(const double coef[6], const float* n, double out[3]) {
+    const double Y = coef[0] + coef[1] * n[0] + coef[2] * n[1] + coef[3] * n[2];
+    out[0] = Y + coef[4] - coef[5];
+    out[1] = Y + coef[5];
+    out[2] = Y - coef[4] - coef[5];
+}
+
+// 3x3 determinant by cofactors.
+double det3(const double m[3][3]) {
+    return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+           m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+}
+
+// This iteration's fit of one touched cell (the reading above), in FP64.
+void sh_fit(const ShCell& c, double ridge, double out[6]) {
+    using i128 = __int128;
+    const int64_t W = c.s[3];
+    const int64_t* sn = c.s + 4;
+    const int64_t* sYn = c.s + 7;
+    const int64_t* snn = c.s + 10;
+    const int idx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    double m[3][3], r[3];
+    const double Wd = static_cast<double>(W);
+    for (int j = 0; j < 3; ++j) {
+        for (int k = 0; k < 3; ++k) {
+            const i128 mjk = static_cast<i128>(W) * snn[idx[j][k]] - static_cast<i128>(sn[j]) * sn[k];
+            m[j][k] = static_cast<double>(mjk);
+        }
+        m[j][j] += ridge * Wd * Wd;
+        r[j] = static_cast<double>(static_cast<i128>(W) * sYn[j] - static_cast<i128>(c.s[0]) * sn[j]);
+    }
+    // positive definite: the leading principal minors are positive (Sylvester's criterion)
+    const double d1 = m[0][0], d2 = m[0][0] * m[1][1] - m[0][1] * m[1][0], d3 = det3(m);
+    double g[3] = {0.0, 0.0, 0.0};
+    if (d1 > 0.0 && d2 > 0.0 && d3 > 0.0) {
+        for (int col = 0; col < 3; ++col) {  // Cramer's rule
+            double mc[3][3];
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) mc[j][k] = (k == col) ? r[j] : m[j][k];
+            g[col] = det3(mc) / d3;
+        }
+    }
+    out[0] = (static_cast<double>(c.s[0]) - (g[0] * sn[0] + g[1] * sn[1] + g[2] * sn[2])) / Wd;
+    out[1] = g[0];
+    out[2] = g[1];
+    out[3] = g[2];
+    out[4] = static_cast<double>(c.s[1]) / Wd;
+    out[5] = static_cast<double>(c.s[2]) / Wd;
+}
+
+}  // namespace
+
+typedef struct {
+    uint64_t key;
+    int64_t sum[16];  // Y, Co, Cg, c_new, n(3), Y n(3), n n(6) -- this iteration's fixed-point sums
+    int64_t c_old;
+    double coef[6];   // a, g_x, g_y, g_z, Co, Cg
+} oracle_sh_record;
+
+void* oracle_sh_create(const oracle_config* cfg, double ridge) {
+    if (!cfg || cfg->dir_bits_d > 5 || cfg->pos_bits_q > 20 || cfg->frac_bits < 8 || cfg->frac_bits > 32 ||
+        cfg->levels > 1 || !(ridge >= 0.0))
+        return nullptr;
+    ShOracle* o = new ShOracle();
+    std::memcpy(&o->cfg, cfg, sizeof(Config));
+    o->ridge = ridge;
+    return o;
+}
+
+void oracle_sh_destroy(void* h) { delete static_cast<ShOracle*>(h); }
+
+uint32_t oracle_sh_insert(void* h, const float* verts, uint64_t n) {
+    ShOracle* o = static_cast<ShOracle*>(h);
+    const Config& c = o->cfg;
+    const double scale = std::ldexp(1.0, static_cast<int>(c.frac_bits));
+    auto fx = [scale](float x) { return std::llrint(static_cast<double>(x) * scale); };
+    uint32_t status = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        const float* v = verts + 16 * i;
+        const float* nr = v + 4;
+        CellKey key;
+        bool ok = vertex_cell(c, v, &key);
+        const float w = v[3];
+        ok = ok && (w >= 0.0f) && (w <= 32768.0f);
+        for (int k = 0; k < 3 && ok; ++k) ok = std::fabs(nr[k]) <= 2.0f;
+        float p[3] = {0.0f, 0.0f, 0.0f};
+        for (int ch = 0; ch < 3 && ok; ++ch) {
+            p[ch] = w * v[12 + ch];
+            ok = std::isfinite(p[ch]) && std::fabs(p[ch]) <= 32768.0f;
+        }
+        if (!ok) {
+            status |= ST_RANGE;
+            o->dropped++;
+            continue;
+        }
+        const int64_t cw = std::llrint(static_cast<double>(w) * scale);
+        if (cw == 0) {
+            o->zero_weight++;
+            continue;
+        }
+        float wY = 0.25f * p[0] + 0.5f * p[1];
+        wY = wY + 0.25f * p[2];
+        const float wCo = 0.5f * p[0] - 0.5f * p[2];
+        float wCg = 0.5f * p[1] - 0.25f * p[0];
+        wCg = wCg - 0.25f * p[2];
+        const float m[3] = {w * nr[0], w * nr[1], w * nr[2]};
+        ShCell& cell = o->cells[key];
+        cell.s[0] += fx(wY);
+        cell.s[1] += fx(wCo);
+        cell.s[2] += fx(wCg);
+        cell.s[3] += cw;
+        for (int k = 0; k < 3; ++k) {
+            cell.s[4 + k] += fx(m[k]);
+            cell.s[7 + k] += fx(wY * nr[k]);
+        }
+        cell.s[10] += fx(m[0] * nr[0]);
+        cell.s[11] += fx(m[0] * nr[1]);
+        cell.s[12] += fx(m[0] * nr[2]);
+        cell.s[13] += fx(m[1] * nr[1]);
+        cell.s[14] += fx(m[1] * nr[2]);
+        cell.s[15] += fx(m[2] * nr[2]);
+    }
+    return status;
+}
+
+// eq. (10)-(11) on the six coefficients of every touched cell.
+uint32_t oracle_sh_update(void* h) {
+    ShOracle* o = static_cast<ShOracle*>(h);
+    const Config& c = o->cfg;
+    for (auto& kv : o->cells) {
+        ShCell& cell = kv.second;
+        if (cell.s[3] == 0) continue;
+        const double cn = static_cast<double>(cell.s[3]);
+        const double co = static_cast<double>(cell.c_old);
+        const double alpha = c.blend_mode == 0 ? std::max(std::sqrt(cn / (co + cn)), c.alpha_min) : c.alpha_min;
+        double fit[6];
+        sh_fit(cell, o->ridge, fit);
+        for (int k = 0; k < 6; ++k) cell.coef[k] = (1.0 - alpha) * cell.coef[k] + alpha * fit[k];
+        cell.c_old = sat_add(cell.c_old, cell.s[3]);
+        for (int k = 0; k < SH_SUMS; ++k) cell.s[k] = 0;
+    }
+    return 0;
+}
+
+void oracle_sh_reset(void* h) {
+    for (auto& kv : static_cast<ShOracle*>(h)->cells) kv.second.c_old = 0;
+}
+
+// RGB approximant of each vertex's cell at the vertex's own normal (0 when absent).
+void oracle_sh_lookup(void* h, const float* verts, uint64_t n, double* C_out) {
+    ShOracle* o = static_cast<ShOracle*>(h);
+    for (uint64_t i = 0; i < n; ++i) {
+        double* C = C_out + 3 * i;
+        C[0] = C[1] = C[2] = 0.0;
+        CellKey key;
+        if (!vertex_cell(o->cfg, verts + 16 * i, &key)) continue;
+        auto it = o->cells.find(key);
+        if (it != o->cells.end()) sh_rgb(it->second.coef, verts + 16 * i + 4, C);
+    }
+}
+
+// The control variate of oracle_query_cv with C_j the SH payload's RGB at vertex j's normal.
+void oracle_sh_query_cv(void* h, const float* verts, uint32_t P, uint32_t D, double* out) {
+    ShOracle* o = static_cast<ShOracle*>(h);
+    const Config& c = o->cfg;
+    std::vector<double> C(3 * static_cast<size_t>(P) * D);
+    oracle_sh_lookup(h, verts, static_cast<uint64_t>(P) * D, C.data());
+    for (uint64_t p = 0; p < P; ++p)
+        for (uint64_t j = 0; j < D; ++j) {
+            const uint64_t idx = j * P + p;
+            const float* v = verts + 16 * idx;
+            const double t[3] = {v[7], v[11], v[15]};
+            const bool cv = j + 1 < D && j < c.cv_max_depth;
+            for (int ch = 0; ch < 3; ++ch) {
+                const double L = v[12 + ch];
+                out[3 * idx + ch] = cv ? (L - c.beta * (t[ch] * C[3 * (idx + P) + ch]) + c.beta * C[3 * idx + ch]) : L;
+            }
+        }
+}
+
+uint64_t oracle_sh_size(void* h) { return static_cast<ShOracle*>(h)->cells.size(); }
+
+void oracle_sh_counters(void* h, uint64_t* dropped, uint64_t* zero_weight) {
+    ShOracle* o = static_cast<ShOracle*>(h);
+    *dropped = o->dropped;
+    *zero_weight = o->zero_weight;
+}
+
+uint64_t oracle_sh_export(void* h, oracle_sh_record* out, uint64_t cap) {
+    ShOracle* o = static_cast<ShOracle*>(h);
+    uint64_t i = 0;
+    for (const auto& kv : o->cells) {
+        if (i >= cap) break;
+        oracle_sh_record& r = out[i++];
+        r.key = pack_key(o->cfg, kv.first);
+        for (int k = 0; k < SH_SUMS; ++k) r.sum[k] = kv.second.s[k];
+        r.c_old = kv.second.c_old;
+        for (int k = 0; k < 6; ++k) r.coef[k] = kv.second.coef[k];
+    }
+    return i;
+}
+
 uint32_t oracle_status_range() { return ST_RANGE; }
 uint32_t oracle_status_table_full() { return ST_TABLE_FULL; }
 

@@ -14,7 +14,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "psf_oracle.cpp")
 PINS = ["tests/test_oracle_keys.py", "tests/test_oracle_accumulate.py", "tests/test_oracle_cv.py",
-        "tests/test_oracle_levels.py", "tests/test_oracle_progressive.py"]
+        "tests/test_oracle_levels.py", "tests/test_oracle_progressive.py", "tests/test_oracle_sh.py"]
 INSERT_SCALE = ("uint32_t oracle_insert(void* h, const float* verts, uint64_t n) {\n    Oracle* o = static_cast<Oracle*>(h);\n"
                 "    const Config& c = o->cfg;\n    const double scale = std::ldexp(1.0, static_cast<int>(c.frac_bits));")
 PROG = "value[3 * idx + ch] = field == 0 ? Le + t[ch] * C_next[ch] : t[ch] * (Le_next[ch] + C_next[ch]);"
@@ -68,6 +68,32 @@ MUTANTS = {
     "progressive_alg1_own_cell": (PROG, PROG.replace("? Le + t[ch] * C_next[ch]", "? Le + t[ch] * C[ch]")),
     "progressive_alg1_without_throughput": (PROG, PROG.replace("? Le + t[ch] * C_next[ch]", "? Le + C_next[ch]")),
     "progressive_alg2_own_emission": (PROG, PROG.replace("(Le_next[ch] + C_next[ch])", "(Le + C_next[ch])")),
+    "sh_centering_sign": ('static_cast<i128>(W) * snn[idx[j][k]] - static_cast<i128>(sn[j]) * sn[k]',
+                         'static_cast<i128>(W) * snn[idx[j][k]] + static_cast<i128>(sn[j]) * sn[k]'),
+    "sh_cross_term_uses_chroma": ('static_cast<i128>(W) * sYn[j] - static_cast<i128>(c.s[0]) * sn[j]',
+                                 'static_cast<i128>(W) * sYn[j] - static_cast<i128>(c.s[1]) * sn[j]'),
+    "sh_ridge_not_scaled_by_weight": ('m[j][j] += ridge * Wd * Wd;',
+                                     'm[j][j] += ridge * Wd;'),
+    "sh_intercept_without_gradient": ('(static_cast<double>(c.s[0]) - (g[0] * sn[0] + g[1] * sn[1] + g[2] * sn[2])) / Wd',
+                                     'static_cast<double>(c.s[0]) / Wd'),
+    "sh_chroma_swapped": ('out[4] = static_cast<double>(c.s[1]) / Wd;\n    out[5] = static_cast<double>(c.s[2]) / Wd;',
+                         'out[4] = static_cast<double>(c.s[2]) / Wd;\n    out[5] = static_cast<double>(c.s[1]) / Wd;'),
+    "sh_inverse_blue_sign": ('out[2] = Y - coef[4] - coef[5];',
+                            'out[2] = Y - coef[4] + coef[5];'),
+    "sh_luminance_weights": ('float wY = 0.25f * p[0] + 0.5f * p[1];',
+                            'float wY = 0.5f * p[0] + 0.25f * p[1];'),
+    "sh_moment_index_transposed": ('{{0, 1, 2}, {1, 3, 4}, {2, 4, 5}}',
+                                  '{{0, 1, 2}, {1, 3, 5}, {2, 5, 4}}'),
+    "sh_lookup_at_direction": ('sh_rgb(it->second.coef, verts + 16 * i + 4, C);',
+                              'sh_rgb(it->second.coef, verts + 16 * i + 8, C);'),
+    "sh_band1_not_blended": ('for (int k = 0; k < 6; ++k) cell.coef[k] = (1.0 - alpha) * cell.coef[k] + alpha * fit[k];',
+                            'for (int k = 0; k < 6; ++k) cell.coef[k] = (k >= 1 && k <= 3) ? fit[k] : (1.0 - alpha) * cell.coef[k] + alpha * fit[k];'),
+    "sh_luminance_moment_uses_weight": ('cell.s[7 + k] += fx(wY * nr[k]);',
+                                       'cell.s[7 + k] += fx(m[k]);'),
+    "sh_normal_bound_exclusive": ('ok = std::fabs(nr[k]) <= 2.0f;',
+                                 'ok = std::fabs(nr[k]) < 2.0f;'),
+    "sh_cv_sign_of_control": ('(L - c.beta * (t[ch] * C[3 * (idx + P) + ch]) + c.beta * C[3 * idx + ch])',
+                             '(L + c.beta * (t[ch] * C[3 * (idx + P) + ch]) + c.beta * C[3 * idx + ch])'),
     "progressive_alg2_without_throughput": (PROG, PROG.replace("t[ch] * (Le_next[ch] + C_next[ch])",
                                                                "(Le_next[ch] + C_next[ch])")),
 }
