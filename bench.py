@@ -74,7 +74,7 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def algorithmic_bytes(V: int, touched: float, cache_fp16: bool, slot_cache: bool = False) -> dict:
+def algorithmic_bytes(V: int, touched: float, cache_fp16: bool, slot_cache: bool = False, payload: int = 0) -> dict:
     """Bytes each kernel must move at minimum (per launch).
 
     insert: read the 64-B vertex record of every vertex; per touched cell read its
@@ -84,7 +84,14 @@ def algorithmic_bytes(V: int, touched: float, cache_fp16: bool, slot_cache: bool
     query:  read the 64-B record and write the 12-B output of every vertex; per
             touched cell read its key and its approximant (8 + 16, or 8 + 8 for FP16).
     With the slot cache the insert also writes, and the query reads, a 4-B slot per vertex.
+    The SH payload (payload 1) has sixteen 64-bit sums and six coefficients per cell: the
+    insert read-modify-writes 128 B per touched cell (8 + 256), the update reads and zeroes
+    them and reads and writes c_old and the 24-B coefficients (320), the query reads the key
+    and the coefficients (8 + 24).
     """
+    if payload == 1:
+        return {"k_insert": 64.0 * V + 264.0 * touched, "k_update": 320.0 * touched,
+                "k_query": 76.0 * V + 32.0 * touched}
     extra = 4.0 * V if slot_cache else 0.0
     return {
         "k_insert": 64.0 * V + 72.0 * touched + extra,
@@ -509,7 +516,7 @@ def run_psf(args) -> None:
     off = rank_seed_offset(rank)
     n_iter = min(args.warmup + args.steps, POOL)
     host = generate(args.workload, [off + i for i in range(n_iter)], os.cpu_count() or 1)
-    extras = rank == 0 and world == 1 and not args.no_cpu_baseline
+    extras = rank == 0 and world == 1 and not args.no_cpu_baseline and args.payload == "rgb"
     sessions_host = None
     if extras and args.batched_extra:
         from synth.scene import session_workloads
@@ -537,10 +544,16 @@ def run_psf(args) -> None:
     log2cap = w["log2_capacity"]
     fp16 = bool(args.fp16 or w["cache_fp16"])
 
+    sh = args.payload == "sh"
+    if sh:  # the SH payload keeps no FP16 copy and no slot cache; the paper's 5-d key
+        fp16 = False
+        args.slot_cache = 0
+
     def make_cfg(cache_fp16):
         return psf.make_config(log2_capacity=log2cap, pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],
                                alpha_min=w["alpha_min"], cache_fp16=cache_fp16, key_layout=args.key_layout,
-                               levels=args.levels)
+                               levels=args.levels, payload=1 if sh else 0, sh_ridge=args.sh_ridge,
+                               use_normal=not sh)
 
     def new_table(cache_fp16):
         t = psf.Table(make_cfg(cache_fp16))
@@ -563,7 +576,7 @@ def run_psf(args) -> None:
     agg = aggregate(per_rank, V, args.steps, world)
 
     other = None
-    if extras:  # the same steps with the other query cache
+    if extras and not sh:  # the same steps with the other query cache
         t2 = new_table(not fp16)
         m2 = time_single(psf, t2, dev, P, D, args.steps, args.warmup, bool(args.slot_cache), local, 1)
         t2.close()
@@ -581,7 +594,7 @@ def run_psf(args) -> None:
         t3.close()
 
     peaks = load_peaks()
-    alg = algorithmic_bytes(V, touched, fp16, bool(args.slot_cache))
+    alg = algorithmic_bytes(V, touched, fp16, bool(args.slot_cache), 1 if sh else 0)
     avg = {k: sum(v) / len(v) for k, v in kt.items()}
     dominant = max(avg, key=avg.get)
     achieved = alg[dominant] / (avg[dominant] / 1e3) / 1e9
@@ -593,7 +606,8 @@ def run_psf(args) -> None:
     probe_words = 8 << log2cap
     mode = 4 if args.sum_reduction == 0 else 2
     pname = {4: "insert_pattern_bulk32_1or", 2: "insert_pattern_4red_1or"}[mode]
-    probe = atomic_probe_rates(modes=(mode,), n_words=probe_words, n_distinct=max(1, int(touched))) if rank == 0 else {}
+    probe = (atomic_probe_rates(modes=(mode,), n_words=probe_words, n_distinct=max(1, int(touched)))
+             if rank == 0 and not sh else {})
     peak_groups = probe[pname] / 5.0 if probe else float("nan")
     group_rate = leaders / (avg["k_insert"] / 1e3)
     atomic_roofline = {"kernel": "k_insert", "achieved": group_rate / 1e9, "unit": "G groups/s",
@@ -610,6 +624,8 @@ def run_psf(args) -> None:
     staged = {"k_insert": bool(args.staging & 1), "k_query": bool(args.staging & 2)}.get(dominant, False)
     setup = {"workload": w["name"], "cache": "fp16" if fp16 else "fp32", "levels": args.levels, "log2_capacity": log2cap,
              "slot_cache": bool(args.slot_cache)}
+    if sh:
+        setup["payload"] = "sh"
     roofline = {"kernel": dominant, "traffic": load_traffic(dominant, staged, setup), "hbm": hbm}
     binding = hbm
     roofline["bound"] = "hbm"
@@ -641,6 +657,7 @@ def run_psf(args) -> None:
                    "sum_reduction": {0: "bulk (TMA) 32-B reduction", 1: "4 x red.add.u64"}[args.sum_reduction],
                    "slot_cache": bool(args.slot_cache),
                    "key_layout": {0: "auto", 1: "dense key array", 2: "keys in slot records"}[args.key_layout],
+                   "payload": ("YCoCg two-band SH over the normal, ridge %g, 5-d key" % args.sh_ridge) if sh else "RGB",
                    "parallelism": f"sessions x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "mean": float(np.mean(step_ms))},
@@ -1030,6 +1047,9 @@ def main(argv=None) -> None:
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=60.0, help="serving: device memory for tables")
+    ap.add_argument("--payload", default="rgb", choices=["rgb", "sh"],
+                    help="cell payload: RGB, or YCoCg with luminance in two SH bands over the normal")
+    ap.add_argument("--sh-ridge", type=float, default=0.01, help="SH payload: ridge on band 1")
     ap.add_argument("--batched-extra", type=int, default=1,
                     help="single-session runs at N=1 also measure the 64-session batched form (extra key)")
     args = ap.parse_args(argv)

@@ -52,6 +52,12 @@
  * any of p, n, d, L, w is non-finite, d is zero, a cell index leaves [-2^15, 2^15),
  * w < 0, w > 2^15 or |fl32(w * L_c)| > 2^15.  A vertex whose fixed-point weight
  * round(w * 2^F) is 0 carries no weight and is skipped silently (zero_weight_vertices).
+ * Sum range: an accepted vertex adds codes of magnitude at most 2^(15+F) (the SH payload's
+ * normal moments: below 2^(16+F)), so every sum is exact while fewer than 2^(48-F) vertices
+ * (SH payload: 2^(47-F)) are inserted into a table between two updates -- 2^24 at F = 24.
+ * The host counts the vertices handed to the inserts (dropped ones included) and sets the
+ * sticky PSF_STATUS_SUM_RANGE once an iteration reaches that count; the device adds modulo
+ * 2^64 (two's complement), so a sum that does overflow wraps.
  */
 #ifndef PSF_H
 #define PSF_H
@@ -72,6 +78,9 @@ extern "C" {
 #define PSF_STATUS_TABLE_FULL 1u /* a key found no slot within the probe bound; its vertices were dropped */
 #define PSF_STATUS_RANGE 2u      /* at least one vertex failed the range rule */
 #define PSF_STATUS_TIMEOUT 4u    /* a bounded device-side wait gave up (batched step) */
+#define PSF_STATUS_SUM_RANGE 8u  /* so many vertices were inserted between two updates that a cell's
+                                    fixed-point sum may have left the 64-bit range (see the range rule);
+                                    sums then wrap modulo 2^64 */
 
 #define PSF_MAX_PROBE 4096u      /* slots a probe visits before declaring the table full */
 #define PSF_MAX_BATCH 256u       /* tables per psf_batch_step call */
@@ -103,6 +112,27 @@ typedef struct {
                                the queries and by psf_insert_progressive (the paper's level choice is a
                                path-footprint heuristic it does not give; the depth stands in for the
                                footprint).  A table holds up to L times the cells of a flat one. */
+    uint32_t payload;       /* what a cell holds.  0: RGB (three sums, an RGB approximant).  1: the YCoCg
+                               two-band spherical-harmonics payload of Section "Basis functions and data
+                               structures: spatio-directional hashing" (last paragraph): luminance in two
+                               SH bands over the normal, chroma per cell, so the basis spans normal
+                               variation inside a cell.  Per cell and iteration the luminance is fitted by
+                               weighted least squares, Y(n) ~ a + g . n (the span of bands 0 and 1),
+                               minimising sum w (Y - a - g . n)^2 + sh_ridge * W |g|^2 (W = sum w); chroma
+                               (Co, Cg) is the weighted mean; eq. (10)-(11) blend the six coefficients;
+                               a query reads the cell's fit at the vertex's own normal, turned back into
+                               RGB (R = Y + Co - Cg, G = Y + Cg, B = Y - Co - Cg).  The paper names the
+                               representation but not its estimator: the fit is this library's reading,
+                               whose band-0 part is eq. (6)'s weighted mean.  Payload 1 needs
+                               cache_fp16 = 0, levels <= 1 and key_layout != 2; its cells are 192-byte
+                               records plus a dense 8-byte key; it adds |n_k| <= 1 + 2^-10 (unit
+                               normals) to the range rule;
+                               psf_insert_slots, psf_query_cv_slots, psf_insert_progressive, psf_export
+                               and the batched calls reject it (PSF_ERR_INVALID_ARG), psf_export_sh
+                               exports it. */
+    float sh_ridge;         /* payload 1: ridge weight on band 1 relative to the cell's weight, >= 0 and
+                               finite (0.01 suggested; 0 allows an unregularised fit, and an iteration
+                               whose normal moments leave the system singular then keeps band 1 at 0) */
 } psf_config;
 
 /* One exported cell (psf_export), in ascending key order. */
@@ -115,6 +145,17 @@ typedef struct {
     uint16_t L_fp16[3];   /* its FP16 copy (IEEE binary16 bits; 0 when cache_fp16 = 0) */
     uint16_t pad;
 } psf_cell_record;
+
+/* One exported cell of a table with the SH payload (psf_export_sh), in ascending key order. */
+typedef struct {
+    uint64_t key;
+    int64_t sum[16];  /* this iteration's fixed-point sums (0 after psf_update): Y, Co, Cg, c_new,
+                         n_x, n_y, n_z, Y n_x, Y n_y, Y n_z, n_x n_x, n_x n_y, n_x n_z, n_y n_y, n_y n_z,
+                         n_z n_z -- each the cell's sum of round(x * 2^F) over its vertices, with x formed
+                         in FP32 as w L_c -> YCoCg, w n_k, (w Y) n_k, (w n_j) n_k */
+    int64_t c_old;    /* cumulative counter of all blended iterations, saturating */
+    float coef[6];    /* a, g_x, g_y, g_z, Co, Cg: luminance a + g . n */
+} psf_sh_cell_record;
 
 typedef struct {
     uint64_t capacity;             /* slots */
@@ -155,9 +196,13 @@ int psf_insert(psf_table* t, const float* d_vertices, uint64_t n, void* stream);
  * the vertex's emitted radiance L_e and t_j as its throughput to vertex j + 1.
  *   field 0 (L~_o, Alg. 1):      value_j = L_e,j + t_j * L~old(x_{j+1})     (last vertex: L_e,j)
  *   field 1 (L~_{o\e}, Alg. 2):  value_j = t_j * (L_e,j+1 + L~old(x_{j+1}))  (last vertex: 0)
- * computed in FP32 from the FP32 approximant (also with cache_fp16), then scattered
- * exactly as psf_insert scatters L = value (range rule included).  The next-event term
- * that Alg. 2 may add at a vertex is the caller's to add through a plain psf_insert. */
+ * computed in FP32 from the FP32 approximant (also with cache_fp16), then scattered as
+ * psf_insert scatters L = value, except for the range rule: it applies to the vertex's own
+ * record (its L_e as the value, and a finite throughput), and the computed value then
+ * saturates at |fl32(w * value)| = 2^15 instead of dropping the vertex (a NaN value drops
+ * it), so the decision never depends on the precision the value is computed in.  The
+ * next-event term that Alg. 2 may add at a vertex is the caller's to add through a plain
+ * psf_insert. */
 int psf_insert_progressive(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, uint32_t field,
                            void* stream);
 
@@ -166,7 +211,8 @@ int psf_insert_progressive(psf_table* t, const float* d_vertices, uint32_t P, ui
  *   L~ = (1 - alpha) L~ + alpha * sum / c_new                    (eq. 10)
  *   c_old = c_old + c_new (saturating), sums = c_new = 0,
  * in FP32, plus the FP16 copy when cache_fp16 = 1; untouched cells keep their state.
- * Returns the sticky status bits as last copied back (>= 0), or a negative error. */
+ * Returns the sticky status bits as last copied back (>= 0, including PSF_STATUS_SUM_RANGE set on the
+ * host), or a negative error.  Resets the count of vertices inserted this iteration. */
 int psf_update(psf_table* t, void* stream);
 
 /* Control-variate estimate for P paths of depth D (d_vertices: D*P records, depth-major).
@@ -215,6 +261,10 @@ int psf_reset(psf_table* t, void* stream);
  * of cells; if it exceeds cap nothing is written and PSF_ERR_NO_MEM is returned.
  * Synchronises `stream`.  Uses a temporary device buffer (stream-ordered allocation). */
 int psf_export(psf_table* t, psf_cell_record* h_out, size_t cap, size_t* n_out, void* stream);
+
+/* psf_export for a table with the SH payload (psf_config.payload = 1); other tables return
+ * PSF_ERR_INVALID_ARG.  Same conventions as psf_export. */
+int psf_export_sh(psf_table* t, psf_sh_cell_record* h_out, size_t cap, size_t* n_out, void* stream);
 
 /* Synchronised statistics and sticky status.  Synchronises `stream`. */
 int psf_get_stats(psf_table* t, psf_stats* out, void* stream);
@@ -331,7 +381,7 @@ int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, const psf_ba
 const char* psf_last_cuda_error(void);
 
 /* ABI version of this header: bump on any incompatible change. */
-#define PSF_ABI_VERSION 6
+#define PSF_ABI_VERSION 7
 int psf_abi_version(void);
 
 #ifdef __cplusplus

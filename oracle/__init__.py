@@ -20,6 +20,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 STATUS_TABLE_FULL = 1
 STATUS_RANGE = 2
+STATUS_SUM_RANGE = 8
 
 RECORD_DTYPE = np.dtype([("key", "<u8"), ("sum", "<i8", (3,)), ("c_new", "<i8"), ("c_old", "<i8"),
                          ("L", "<f8", (3,))])
@@ -39,10 +40,11 @@ class _Config(ctypes.Structure):
 def build(force: bool = False) -> str:
     """Compile liboracle.so with g++ (IEEE single-rounding semantics: no FP contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = f"{_LIB}.{os.getpid()}.tmp"  # concurrent test workers each build their own copy
         cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               _SRC, "-o", _LIB + ".tmp"]
+               _SRC, "-o", tmp]
         subprocess.run(cmd, check=True)
-        os.replace(_LIB + ".tmp", _LIB)
+        os.replace(tmp, _LIB)
     return _LIB
 
 

@@ -49,6 +49,7 @@ namespace {
 
 constexpr uint32_t ST_TABLE_FULL = 1u;  // not produced by the oracle (unbounded map)
 constexpr uint32_t ST_RANGE = 2u;
+constexpr uint32_t ST_SUM_RANGE = 8u;  // an iteration received enough vertices that a sum may wrap
 
 struct Config {
     uint32_t pos_bits_q;
@@ -79,6 +80,7 @@ struct Oracle {
     std::map<CellKey, Cell> cells;
     uint64_t dropped = 0;       // vertices rejected by the range rule
     uint64_t zero_weight = 0;   // vertices whose weight rounds to zero in fixed point
+    uint64_t iter_vertices = 0; // vertices handed to the inserts since the last update
 };
 
 bool finite3(const float* a) { return std::isfinite(a[0]) && std::isfinite(a[1]) && std::isfinite(a[2]); }
@@ -178,6 +180,21 @@ uint64_t pack_key(const Config& c, const CellKey& k) {
     return (level << 61) | (nb << 58) | (dbin << 48) | (bx << 32) | (by << 16) | bz;
 }
 
+// Fixed-point sums add modulo 2^64 (two's complement), as 64-bit integer adders do: the
+// result is defined even where a sum leaves the int64 range.
+int64_t wrap_add(int64_t a, int64_t b) {
+    return static_cast<int64_t>(static_cast<uint64_t>(a) + static_cast<uint64_t>(b));
+}
+
+// The sum-range rule: every accepted vertex adds codes of magnitude at most 2^(15+F)
+// (|fl32(w L_c)| <= 2^15 and w <= 2^15) to a cell, so the sums are exact while fewer than
+// 2^(48-F) vertices are inserted between two updates; `extra_bits` tightens the count for a
+// payload with larger codes.  Returns ST_SUM_RANGE once the iteration's count reaches it.
+uint32_t count_vertices(uint64_t* iter_vertices, uint64_t n, uint32_t frac_bits, uint32_t extra_bits) {
+    *iter_vertices += n;
+    return *iter_vertices >= (uint64_t{1} << (48u - frac_bits - extra_bits)) ? ST_SUM_RANGE : 0u;
+}
+
 int64_t sat_add(int64_t a, int64_t b) {
     // both operands are non-negative counters
     if (a > INT64_MAX - b) return INT64_MAX;
@@ -270,11 +287,12 @@ uint32_t oracle_insert(void* h, const float* verts, uint64_t n) {
         for (uint32_t l = 0; l < level_count(c); ++l) {  // every level's cell receives the vertex
             vertex_cell(c, v, &key, l);
             Cell& cell = o->cells[key];
-            for (int ch = 0; ch < 3; ++ch) cell.sum[ch] += std::llrint(static_cast<double>(prod[ch]) * scale);
-            cell.c_new += cw;
+            for (int ch = 0; ch < 3; ++ch)
+                cell.sum[ch] = wrap_add(cell.sum[ch], std::llrint(static_cast<double>(prod[ch]) * scale));
+            cell.c_new = wrap_add(cell.c_new, cw);
         }
     }
-    return status;
+    return status | count_vertices(&o->iter_vertices, n, c.frac_bits, 0u);
 }
 
 // Progressive update values (Section "Progressive solver", eq. (9); Alg. 1 and Alg. 2):
@@ -285,7 +303,8 @@ uint32_t oracle_insert(void* h, const float* verts, uint64_t n) {
 //   field 1, L~_{o\e} (Alg. 2): value_j = t_j * (L_e,j+1 + L~old(x_{j+1}))  (last vertex: 0;
 //                               the optional next-event-estimation term is not modelled)
 // L~old is read before anything of this call is scattered.  Each vertex is then scattered
-// as oracle_insert does, with L = value_j (fixed point of w * value in FP64).
+// as oracle_insert does, with L = value_j (fixed point of w * value in FP64, saturated at
+// |w * value| = 2^15; the range rule is applied to the vertex's own record).
 uint32_t oracle_insert_progressive(void* h, const float* verts, uint32_t P, uint32_t D, uint32_t field) {
     Oracle* o = static_cast<Oracle*>(h);
     const Config& c = o->cfg;
@@ -313,6 +332,10 @@ uint32_t oracle_insert_progressive(void* h, const float* verts, uint32_t P, uint
             }
         }
     }
+    // A vertex is dropped when its own record fails the range rule (with its L_e as the value:
+    // |fl32(w L_e,c)| <= 2^15, finite throughput) or its computed value is NaN; otherwise the
+    // product w * value saturates at +-2^15, so the FP64 value here and the FP32 value of a
+    // kernel take the same decision even at the bound.
     uint32_t status = 0;
     for (uint64_t i = 0; i < n; ++i) {
         const float* v = verts + 16 * i;
@@ -320,10 +343,15 @@ uint32_t oracle_insert_progressive(void* h, const float* verts, uint32_t P, uint
         bool ok = vertex_cell(c, v, &key);
         const double w = v[3];
         ok = ok && (w >= 0.0) && (w <= 32768.0);
+        for (int ch = 0; ch < 3 && ok; ++ch) {
+            const float own = v[3] * v[12 + ch];  // one FP32 rounding, as oracle_insert
+            ok = std::isfinite(own) && std::fabs(own) <= 32768.0f && std::isfinite(v[ch == 0 ? 7 : ch == 1 ? 11 : 15]);
+        }
         double prod[3] = {0.0, 0.0, 0.0};
         for (int ch = 0; ch < 3 && ok; ++ch) {
             prod[ch] = w * value[3 * i + ch];
-            ok = std::isfinite(prod[ch]) && std::fabs(prod[ch]) <= 32768.0;
+            ok = !std::isnan(prod[ch]);
+            prod[ch] = std::min(std::max(prod[ch], -32768.0), 32768.0);
         }
         if (!ok) {
             status |= ST_RANGE;
@@ -338,11 +366,11 @@ uint32_t oracle_insert_progressive(void* h, const float* verts, uint32_t P, uint
         for (uint32_t l = 0; l < level_count(c); ++l) {
             vertex_cell(c, v, &key, l);
             Cell& cell = o->cells[key];
-            for (int ch = 0; ch < 3; ++ch) cell.sum[ch] += std::llrint(prod[ch] * scale);
-            cell.c_new += cw;
+            for (int ch = 0; ch < 3; ++ch) cell.sum[ch] = wrap_add(cell.sum[ch], std::llrint(prod[ch] * scale));
+            cell.c_new = wrap_add(cell.c_new, cw);
         }
     }
-    return status;
+    return status | count_vertices(&o->iter_vertices, n, c.frac_bits, 0u);
 }
 
 // End-of-iteration temporal blend, eq. (10)-(11), for every cell touched this iteration.
@@ -352,6 +380,11 @@ uint32_t oracle_update(void* h) {
     for (auto& kv : o->cells) {
         Cell& cell = kv.second;
         if (cell.c_new == 0) continue;  // not touched this iteration: left as it is
+        if (cell.c_new < 0) {  // the counter wrapped (ST_SUM_RANGE): this iteration's sums are dropped
+            for (int ch = 0; ch < 3; ++ch) cell.sum[ch] = 0;
+            cell.c_new = 0;
+            continue;
+        }
         const double cn = static_cast<double>(cell.c_new);
         const double co = static_cast<double>(cell.c_old);
         double alpha;
@@ -367,6 +400,7 @@ uint32_t oracle_update(void* h) {
         cell.c_old = sat_add(cell.c_old, cell.c_new);
         cell.c_new = 0;
     }
+    o->iter_vertices = 0;
     return 0;
 }
 
@@ -544,7 +578,8 @@ void oracle_import(void* h, const oracle_record* recs, uint64_t n) {
 // Fixed-point codes, in FP32 with one rounding per step in this order (the kernel takes
 // the same decisions): p_c = w L_c; wY = (p_r/4 + p_g/2) + p_b/4; wCo = p_r/2 - p_b/2;
 // wCg = (p_g/2 - p_r/4) - p_b/4; m_k = w n_k; Yn_k = wY n_k; nn_jk = m_j n_k; each
-// rounded to nearest even at 2^F.  Range rule: that of the RGB payload plus |n_k| <= 2.
+// rounded to nearest even at 2^F.  Range rule: that of the RGB payload plus |n_k| <= 1 + 2^-10
+// (unit normals).
 // ------------------------------------------------------------------------------------
 
 namespace {
@@ -563,6 +598,7 @@ struct ShOracle {
     std::map<CellKey, ShCell> cells;
     uint64_t dropped = 0;
     uint64_t zero_weight = 0;
+    uint64_t iter_vertices = 0;
 };
 
 // The cell fit's RGB at normal n.
@@ -577,6 +613,13 @@ void sh_rgb(const double coef[6], const float* n, double out[3]) {
 double det3(const double m[3][3]) {
     return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
            m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+}
+
+// eq. (11) for the SH payload's cells: the same rule as the RGB blend.
+double sh_alpha(const Config& c, int64_t c_new, int64_t c_old) {
+    const double cn = static_cast<double>(c_new);
+    const double total = static_cast<double>(c_old) + cn;
+    return c.blend_mode == 0 ? std::max(std::sqrt(cn / total), c.alpha_min) : c.alpha_min;
 }
 
 // This iteration's fit of one touched cell (the reading above), in FP64.
@@ -650,7 +693,7 @@ uint32_t oracle_sh_insert(void* h, const float* verts, uint64_t n) {
         bool ok = vertex_cell(c, v, &key);
         const float w = v[3];
         ok = ok && (w >= 0.0f) && (w <= 32768.0f);
-        for (int k = 0; k < 3 && ok; ++k) ok = std::fabs(nr[k]) <= 2.0f;
+        for (int k = 0; k < 3 && ok; ++k) ok = std::fabs(nr[k]) <= 1.0009765625f;
         float p[3] = {0.0f, 0.0f, 0.0f};
         for (int ch = 0; ch < 3 && ok; ++ch) {
             p[ch] = w * v[12 + ch];
@@ -661,7 +704,7 @@ uint32_t oracle_sh_insert(void* h, const float* verts, uint64_t n) {
             o->dropped++;
             continue;
         }
-        const int64_t cw = std::llrint(static_cast<double>(w) * scale);
+        const int64_t cw = fx(w);
         if (cw == 0) {
             o->zero_weight++;
             continue;
@@ -672,23 +715,16 @@ uint32_t oracle_sh_insert(void* h, const float* verts, uint64_t n) {
         float wCg = 0.5f * p[1] - 0.25f * p[0];
         wCg = wCg - 0.25f * p[2];
         const float m[3] = {w * nr[0], w * nr[1], w * nr[2]};
+        const int64_t code[SH_SUMS] = {fx(wY), fx(wCo), fx(wCg), cw,
+                                       fx(m[0]), fx(m[1]), fx(m[2]),
+                                       fx(wY * nr[0]), fx(wY * nr[1]), fx(wY * nr[2]),
+                                       fx(m[0] * nr[0]), fx(m[0] * nr[1]), fx(m[0] * nr[2]),
+                                       fx(m[1] * nr[1]), fx(m[1] * nr[2]), fx(m[2] * nr[2])};
         ShCell& cell = o->cells[key];
-        cell.s[0] += fx(wY);
-        cell.s[1] += fx(wCo);
-        cell.s[2] += fx(wCg);
-        cell.s[3] += cw;
-        for (int k = 0; k < 3; ++k) {
-            cell.s[4 + k] += fx(m[k]);
-            cell.s[7 + k] += fx(wY * nr[k]);
-        }
-        cell.s[10] += fx(m[0] * nr[0]);
-        cell.s[11] += fx(m[0] * nr[1]);
-        cell.s[12] += fx(m[0] * nr[2]);
-        cell.s[13] += fx(m[1] * nr[1]);
-        cell.s[14] += fx(m[1] * nr[2]);
-        cell.s[15] += fx(m[2] * nr[2]);
+        for (int k = 0; k < SH_SUMS; ++k) cell.s[k] = wrap_add(cell.s[k], code[k]);
     }
-    return status;
+    // the normal moments reach 2^15 (1 + 2^-10)^2 per vertex: one bit fewer vertices
+    return status | count_vertices(&o->iter_vertices, n, c.frac_bits, 1u);
 }
 
 // eq. (10)-(11) on the six coefficients of every touched cell.
@@ -698,15 +734,18 @@ uint32_t oracle_sh_update(void* h) {
     for (auto& kv : o->cells) {
         ShCell& cell = kv.second;
         if (cell.s[3] == 0) continue;
-        const double cn = static_cast<double>(cell.s[3]);
-        const double co = static_cast<double>(cell.c_old);
-        const double alpha = c.blend_mode == 0 ? std::max(std::sqrt(cn / (co + cn)), c.alpha_min) : c.alpha_min;
+        if (cell.s[3] < 0) {  // the counter wrapped (ST_SUM_RANGE): this iteration's sums are dropped
+            for (int k = 0; k < SH_SUMS; ++k) cell.s[k] = 0;
+            continue;
+        }
+        const double alpha = sh_alpha(c, cell.s[3], cell.c_old);
         double fit[6];
         sh_fit(cell, o->ridge, fit);
         for (int k = 0; k < 6; ++k) cell.coef[k] = (1.0 - alpha) * cell.coef[k] + alpha * fit[k];
         cell.c_old = sat_add(cell.c_old, cell.s[3]);
         for (int k = 0; k < SH_SUMS; ++k) cell.s[k] = 0;
     }
+    o->iter_vertices = 0;
     return 0;
 }
 
@@ -769,6 +808,7 @@ uint64_t oracle_sh_export(void* h, oracle_sh_record* out, uint64_t cap) {
 }
 
 uint32_t oracle_status_range() { return ST_RANGE; }
+uint32_t oracle_status_sum_range() { return ST_SUM_RANGE; }
 uint32_t oracle_status_table_full() { return ST_TABLE_FULL; }
 
 }  // extern "C"

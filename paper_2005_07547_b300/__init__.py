@@ -11,10 +11,14 @@ marshals arguments.  There is no CPU fallback.
 
 from ._abi import (  # noqa: F401
     CELL_DTYPE,
+    PAYLOAD_RGB,
+    PAYLOAD_SH,
+    SH_CELL_DTYPE,
     Config,
     MAX_BATCH,
     MAX_PROBE,
     STATUS_RANGE,
+    STATUS_SUM_RANGE,
     STATUS_TABLE_FULL,
     STATUS_TIMEOUT,
     Stats,

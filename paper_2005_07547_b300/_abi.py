@@ -24,6 +24,7 @@ NOALLOC_MAX_ITEMS = 64
 STATUS_TABLE_FULL = 1
 STATUS_RANGE = 2
 STATUS_TIMEOUT = 4
+STATUS_SUM_RANGE = 8
 
 MAX_PROBE = 4096
 MAX_BATCH = 256
@@ -48,15 +49,21 @@ class Config(ctypes.Structure):
         ("blend_mode", ctypes.c_uint32),
         ("key_layout", ctypes.c_uint32),
         ("levels", ctypes.c_uint32),
+        ("payload", ctypes.c_uint32),
+        ("sh_ridge", ctypes.c_float),
     ]
+
+
+PAYLOAD_RGB = 0
+PAYLOAD_SH = 1  # YCoCg, luminance in two SH bands over the normal
 
 
 def make_config(log2_capacity: int = 16, pos_bits: int = 4, dir_bits: int = 2, use_normal: bool = True,
                 alpha_min: float = 0.1, beta: float = 1.0, cv_max_depth: int = 0xFFFFFFFF,
                 frac_bits: int = 24, cache_fp16: bool = False, blend_mode: int = 0, key_layout: int = 0,
-                levels: int = 1) -> Config:
+                levels: int = 1, payload: int = PAYLOAD_RGB, sh_ridge: float = 0.01) -> Config:
     return Config(log2_capacity, pos_bits, dir_bits, int(bool(use_normal)), alpha_min, beta, cv_max_depth,
-                  frac_bits, int(bool(cache_fp16)), blend_mode, key_layout, levels)
+                  frac_bits, int(bool(cache_fp16)), blend_mode, key_layout, levels, payload, sh_ridge)
 
 
 class Stats(ctypes.Structure):
@@ -120,6 +127,9 @@ class BatchConfig(ctypes.Structure):
 CELL_DTYPE = np.dtype([("key", "<u8"), ("sum", "<i8", (3,)), ("c_new", "<i8"), ("c_old", "<i8"),
                        ("L", "<f4", (3,)), ("L_fp16", "<u2", (3,)), ("pad", "<u2")], align=True)
 assert CELL_DTYPE.itemsize == 72
+# psf_sh_cell_record (168 bytes)
+SH_CELL_DTYPE = np.dtype([("key", "<u8"), ("sum", "<i8", (16,)), ("c_old", "<i8"), ("coef", "<f4", (6,))], align=True)
+assert SH_CELL_DTYPE.itemsize == 168
 
 # every function the header declares, with its ctypes signature
 _vp, _u32, _u64, _i = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
@@ -136,6 +146,7 @@ SIGNATURES = {
     "psf_query_biased": (_i, [_vp, _vp, _u32, _u32, ctypes.c_float, _u32, _u32, _vp, _vp]),
     "psf_reset": (_i, [_vp, _vp]),
     "psf_export": (_i, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _vp]),
+    "psf_export_sh": (_i, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _vp]),
     "psf_get_stats": (_i, [_vp, ctypes.POINTER(Stats), _vp]),
     "psf_destroy": (_i, [_vp]),
     "psf_set_launch_config": (_i, [_vp, ctypes.POINTER(LaunchConfig)]),

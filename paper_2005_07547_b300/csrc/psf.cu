@@ -33,6 +33,15 @@ thread_local std::string psf_g_last_error;
 
 using psf::kThreads;
 
+// Every accepted vertex adds codes of magnitude at most 2^(15+F) to a cell (|fl32(w L_c)| and
+// w are at most 2^15; the SH payload's (w n_j) n_k at most 2^15 (1 + 2^-10)^2 after rounding),
+// so n vertices cannot overflow a 64-bit sum while n < 2^(48-F) (SH: 2^(47-F)).
+void psf_count_iteration_vertices(psf_table* t, unsigned long long n) {
+    const unsigned shift = 48u - t->cfg.frac_bits - (t->cfg.payload == psf::kPayloadSH ? 1u : 0u);
+    t->iter_vertices += n;
+    if (t->iter_vertices >= (1ull << shift)) t->host_status |= PSF_STATUS_SUM_RANGE;
+}
+
 bool psf_cuda_ok(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return true;
     psf_g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
@@ -93,6 +102,7 @@ size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 // all go to DRAM (1920x1080: 7.1 vs 6.25 G vertices/s); and an FP16 query reads the compact
 // copy, so its keys are best in the dense array beside it (12.95 vs 12.34 G vertices/s).
 bool keys_inline(const psf_config* c) {
+    if (c->payload == psf::kPayloadSH) return false;  // SH records have no key field
     return c->key_layout == 2 || (c->key_layout == 0 && c->log2_capacity <= 22 && !c->cache_fp16);
 }
 
@@ -104,6 +114,10 @@ bool config_valid(const psf_config* c) {
     if (c->frac_bits < 8 || c->frac_bits > 32) return false;
     if (!(c->alpha_min >= 0.0f && c->alpha_min <= 1.0f)) return false;
     if (!(c->beta == c->beta) || c->blend_mode > 1 || c->use_normal > 1 || c->cache_fp16 > 1) return false;
+    if (c->payload > psf::kPayloadSH) return false;
+    if (c->payload == psf::kPayloadSH &&
+        (c->cache_fp16 || c->levels > 1 || c->key_layout == 2 || !(c->sh_ridge >= 0.0f && c->sh_ridge <= 3.0e38f)))
+        return false;
     return true;
 }
 
@@ -116,7 +130,7 @@ Layout layout_of(const psf_config* c) {
     L.keys = off;
     if (!keys_inline(c)) off = align256(off + cap * sizeof(unsigned long long));
     L.slots = off;
-    off = align256(off + cap * sizeof(Slot));
+    off = align256(off + cap * (c->payload == psf::kPayloadSH ? sizeof(psf::SlotSH) : sizeof(Slot)));
     L.mirror = off;
     if (c->cache_fp16) off = align256(off + cap * sizeof(uint2));
     L.dirty = off;
@@ -198,6 +212,56 @@ __global__ void __launch_bounds__(kThreads, kHier ? 4 : 0) k_insert(TableView t,
     }
 }
 
+// k_insert for a table with the SH payload (flat tables; the next grid-stride tile's records
+// are loaded while the current one probes and adds).
+template <int kMode>
+__global__ void __launch_bounds__(kThreads) k_insert_sh(TableView t, const float4* __restrict__ v, unsigned long long n) {
+    __shared__ unsigned s_max_probe;
+    __shared__ unsigned long long s_leaders;
+    __shared__ psf::ShSums s_stage[kThreads];
+    if (threadIdx.x == 0) {
+        s_max_probe = 0;
+        s_leaders = 0;
+    }
+    __syncthreads();
+    psf::ShSums* stage = s_stage + (threadIdx.x & ~31u);
+    unsigned max_len = 0, leaders = 0;
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+    unsigned long long base = static_cast<unsigned long long>(blockIdx.x) * blockDim.x;
+    float4 v0 = make_float4(0, 0, 0, 0), v1 = v0, v2 = v0, v3 = v0;
+    if (base + threadIdx.x < n) {
+        const float4* r = v + 4 * (base + threadIdx.x);
+        v0 = __ldcs(r);
+        v1 = __ldcs(r + 1);
+        v2 = __ldcs(r + 2);
+        v3 = __ldcs(r + 3);
+    }
+    for (; base < n; base += stride) {
+        const unsigned long long nx = base + stride + threadIdx.x;
+        float4 n0 = make_float4(0, 0, 0, 0), n1 = n0, n2 = n0, n3 = n0;
+        if (nx < n) {
+            const float4* r = v + 4 * nx;
+            n0 = __ldcs(r);
+            n1 = __ldcs(r + 1);
+            n2 = __ldcs(r + 2);
+            n3 = __ldcs(r + 3);
+        }
+        psf::insert_warp_sh<kMode>(t, base + threadIdx.x < n, v0, v1, v2, v3, &max_len, stage, &leaders);
+        v0 = n0;
+        v1 = n1;
+        v2 = n2;
+        v3 = n3;
+    }
+    psf::bulk_wait_done();
+    if (max_len) atomicMax(&s_max_probe, max_len);
+    if ((threadIdx.x & 31u) == 0 && leaders) atomicAdd(&s_leaders, static_cast<unsigned long long>(leaders));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_max_probe) atomicMax(&t.hdr->max_probe, s_max_probe);
+        if (s_leaders) atomicAdd(&t.hdr->leaders, s_leaders);
+    }
+}
+
 // Progressive update values (Section "Progressive solver", eq. (9); Alg. 1 and Alg. 2):
 // one thread per path walks its vertices last to first; the FP32 approximant of each
 // vertex's cell (read before this iteration's blend, so it is L~old) feeds the value of
@@ -243,7 +307,14 @@ __global__ void __launch_bounds__(kThreads) k_insert_progressive(TableView t, co
                 val.y = __fmul_rn(v2.w, __fadd_rn(le_next.y, c_next.y));
                 val.z = __fmul_rn(v3.w, __fadd_rn(le_next.z, c_next.z));
             }
-            psf::insert_warp<kMode, kHier>(t, valid, v0, v1, v2, val, &max_len, stage, &leaders);
+            // the range rule applies to the vertex's own record (its L_e as the value, a finite
+            // throughput); a record that fails it is dropped through a NaN value, and the
+            // computed value of one that passes saturates at |w value| = 2^15
+            const bool own_ok = fabsf(__fmul_rn(v0.w, v3.x)) <= 32768.0f && fabsf(__fmul_rn(v0.w, v3.y)) <= 32768.0f &&
+                                fabsf(__fmul_rn(v0.w, v3.z)) <= 32768.0f && isfinite(v1.w) && isfinite(v2.w) &&
+                                isfinite(v3.w);
+            if (!own_ok) val.x = __int_as_float(0x7fffffff);
+            psf::insert_warp<kMode, kHier, false, true>(t, valid, v0, v1, v2, val, &max_len, stage, &leaders);
             c_next = c;
             le_next = le;
         }
@@ -399,6 +470,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_query_staged(TableView t, psf::
     }
 }
 
+template <bool kSH = false>
 __global__ void __launch_bounds__(kThreads, 4) k_update(TableView t) {
     __shared__ unsigned long long s_touched;
     if (threadIdx.x == 0) s_touched = 0;
@@ -412,20 +484,20 @@ __global__ void __launch_bounds__(kThreads, 4) k_update(TableView t) {
         t.hdr->iterations += 1;
     }
     unsigned long long touched = 0;
-    for (unsigned long long w0 = warp * 32ull; w0 < nwords; w0 += nwarps * 32ull) touched += psf::update_words(t, w0, nwords);
+    for (unsigned long long w0 = warp * 32ull; w0 < nwords; w0 += nwarps * 32ull) touched += psf::update_words<kSH>(t, w0, nwords);
     if ((threadIdx.x & 31u) == 0 && touched) atomicAdd(&s_touched, touched);
     __syncthreads();
     if (threadIdx.x == 0 && s_touched) atomicAdd(&t.hdr->touched, s_touched);
 }
 
-template <bool kSlots = false>
+template <bool kSlots = false, bool kSH = false>
 __global__ void __launch_bounds__(kThreads) k_query(TableView t, psf::Estimator e, const float4* __restrict__ v,
                                                     unsigned P, unsigned D, float* __restrict__ out,
                                                     const unsigned* __restrict__ slots = nullptr) {
     const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
     for (unsigned long long p = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < P;
          p += stride)
-        psf::query_path<kSlots>(t, e, v, P, D, p, out, slots);
+        psf::query_path<kSlots, kSH>(t, e, v, P, D, p, out, slots);
 }
 
 __global__ void __launch_bounds__(kThreads) k_export(TableView t, unsigned long long s0, unsigned long long s1,
@@ -468,6 +540,36 @@ __global__ void __launch_bounds__(kThreads) k_export(TableView t, unsigned long 
     }
 }
 
+__global__ void __launch_bounds__(kThreads) k_export_sh(TableView t, unsigned long long s0, unsigned long long s1,
+                                                        psf_sh_cell_record* out, unsigned* count) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+    for (unsigned long long base = s0 + static_cast<unsigned long long>(blockIdx.x) * blockDim.x; base < s1;
+         base += stride) {
+        const unsigned long long s = base + threadIdx.x;
+        const unsigned long long key = s < s1 ? *psf::key_ptr(t, s) : psf::kEmpty;
+        const bool live = key != psf::kEmpty;
+        const unsigned m = __ballot_sync(psf::kFull, live);
+        if (!m) continue;
+        unsigned first = 0;
+        if (lane == 0) first = atomicAdd(count, __popc(m));
+        first = __shfl_sync(psf::kFull, first, 0);
+        if (!live) continue;
+        psf_sh_cell_record r;
+        r.key = key;
+        const psf::SlotSH& a = t.sh[s];
+        for (int c = 0; c < psf::kShSums; ++c) r.sum[c] = a.s[c];
+        r.c_old = a.c_old;
+        r.coef[0] = a.coef_a.x;
+        r.coef[1] = a.coef_a.y;
+        r.coef[2] = a.coef_a.z;
+        r.coef[3] = a.coef_a.w;
+        r.coef[4] = a.coef_c.x;
+        r.coef[5] = a.coef_c.y;
+        out[first + __popc(m & ((1u << lane) - 1u))] = r;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_count_live(TableView t, unsigned long long* count) {
     __shared__ unsigned long long s_count;
     if (threadIdx.x == 0) s_count = 0;
@@ -494,8 +596,12 @@ __global__ void __launch_bounds__(kThreads) k_init_keys(TableView t) {
 __global__ void __launch_bounds__(kThreads) k_reset(TableView t) {
     const unsigned long long cap = 1ull << t.log2cap;
     const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
-    for (unsigned long long s = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; s < cap; s += stride)
-        t.slots[s].c_old = 0;
+    for (unsigned long long s = static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x; s < cap; s += stride) {
+        if (t.payload == psf::kPayloadSH)
+            t.sh[s].c_old = 0;
+        else
+            t.slots[s].c_old = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -563,6 +669,57 @@ void launch_insert_progressive(const psf_table* t, const float4* v, uint32_t P, 
 
 }  // namespace
 
+namespace {
+
+// Every occupied cell as a record of type Rec (written by `kernel` over chunks of slots),
+// sorted by key on the host.
+template <typename Rec>
+int export_cells(psf_table* t, void (*kernel)(TableView, unsigned long long, unsigned long long, Rec*, unsigned*),
+                 Rec* h_out, size_t cap_out, size_t* n_out, void* stream) {
+    if (!n_out || (cap_out && !h_out)) return PSF_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned long long cap = 1ull << t->cfg.log2_capacity;
+    const unsigned long long chunk = std::min<unsigned long long>(cap, 1ull << 20);
+    void* scratch = nullptr;
+    const size_t scratch_bytes = chunk * sizeof(Rec) + 256;
+    if (!cuda_ok(cudaMallocAsync(&scratch, scratch_bytes, st), "cudaMallocAsync")) return PSF_ERR_CUDA;
+    Rec* d_rec = reinterpret_cast<Rec*>(static_cast<char*>(scratch) + 256);
+    unsigned* d_count = static_cast<unsigned*>(scratch);
+    std::vector<Rec> all;
+    int rc = PSF_OK;
+    for (unsigned long long s0 = 0; s0 < cap && rc == PSF_OK; s0 += chunk) {
+        unsigned n = 0;
+        const int grid = grid_for(t, 4, chunk);
+        if (!cuda_ok(cudaMemsetAsync(d_count, 0, sizeof(unsigned), st), "cudaMemsetAsync")) {
+            rc = PSF_ERR_CUDA;
+            break;
+        }
+        kernel<<<grid, kThreads, 0, st>>>(t->view, s0, s0 + chunk, d_rec, d_count);
+        if (!cuda_ok(cudaGetLastError(), "k_export") ||
+            !cuda_ok(cudaMemcpyAsync(&n, d_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") ||
+            !cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize")) {
+            rc = PSF_ERR_CUDA;
+            break;
+        }
+        const size_t old = all.size();
+        all.resize(old + n);
+        if (n && !cuda_ok(cudaMemcpyAsync(all.data() + old, d_rec, n * sizeof(Rec), cudaMemcpyDeviceToHost, st),
+                          "cudaMemcpyAsync"))
+            rc = PSF_ERR_CUDA;
+        if (rc == PSF_OK && !cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize")) rc = PSF_ERR_CUDA;
+    }
+    cudaFreeAsync(scratch, st);
+    if (!cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize") && rc == PSF_OK) rc = PSF_ERR_CUDA;
+    if (rc != PSF_OK) return rc;
+    std::sort(all.begin(), all.end(), [](const Rec& a, const Rec& b) { return a.key < b.key; });
+    *n_out = all.size();
+    if (all.size() > cap_out) return PSF_ERR_NO_MEM;
+    if (!all.empty()) std::memcpy(h_out, all.data(), all.size() * sizeof(Rec));
+    return PSF_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int psf_abi_version(void) { return PSF_ABI_VERSION; }
@@ -589,7 +746,10 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     t->bytes = bytes;
     if (!cuda_ok(cudaGetDevice(&t->device), "cudaGetDevice") ||
         !cuda_ok(cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device), "cudaDeviceGetAttribute") ||
-        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->update_blocks_per_sm, k_update, kThreads, 0), "occupancy") ||
+        !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->update_blocks_per_sm,
+                                                               cfg->payload == psf::kPayloadSH ? k_update<true> : k_update<false>,
+                                                               kThreads, 0),
+                 "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->query_blocks_per_sm, k_query<false>, kThreads, 0), "occupancy") ||
         !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->staged_query_blocks_per_sm, k_query_staged, kThreads, 0),
                  "occupancy")) {
@@ -634,6 +794,9 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     v.alpha_min = cfg->alpha_min;
     v.beta = cfg->beta;
     v.levels = cfg->levels == 0 ? 1u : cfg->levels;
+    v.payload = cfg->payload;
+    v.ridge = cfg->sh_ridge;
+    v.sh = cfg->payload == psf::kPayloadSH ? reinterpret_cast<psf::SlotSH*>(base + L.slots) : nullptr;
 
     const size_t cap = size_t{1} << cfg->log2_capacity;
     bool ok = cuda_ok(cudaMemsetAsync(base, 0, L.total, st), "cudaMemsetAsync");
@@ -658,19 +821,27 @@ int psf_insert(psf_table* t, const float* d_vertices, uint64_t n, void* stream) 
     if (!d_vertices || (reinterpret_cast<uintptr_t>(d_vertices) & 15u)) return PSF_ERR_INVALID_ARG;
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->view.levels > 1)
+    psf_count_iteration_vertices(t, n);
+    if (t->view.payload == psf::kPayloadSH) {
+        if (t->launch.insert_mode == 1)
+            launch_sized(t, k_insert_sh<psf::kAggNone>, n, st, t->view, v, n);
+        else
+            launch_sized(t, k_insert_sh<psf::kAggWarp>, n, st, t->view, v, n);
+    } else if (t->view.levels > 1) {
         launch_insert<true>(t, v, n, st);
-    else
+    } else {
         launch_insert<false>(t, v, n, st);
+    }
     return cuda_ok(cudaGetLastError(), "k_insert") ? PSF_OK : PSF_ERR_CUDA;
 }
 
 int psf_insert_progressive(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, uint32_t field, void* stream) {
-    if (!t || field > 1) return PSF_ERR_INVALID_ARG;
+    if (!t || field > 1 || t->view.payload != psf::kPayloadRGB) return PSF_ERR_INVALID_ARG;
     if (P == 0 || D == 0) return PSF_OK;
     if (!d_vertices || (reinterpret_cast<uintptr_t>(d_vertices) & 15u)) return PSF_ERR_INVALID_ARG;
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    psf_count_iteration_vertices(t, static_cast<unsigned long long>(P) * D);
     if (t->view.levels > 1)
         launch_insert_progressive<true>(t, v, P, D, field, st);
     else
@@ -682,9 +853,13 @@ int psf_update(psf_table* t, void* stream) {
     if (!t) return PSF_ERR_INVALID_ARG;
     const unsigned long long nwords = ((1ull << t->cfg.log2_capacity) + 31ull) >> 5;
     const int grid = grid_for(t, t->update_blocks_per_sm, nwords, t->launch.update_blocks_per_sm);  // a warp per 32 words
-    k_update<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view);
+    if (t->view.payload == psf::kPayloadSH)
+        k_update<true><<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view);
+    else
+        k_update<false><<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(t->view);
     if (!cuda_ok(cudaGetLastError(), "k_update")) return PSF_ERR_CUDA;
-    return static_cast<int>(*reinterpret_cast<volatile unsigned*>(t->h_status) & 0x7fffffffu);
+    t->iter_vertices = 0;
+    return static_cast<int>((*reinterpret_cast<volatile unsigned*>(t->h_status) | t->host_status) & 0x7fffffffu);
 }
 
 namespace {
@@ -698,7 +873,11 @@ int launch_query(psf_table* t, const psf::Estimator& e, const float* d_vertices,
         return PSF_ERR_INVALID_ARG;
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->launch.vertex_staging & 2u) {
+    if (t->view.payload == psf::kPayloadSH) {
+        const int grid = grid_for(t, resident_blocks(t, reinterpret_cast<const void*>(k_query<false, true>)), P,
+                                  t->launch.query_blocks_per_sm);
+        k_query<false, true><<<grid, kThreads, 0, st>>>(t->view, e, v, P, D, d_out_rgb);
+    } else if (t->launch.vertex_staging & 2u) {
         const int grid = grid_for(t, t->staged_query_blocks_per_sm, P, t->launch.query_blocks_per_sm);
         k_query_staged<<<grid, kThreads, 0, st>>>(t->view, e, v, P, D, d_out_rgb);
     } else {
@@ -722,7 +901,7 @@ int psf_query_biased(psf_table* t, const float* d_vertices, uint32_t P, uint32_t
 }
 
 int psf_insert_slots(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, uint32_t* d_slots, void* stream) {
-    if (!t) return PSF_ERR_INVALID_ARG;
+    if (!t || t->view.payload != psf::kPayloadRGB) return PSF_ERR_INVALID_ARG;
     const unsigned long long n = static_cast<unsigned long long>(P) * D;
     if (n == 0) return PSF_OK;
     if (!d_vertices || !d_slots || (reinterpret_cast<uintptr_t>(d_vertices) & 15u) ||
@@ -730,6 +909,7 @@ int psf_insert_slots(psf_table* t, const float* d_vertices, uint32_t P, uint32_t
         return PSF_ERR_INVALID_ARG;
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    psf_count_iteration_vertices(t, n);
     if (t->view.levels > 1)
         launch_insert_slots<true>(t, v, P, D, d_slots, st);
     else
@@ -739,7 +919,7 @@ int psf_insert_slots(psf_table* t, const float* d_vertices, uint32_t P, uint32_t
 
 int psf_query_cv_slots(psf_table* t, const float* d_vertices, const uint32_t* d_slots, uint32_t P, uint32_t D,
                        float* d_out_rgb, void* stream) {
-    if (!t) return PSF_ERR_INVALID_ARG;
+    if (!t || t->view.payload != psf::kPayloadRGB) return PSF_ERR_INVALID_ARG;
     if (P == 0 || D == 0) return PSF_OK;
     if (!d_vertices || !d_slots || !d_out_rgb || (reinterpret_cast<uintptr_t>(d_vertices) & 15u) ||
         (reinterpret_cast<uintptr_t>(d_slots) & 3u) || (reinterpret_cast<uintptr_t>(d_out_rgb) & 3u))
@@ -781,46 +961,13 @@ int psf_get_launch_config(const psf_table* t, psf_launch_config* out) {
 }
 
 int psf_export(psf_table* t, psf_cell_record* h_out, size_t cap_out, size_t* n_out, void* stream) {
-    if (!t || !n_out || (cap_out && !h_out)) return PSF_ERR_INVALID_ARG;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const unsigned long long cap = 1ull << t->cfg.log2_capacity;
-    const unsigned long long chunk = std::min<unsigned long long>(cap, 1ull << 20);
-    void* scratch = nullptr;
-    const size_t scratch_bytes = chunk * sizeof(psf_cell_record) + 256;
-    if (!cuda_ok(cudaMallocAsync(&scratch, scratch_bytes, st), "cudaMallocAsync")) return PSF_ERR_CUDA;
-    psf_cell_record* d_rec = reinterpret_cast<psf_cell_record*>(static_cast<char*>(scratch) + 256);
-    unsigned* d_count = static_cast<unsigned*>(scratch);
-    std::vector<psf_cell_record> all;
-    int rc = PSF_OK;
-    for (unsigned long long s0 = 0; s0 < cap && rc == PSF_OK; s0 += chunk) {
-        unsigned n = 0;
-        const int grid = grid_for(t, 4, chunk);
-        if (!cuda_ok(cudaMemsetAsync(d_count, 0, sizeof(unsigned), st), "cudaMemsetAsync")) {
-            rc = PSF_ERR_CUDA;
-            break;
-        }
-        k_export<<<grid, kThreads, 0, st>>>(t->view, s0, s0 + chunk, d_rec, d_count);
-        if (!cuda_ok(cudaGetLastError(), "k_export") ||
-            !cuda_ok(cudaMemcpyAsync(&n, d_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") ||
-            !cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize")) {
-            rc = PSF_ERR_CUDA;
-            break;
-        }
-        const size_t old = all.size();
-        all.resize(old + n);
-        if (n && !cuda_ok(cudaMemcpyAsync(all.data() + old, d_rec, n * sizeof(psf_cell_record), cudaMemcpyDeviceToHost, st),
-                          "cudaMemcpyAsync"))
-            rc = PSF_ERR_CUDA;
-        if (rc == PSF_OK && !cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize")) rc = PSF_ERR_CUDA;
-    }
-    cudaFreeAsync(scratch, st);
-    if (!cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize") && rc == PSF_OK) rc = PSF_ERR_CUDA;
-    if (rc != PSF_OK) return rc;
-    std::sort(all.begin(), all.end(), [](const psf_cell_record& a, const psf_cell_record& b) { return a.key < b.key; });
-    *n_out = all.size();
-    if (all.size() > cap_out) return PSF_ERR_NO_MEM;
-    if (!all.empty()) std::memcpy(h_out, all.data(), all.size() * sizeof(psf_cell_record));
-    return PSF_OK;
+    if (!t || t->view.payload != psf::kPayloadRGB) return PSF_ERR_INVALID_ARG;
+    return export_cells(t, k_export, h_out, cap_out, n_out, stream);
+}
+
+int psf_export_sh(psf_table* t, psf_sh_cell_record* h_out, size_t cap_out, size_t* n_out, void* stream) {
+    if (!t || t->view.payload != psf::kPayloadSH) return PSF_ERR_INVALID_ARG;
+    return export_cells(t, k_export_sh, h_out, cap_out, n_out, stream);
 }
 
 int psf_get_stats(psf_table* t, psf_stats* out, void* stream) {
@@ -846,7 +993,7 @@ int psf_get_stats(psf_table* t, psf_stats* out, void* stream) {
     out->dropped_vertices = h.dropped;
     out->zero_weight_vertices = h.zero_weight;
     out->iterations = h.iterations;
-    out->status = h.status;
+    out->status = h.status | t->host_status;
     out->max_probe = h.max_probe;
     out->table_bytes = layout_of(&t->cfg).total;
     out->touched_cells = h.touched;

@@ -256,7 +256,7 @@ int psf_batch_set(psf_batch* b, const psf_batch_item* items, uint32_t n, void* s
     if (!b || n > b->max_items || (n && !items)) return PSF_ERR_INVALID_ARG;
     for (uint32_t i = 0; i < n; ++i) {
         const psf_batch_item& it = items[i];
-        if (!it.table) return PSF_ERR_INVALID_ARG;
+        if (!it.table || it.table->view.payload != psf::kPayloadRGB) return PSF_ERR_INVALID_ARG;
         const unsigned long long nv = static_cast<unsigned long long>(it.P) * it.D;
         if (nv && (!it.d_vertices || !it.d_out_rgb || (reinterpret_cast<uintptr_t>(it.d_vertices) & 15u) ||
                    (reinterpret_cast<uintptr_t>(it.d_out_rgb) & 3u) || (reinterpret_cast<uintptr_t>(it.d_slots) & 3u)))
@@ -275,6 +275,9 @@ int psf_batch_set(psf_batch* b, const psf_batch_item* items, uint32_t n, void* s
         const psf_batch_item& it = items[i];
         BatchItemDev& d = dev[i];
         d.t = it.table->view;
+        // each launch inserts the item's vertices and blends them: one iteration of P*D vertices
+        it.table->iter_vertices = 0;
+        psf_count_iteration_vertices(it.table, static_cast<unsigned long long>(it.P) * it.D);
         d.v = reinterpret_cast<const float4*>(it.d_vertices);
         d.out = it.d_out_rgb;
         d.slots = it.d_slots;
@@ -407,7 +410,7 @@ extern "C" int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, c
     if (c.insert_mode > 1) return PSF_ERR_INVALID_ARG;
     for (uint32_t i = 0; i < n; ++i) {
         const psf_batch_item& it = items[i];
-        if (!it.table) return PSF_ERR_INVALID_ARG;
+        if (!it.table || it.table->view.payload != psf::kPayloadRGB) return PSF_ERR_INVALID_ARG;
         const unsigned long long nv = static_cast<unsigned long long>(it.P) * it.D;
         if (nv && (!it.d_vertices || !it.d_out_rgb || (reinterpret_cast<uintptr_t>(it.d_vertices) & 15u) ||
                    (reinterpret_cast<uintptr_t>(it.d_out_rgb) & 3u) || (reinterpret_cast<uintptr_t>(it.d_slots) & 3u)))
@@ -433,6 +436,9 @@ extern "C" int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, c
         const psf_batch_item& it = items[i];
         BatchItemDev& d = dev_items[i];
         d.t = it.table->view;
+        // each launch inserts the item's vertices and blends them: one iteration of P*D vertices
+        it.table->iter_vertices = 0;
+        psf_count_iteration_vertices(it.table, static_cast<unsigned long long>(it.P) * it.D);
         d.v = reinterpret_cast<const float4*>(it.d_vertices);
         d.out = it.d_out_rgb;
         d.slots = it.d_slots;

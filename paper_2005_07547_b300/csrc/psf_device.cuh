@@ -9,6 +9,8 @@
 //                                   64-byte block per cell
 //   mirror uint2[cap] (8 B)         FP16 copy of L~ read by queries (cache_fp16 = 1)
 //   dirty  u32[cap/32]              one bit per slot: touched this iteration
+// Tables with the YCoCg two-band SH payload keep dense keys and 192-byte SlotSH records
+// (sixteen 64-bit sums, c_old, six coefficients) instead of Slot and the FP16 copy.
 // Inserts touch keys + the first 32-byte sector of a slot (atomics); the blend reads and
 // writes exactly one 64-byte block per touched cell, the DRAM access granularity, so
 // scattered cells cost no partial bursts; queries read keys + the second sector of the
@@ -56,6 +58,8 @@ static_assert(sizeof(Slot) == 64, "one slot is one 64-byte block");
 constexpr int kAggWarp = 0;  // lanes of a warp on one key merged, one probe per group
 constexpr int kAggNone = 1;  // every vertex probes and adds on its own
 
+struct SlotSH;  // the SH payload's slot record (below)
+
 struct TableView {
     DevHeader* hdr;
     unsigned long long* keys;  // key of slot s at keys[s * key_stride]
@@ -76,7 +80,13 @@ struct TableView {
     float beta;
     uint32_t levels;    // hierarchy levels, 1..4 (1: a flat table)
     uint32_t sum_path;  // how a group's sums reach its slot: kSumsBulk or kSumsRed
+    uint32_t payload;   // kPayloadRGB or kPayloadSH (the cell holds a YCoCg two-band SH fit)
+    float ridge;        // SH payload: ridge weight on band 1, relative to the cell's weight
+    SlotSH* sh;         // SH payload: the 192-byte slot records (slots is unused then)
 };
+
+constexpr uint32_t kPayloadRGB = 0;
+constexpr uint32_t kPayloadSH = 1;
 
 constexpr uint32_t kSumsBulk = 0;  // one 32-byte bulk reduction from shared memory (TMA)
 constexpr uint32_t kSumsRed = 1;   // four 64-bit reductions
@@ -267,13 +277,23 @@ __device__ __forceinline__ unsigned read_level(const TableView& t, unsigned j) {
 }
 
 // Fixed-point contributions of an accepted vertex (eq. 5-6): round(fl32(w L_c) 2^F), round(w 2^F).
-// Returns 1 = accepted, 2 = range rule, 3 = zero fixed-point weight.
+// Returns 1 = accepted, 2 = range rule, 3 = zero fixed-point weight.  With kSaturate (the
+// progressive values, whose record has passed the range rule already) a product beyond
+// +-2^15 is saturated there instead of rejected; a NaN product is still rejected.
+template <bool kSaturate = false>
 __device__ __forceinline__ int vertex_values(const TableView& t, const float4& v0, const float4& v3,
                                              long long* s, long long* cw) {
     const float w = v0.w;
     if (!(w >= 0.0f && w <= 32768.0f)) return 2;
-    const float p0 = __fmul_rn(w, v3.x), p1 = __fmul_rn(w, v3.y), p2 = __fmul_rn(w, v3.z);
-    if (!(fabsf(p0) <= 32768.0f && fabsf(p1) <= 32768.0f && fabsf(p2) <= 32768.0f)) return 2;
+    float p0 = __fmul_rn(w, v3.x), p1 = __fmul_rn(w, v3.y), p2 = __fmul_rn(w, v3.z);
+    if constexpr (kSaturate) {
+        if (isnan(p0) || isnan(p1) || isnan(p2)) return 2;
+        p0 = fminf(fmaxf(p0, -32768.0f), 32768.0f);
+        p1 = fminf(fmaxf(p1, -32768.0f), 32768.0f);
+        p2 = fminf(fmaxf(p2, -32768.0f), 32768.0f);
+    } else if (!(fabsf(p0) <= 32768.0f && fabsf(p1) <= 32768.0f && fabsf(p2) <= 32768.0f)) {
+        return 2;
+    }
     const float sc = pow2f(static_cast<int>(t.frac_bits));
     *cw = __float2ll_rn(__fmul_rn(w, sc));
     if (*cw == 0) return 3;
@@ -429,7 +449,7 @@ __device__ __forceinline__ unsigned heads_after(unsigned joined, unsigned lane) 
 // them).  A lane's LaneSums slot holds its own sums while a kHier group merges and the sums
 // its bulk reduction reads; every write to the slot waits for the lane's earlier bulk
 // reductions to have read it.
-template <int kMode, bool kHier = false, bool kSlots = false>
+template <int kMode, bool kHier = false, bool kSlots = false, bool kSaturate = false>
 __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, const float4& v0, const float4& v1,
                                             const float4& v2, const float4& v3, unsigned* max_len,
                                             LaneSums* stage, unsigned* leaders, SlotNote* note = nullptr) {
@@ -441,7 +461,7 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
         if (!cell_key(t, v0, v1, v2, &key0))
             cls = 2;
         else
-            cls = vertex_values(t, v0, v3, own, &own[3]);
+            cls = vertex_values<kSaturate>(t, v0, v3, own, &own[3]);
     }
     const unsigned accepted = __ballot_sync(kFull, cls == 1);
     const unsigned ranged = __ballot_sync(kFull, cls == 2);
@@ -538,6 +558,269 @@ __device__ __forceinline__ void insert_warp(const TableView& t, bool valid, cons
 }
 
 // ---------------------------------------------------------------------------
+// YCoCg two-band spherical-harmonics payload (Section "Basis functions and data
+// structures: spatio-directional hashing", last paragraph: luminance in two SH bands over
+// the normal, chroma per cell).  Per cell and iteration the luminance is fitted over the
+// normal by weighted least squares on the two bands (their span is {1, n_x, n_y, n_z}:
+// Y(n) ~ a + g . n) with a ridge of `ridge` times the cell's weight on band 1; chroma is
+// the weighted mean.  The integer moments make the fit order-free: the centred moments
+// W sum(w n n^T) - sum(w n) sum(w n)^T and W sum(w Y n) - sum(w Y) sum(w n) are formed
+// exactly in 128-bit integers and rounded once to FP32.  eq. (10)-(11) blend the six
+// coefficients.  YCoCg: Y = R/4 + G/2 + B/4, Co = R/2 - B/2, Cg = G/2 - R/4 - B/4.
+// ---------------------------------------------------------------------------
+constexpr int kShSums = 16;  // Y, Co, Cg, c_new, n(3), Y n(3), n n(xx, xy, xz, yy, yz, zz)
+
+struct alignas(64) SlotSH {
+    long long s[kShSums];  // this iteration's fixed-point sums (bytes 0-127: one bulk reduction)
+    long long c_old;       // cumulative counter of blended iterations
+    long long unused;
+    float4 coef_a;         // a, g_x, g_y, g_z: luminance a + g . n
+    float2 coef_c;         // Co, Cg
+    float pad[6];
+};
+static_assert(sizeof(SlotSH) == 192, "an SH slot is three 64-byte blocks");
+
+struct alignas(16) ShSums {
+    long long v[kShSums];
+};
+
+// Fixed-point codes of an accepted vertex for the SH payload, each rounded to nearest even at
+// 2^F from an FP32 value taken with one rounding per step in this order: p_c = w L_c,
+// wY = (p_r/4 + p_g/2) + p_b/4, wCo = p_r/2 - p_b/2, wCg = (p_g/2 - p_r/4) - p_b/4,
+// m_k = w n_k, Yn_k = wY n_k, nn_jk = m_j n_k.  Returns 1 = accepted, 2 = range rule (that of
+// the RGB payload, plus |n_k| <= 1 + 2^-10: unit normals), 3 = zero fixed-point weight.
+__device__ __forceinline__ int sh_values(const TableView& t, const float4& v0, const float4& v1, const float4& v3,
+                                         long long c[kShSums]) {
+    const float w = v0.w;
+    if (!(w >= 0.0f && w <= 32768.0f)) return 2;
+    constexpr float kNormalBound = 1.0009765625f;  // 1 + 2^-10
+    if (!(fabsf(v1.x) <= kNormalBound && fabsf(v1.y) <= kNormalBound && fabsf(v1.z) <= kNormalBound)) return 2;
+    const float p0 = __fmul_rn(w, v3.x), p1 = __fmul_rn(w, v3.y), p2 = __fmul_rn(w, v3.z);
+    if (!(fabsf(p0) <= 32768.0f && fabsf(p1) <= 32768.0f && fabsf(p2) <= 32768.0f)) return 2;
+    const float sc = pow2f(static_cast<int>(t.frac_bits));
+    const long long cw = __float2ll_rn(__fmul_rn(w, sc));
+    if (cw == 0) return 3;
+    const float wY = __fadd_rn(__fadd_rn(__fmul_rn(0.25f, p0), __fmul_rn(0.5f, p1)), __fmul_rn(0.25f, p2));
+    const float wCo = __fsub_rn(__fmul_rn(0.5f, p0), __fmul_rn(0.5f, p2));
+    const float wCg = __fsub_rn(__fsub_rn(__fmul_rn(0.5f, p1), __fmul_rn(0.25f, p0)), __fmul_rn(0.25f, p2));
+    const float mx = __fmul_rn(w, v1.x), my = __fmul_rn(w, v1.y), mz = __fmul_rn(w, v1.z);
+    auto fx = [sc](float x) { return __float2ll_rn(__fmul_rn(x, sc)); };
+    c[0] = fx(wY);
+    c[1] = fx(wCo);
+    c[2] = fx(wCg);
+    c[3] = cw;
+    c[4] = fx(mx);
+    c[5] = fx(my);
+    c[6] = fx(mz);
+    c[7] = fx(__fmul_rn(wY, v1.x));
+    c[8] = fx(__fmul_rn(wY, v1.y));
+    c[9] = fx(__fmul_rn(wY, v1.z));
+    c[10] = fx(__fmul_rn(mx, v1.x));
+    c[11] = fx(__fmul_rn(mx, v1.y));
+    c[12] = fx(__fmul_rn(mx, v1.z));
+    c[13] = fx(__fmul_rn(my, v1.y));
+    c[14] = fx(__fmul_rn(my, v1.z));
+    c[15] = fx(__fmul_rn(mz, v1.z));
+    return 1;
+}
+
+// One warp's worth of vertices into an SH table (flat tables only): classify, merge runs of
+// adjacent lanes on one key (kAggWarp, the segmented shuffle reduction of insert_warp over
+// the sixteen sums), then one head per group probes and adds the group's sums to the
+// slot's first 128 bytes with one bulk reduction.
+template <int kMode>
+__device__ __forceinline__ void insert_warp_sh(const TableView& t, bool valid, const float4& v0, const float4& v1,
+                                               const float4& v2, const float4& v3, unsigned* max_len, ShSums* stage,
+                                               unsigned* leaders) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned long long key = 0;
+    long long own[kShSums];
+#pragma unroll
+    for (int c = 0; c < kShSums; ++c) own[c] = 0;
+    int cls = 0;
+    if (valid) {
+        if (!cell_key(t, v0, v1, v2, &key))
+            cls = 2;
+        else
+            cls = sh_values(t, v0, v1, v3, own);
+    }
+    const unsigned accepted = __ballot_sync(kFull, cls == 1);
+    const unsigned ranged = __ballot_sync(kFull, cls == 2);
+    const unsigned zero_w = __ballot_sync(kFull, cls == 3);
+    if (lane == 0 && (ranged | zero_w)) {
+        if (ranged) {
+            atomicOr(&t.hdr->status, kStatusRange);
+            atomicAdd(&t.hdr->dropped, static_cast<unsigned long long>(__popc(ranged)));
+        }
+        if (zero_w) atomicAdd(&t.hdr->zero_weight, static_cast<unsigned long long>(__popc(zero_w)));
+    }
+    bool head = cls == 1;
+    unsigned members = 1u << lane;
+    if (kMode == kAggWarp) {
+        const unsigned long long prev = __shfl_up_sync(kFull, key, 1);
+        const bool joins = cls == 1 && lane > 0 && ((accepted >> (lane - 1)) & 1u) && prev == key;
+        const unsigned joined = __ballot_sync(kFull, joins);
+        if (joined) {
+            const unsigned heads = ~joined;
+#pragma unroll
+            for (unsigned off = 1; off < 32; off <<= 1) {
+                const bool in_run = lane + off < 32 && ((heads >> (lane + 1)) & ((1u << off) - 1u)) == 0;
+#pragma unroll
+                for (int c = 0; c < kShSums; ++c) {
+                    const long long o = __shfl_down_sync(kFull, own[c], off);
+                    if (in_run) own[c] += o;
+                }
+            }
+        }
+        head = cls == 1 && !joins;
+        members |= heads_after(joined, lane);
+    }
+    long long slot;
+    unsigned len;
+    probe_warp(t, head, key, &slot, &len);
+    if (head) {
+        *max_len = len > *max_len ? len : *max_len;
+        if (slot < 0) {
+            atomicOr(&t.hdr->status, kStatusTableFull);
+            atomicAdd(&t.hdr->dropped, static_cast<unsigned long long>(__popc(members)));
+        } else {
+            bulk_wait_read();
+            ShSums* src = stage + lane;
+#pragma unroll
+            for (int c = 0; c < kShSums; c += 2)
+                *reinterpret_cast<longlong2*>(&src->v[c]) = make_longlong2(own[c], own[c + 1]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], %2;" ::"l"(t.sh + slot),
+                         "r"(smem_u32(src)), "r"(128u)
+                         : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            atomicOr(t.dirty + (slot >> 5), 1u << (slot & 31));
+        }
+    }
+    *leaders += __popc(__ballot_sync(kFull, head));
+}
+
+// A signed 128-bit integer rounded to the nearest float: the bits below the top 64 are
+// folded into a sticky bit, which keeps the single rounding of the 64-bit conversion
+// correct, then the exponent is restored exactly.
+__device__ __forceinline__ float i128_to_float(__int128 x) {
+    const bool neg = x < 0;
+    const unsigned __int128 m = neg ? static_cast<unsigned __int128>(0) - static_cast<unsigned __int128>(x)
+                                    : static_cast<unsigned __int128>(x);
+    const unsigned long long hi = static_cast<unsigned long long>(m >> 64);
+    float f;
+    if (hi == 0) {
+        f = __ull2float_rn(static_cast<unsigned long long>(m));
+    } else {
+        const int sh = 64 - __clzll(static_cast<long long>(hi));  // 1..64
+        const unsigned long long kept = static_cast<unsigned long long>(m >> sh);
+        const unsigned long long low = static_cast<unsigned long long>(m);
+        const unsigned long long lost = sh == 64 ? low : (low & ((1ull << sh) - 1ull));
+        f = ldexpf(__ull2float_rn(kept | (lost != 0ull ? 1ull : 0ull)), sh);
+    }
+    return neg ? -f : f;
+}
+
+// This iteration's SH fit of one touched cell in FP32: out = a, g_x, g_y, g_z, Co, Cg.  The
+// regularised normal equations (S + ridge I) g = s, with S and s the centred moments over
+// W^2, are solved by a Cholesky factorisation; a pivot that is not positive (the
+// regularised matrix is not positive definite) leaves band 1 at 0 for this iteration.
+__device__ __forceinline__ void sh_fit(float ridge, const long long S[kShSums], float out[6]) {
+    const long long W = S[3];
+    const float fW = __ll2float_rn(W);
+    const float inv = __fdiv_rn(1.0f, fW);
+    auto centred = [W, inv](long long wxy, long long x, long long y) {
+        const __int128 m = static_cast<__int128>(W) * wxy - static_cast<__int128>(x) * y;
+        return __fmul_rn(__fmul_rn(i128_to_float(m), inv), inv);
+    };
+    const float a00 = __fadd_rn(centred(S[10], S[4], S[4]), ridge);
+    const float a01 = centred(S[11], S[4], S[5]);
+    const float a02 = centred(S[12], S[4], S[6]);
+    const float a11 = __fadd_rn(centred(S[13], S[5], S[5]), ridge);
+    const float a12 = centred(S[14], S[5], S[6]);
+    const float a22 = __fadd_rn(centred(S[15], S[6], S[6]), ridge);
+    const float r0 = centred(S[7], S[0], S[4]);
+    const float r1 = centred(S[8], S[0], S[5]);
+    const float r2 = centred(S[9], S[0], S[6]);
+    float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+    if (a00 > 0.0f) {
+        const float l00 = sqrtf(a00);
+        const float l10 = __fdiv_rn(a01, l00), l20 = __fdiv_rn(a02, l00);
+        const float d11 = __fsub_rn(a11, __fmul_rn(l10, l10));
+        if (d11 > 0.0f) {
+            const float l11 = sqrtf(d11);
+            const float l21 = __fdiv_rn(__fsub_rn(a12, __fmul_rn(l20, l10)), l11);
+            const float d22 = __fsub_rn(__fsub_rn(a22, __fmul_rn(l20, l20)), __fmul_rn(l21, l21));
+            if (d22 > 0.0f) {
+                const float l22 = sqrtf(d22);
+                const float y0 = __fdiv_rn(r0, l00);
+                const float y1 = __fdiv_rn(__fsub_rn(r1, __fmul_rn(l10, y0)), l11);
+                const float y2 = __fdiv_rn(__fsub_rn(__fsub_rn(r2, __fmul_rn(l20, y0)), __fmul_rn(l21, y1)), l22);
+                g2 = __fdiv_rn(y2, l22);
+                g1 = __fdiv_rn(__fsub_rn(y1, __fmul_rn(l21, g2)), l11);
+                g0 = __fdiv_rn(__fsub_rn(__fsub_rn(y0, __fmul_rn(l10, g1)), __fmul_rn(l20, g2)), l00);
+            }
+        }
+    }
+    const float Ym = __fdiv_rn(__ll2float_rn(S[0]), fW);
+    const float nx = __fdiv_rn(__ll2float_rn(S[4]), fW), ny = __fdiv_rn(__ll2float_rn(S[5]), fW),
+                nz = __fdiv_rn(__ll2float_rn(S[6]), fW);
+    out[0] = __fsub_rn(Ym, __fadd_rn(__fadd_rn(__fmul_rn(g0, nx), __fmul_rn(g1, ny)), __fmul_rn(g2, nz)));
+    out[1] = g0;
+    out[2] = g1;
+    out[3] = g2;
+    out[4] = __fdiv_rn(__ll2float_rn(S[1]), fW);
+    out[5] = __fdiv_rn(__ll2float_rn(S[2]), fW);
+}
+
+// eq. (10)-(11) on the six coefficients of one touched SH slot, then its sums are cleared.
+__device__ __forceinline__ void blend_sh(const TableView& t, unsigned long long s) {
+    SlotSH* p = t.sh + s;
+    const longlong2* q = reinterpret_cast<const longlong2*>(p->s);
+    long long S[kShSums];
+#pragma unroll
+    for (int c = 0; c < kShSums; c += 2) {
+        const longlong2 x = __ldcg(q + c / 2);
+        S[c] = x.x;
+        S[c + 1] = x.y;
+    }
+    const long long co = __ldcg(&p->c_old);
+    float4 ca = __ldcg(&p->coef_a);
+    float2 cc = __ldcg(&p->coef_c);
+    const long long cn = S[3];
+    if (cn > 0) {
+        const long long ctot = co > (0x7fffffffffffffffll - cn) ? 0x7fffffffffffffffll : co + cn;
+        float alpha = t.alpha_min;
+        if (t.blend_mode == 0)
+            alpha = fmaxf(sqrtf(__fdiv_rn(__ll2float_rn(cn), __ll2float_rn(ctot))), t.alpha_min);
+        const float keep = 1.0f - alpha;
+        float fit[6];
+        sh_fit(t.ridge, S, fit);
+        ca.x = fmaf(alpha, fit[0], keep * ca.x);
+        ca.y = fmaf(alpha, fit[1], keep * ca.y);
+        ca.z = fmaf(alpha, fit[2], keep * ca.z);
+        ca.w = fmaf(alpha, fit[3], keep * ca.w);
+        cc.x = fmaf(alpha, fit[4], keep * cc.x);
+        cc.y = fmaf(alpha, fit[5], keep * cc.y);
+        __stcg(&p->c_old, ctot);
+        __stcg(&p->coef_a, ca);
+        __stcg(&p->coef_c, cc);
+    }
+    longlong2* w = reinterpret_cast<longlong2*>(p->s);
+#pragma unroll
+    for (int c = 0; c < kShSums / 2; ++c) __stcg(w + c, make_longlong2(0, 0));
+}
+
+// The RGB of SH slot s at normal n: Y = a + g . n, then the YCoCg inverse
+// R = Y + Co - Cg, G = Y + Cg, B = Y - Co - Cg.
+__device__ __forceinline__ float3 sh_eval(const TableView& t, unsigned long long s, const float4& n) {
+    const float4 a = __ldcg(&t.sh[s].coef_a);
+    const float2 c = __ldcg(&t.sh[s].coef_c);
+    const float Y = __fadd_rn(__fadd_rn(__fadd_rn(a.x, __fmul_rn(a.y, n.x)), __fmul_rn(a.z, n.y)), __fmul_rn(a.w, n.z));
+    return make_float3(__fsub_rn(__fadd_rn(Y, c.x), c.y), __fadd_rn(Y, c.y), __fsub_rn(__fsub_rn(Y, c.x), c.y));
+}
+
+// ---------------------------------------------------------------------------
 // Temporal blend of one touched cell: eq. (10)-(11).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint2 pack_half4(float a, float b, float c) {
@@ -610,6 +893,7 @@ __device__ __forceinline__ unsigned select_bit(unsigned w, unsigned n) {
 // One warp blends every touched slot of dirty words [w0, w0 + 32): the set bits are
 // compacted across the warp (prefix sum of popcounts) so all 32 lanes stay busy.
 // Returns the number of cells blended (the same value in every lane).
+template <bool kSH = false>
 __device__ __forceinline__ unsigned update_words(const TableView& t, unsigned long long w0, unsigned long long nwords) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long wi = w0 + lane;
@@ -639,7 +923,10 @@ __device__ __forceinline__ unsigned update_words(const TableView& t, unsigned lo
         const unsigned oe = __shfl_sync(kFull, excl, owner);
         if (idx < total) {
             const unsigned long long slot = (w0 + owner) * 32ull + select_bit(ow, idx - oe);
-            blend_store(t, slot, load_slot(t, slot));
+            if constexpr (kSH)
+                blend_sh(t, slot);
+            else
+                blend_store(t, slot, load_slot(t, slot));
         }
     }
     return total;
@@ -685,6 +972,29 @@ __device__ __forceinline__ float3 cell_value(const TableView& t, const float4& v
     return zero;
 }
 
+// The SH payload's approximant of the vertex's cell evaluated at the vertex's own normal (0 if
+// the cell is absent); the home slot's coefficients are loaded together with its key.
+__device__ __forceinline__ float3 cell_value_sh(const TableView& t, const float4& v0, const float4& v1,
+                                                const float4& v2) {
+    const float3 zero = make_float3(0.0f, 0.0f, 0.0f);
+    unsigned long long key;
+    if (!cell_key(t, v0, v1, v2, &key)) return zero;
+    const unsigned long long mask = (1ull << t.log2cap) - 1ull;
+    const unsigned long long keep = policy_evict_last();
+    unsigned long long s = home_slot(t, key);
+    const unsigned long long k0 = load_key(key_ptr(t, s), keep);
+    const float3 c0 = sh_eval(t, s, v1);
+    if (k0 == key) return c0;
+    if (k0 == kEmpty) return zero;
+    for (unsigned i = 1; i < t.max_probe; ++i) {
+        s = (s + 1) & mask;
+        const unsigned long long k = load_key(key_ptr(t, s), keep);
+        if (k == key) return sh_eval(t, s, v1);
+        if (k == kEmpty) return zero;
+    }
+    return zero;
+}
+
 // The estimators that use the approximant are affine in (L_j, t_j C_{j+1}, C_j):
 //   control variate (Section "Control variates", CVEstimator):  a = 1, b = c = beta
 //   biased predictor-corrector (Section "Biased estimation"):    a = b = gamma, c = 1
@@ -707,7 +1017,7 @@ __device__ __forceinline__ float combine(const Estimator& e, float L, float tj, 
 // All vertices of path p (depth-major records j*P + p), last to first so that each vertex
 // is probed once: its cell value serves as C_j here and as C_{j+1} for vertex j - 1.  With
 // kSlots a vertex whose slot the insert noted reads the approximant there directly.
-template <bool kSlots = false>
+template <bool kSlots = false, bool kSH = false>
 __device__ __forceinline__ void query_path(const TableView& t, const Estimator& e, const float4* __restrict__ v,
                                            unsigned P, unsigned D, unsigned long long p, float* __restrict__ out,
                                            const unsigned* __restrict__ slots = nullptr) {
@@ -717,7 +1027,9 @@ __device__ __forceinline__ void query_path(const TableView& t, const Estimator& 
         const float4* r = v + 4 * i;  // streamed once: evict-first
         const float4 v0 = __ldcs(r), v1 = __ldcs(r + 1), v2 = __ldcs(r + 2), v3 = __ldcs(r + 3);
         float3 c;
-        if constexpr (kSlots) {
+        if constexpr (kSH) {
+            c = cell_value_sh(t, v0, v1, v2);
+        } else if constexpr (kSlots) {
             const unsigned sl = __ldcs(slots + i);
             c = sl != kNoSlot ? value_at(t, sl) : cell_value(t, v0, v1, v2, false, read_level(t, static_cast<unsigned>(j)));
         } else {

@@ -14,6 +14,8 @@ struct psf_table {
     void* mem;
     size_t bytes;
     unsigned* h_status;  // host-mapped pinned word written by the update (from a process-wide pool)
+    unsigned host_status;           // status bits decided on the host (PSF_STATUS_SUM_RANGE)
+    unsigned long long iter_vertices;  // vertices handed to inserts since the last update
     unsigned* d_status;  // its device address
     int device;
     int sms;
@@ -28,6 +30,10 @@ struct psf_table {
     mutable int occ_blocks[16];
     mutable int occ_n;
 };
+
+// Count n vertices into the table's current iteration; once the count reaches the number
+// beyond which a cell's 64-bit fixed-point sum could overflow, set PSF_STATUS_SUM_RANGE.
+void psf_count_iteration_vertices(psf_table* t, unsigned long long n);
 
 // Records the CUDA error text for psf_last_cuda_error; true if e is cudaSuccess.
 bool psf_cuda_ok(cudaError_t e, const char* what);

@@ -139,17 +139,20 @@ class Table:
         _abi.check(_abi.load().psf_reset(self._h, _stream_handle(stream)), "psf_reset")
 
     def export(self, stream=None) -> np.ndarray:
-        """All occupied cells in ascending key order (synchronises the stream)."""
+        """All occupied cells in ascending key order (synchronises the stream): psf_cell_record
+        rows, or psf_sh_cell_record rows for a table with the SH payload."""
         lib = _abi.load()
+        sh = self.cfg.payload == _abi.PAYLOAD_SH
+        fn, name, dtype = ((lib.psf_export_sh, "psf_export_sh", _abi.SH_CELL_DTYPE) if sh else
+                           (lib.psf_export, "psf_export", _abi.CELL_DTYPE))
         n = ctypes.c_size_t()
-        rc = lib.psf_export(self._h, None, 0, ctypes.byref(n), _stream_handle(stream))
+        rc = fn(self._h, None, 0, ctypes.byref(n), _stream_handle(stream))
         if rc not in (_abi.PSF_OK, _abi.PSF_ERR_NO_MEM):
-            _abi.check(rc, "psf_export")
-        out = np.zeros(n.value, dtype=_abi.CELL_DTYPE)
+            _abi.check(rc, name)
+        out = np.zeros(n.value, dtype=dtype)
         if n.value:
             got = ctypes.c_size_t()
-            _abi.check(lib.psf_export(self._h, out.ctypes.data, n.value, ctypes.byref(got), _stream_handle(stream)),
-                       "psf_export")
+            _abi.check(fn(self._h, out.ctypes.data, n.value, ctypes.byref(got), _stream_handle(stream)), name)
             out = out[:got.value]
         return out
 

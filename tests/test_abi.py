@@ -59,6 +59,9 @@ int main(void) {
   printf("record %zu %zu %zu %zu %zu\n", sizeof(psf_cell_record), offsetof(psf_cell_record, c_new),
          offsetof(psf_cell_record, c_old), offsetof(psf_cell_record, L), offsetof(psf_cell_record, L_fp16));
   printf("stats %zu %zu %zu\n", sizeof(psf_stats), offsetof(psf_stats, status), offsetof(psf_stats, table_bytes));
+  printf("shrec %zu %zu %zu\n", sizeof(psf_sh_cell_record), offsetof(psf_sh_cell_record, c_old),
+         offsetof(psf_sh_cell_record, coef));
+  printf("config2 %zu %zu\n", offsetof(psf_config, payload), offsetof(psf_config, sh_ridge));
   return 0;
 }
 """)
@@ -73,6 +76,9 @@ int main(void) {
                                                         d.fields["L"][1], d.fields["L_fp16"][1])]
     S = _abi.Stats
     assert lines["stats"].split() == [str(x) for x in (ctypes.sizeof(S), S.status.offset, S.table_bytes.offset)]
+    h = _abi.SH_CELL_DTYPE
+    assert lines["shrec"].split() == [str(x) for x in (h.itemsize, h.fields["c_old"][1], h.fields["coef"][1])]
+    assert lines["config2"].split() == [str(x) for x in (C.payload.offset, C.sh_ridge.offset)]
 
 
 def test_table_bytes_and_config_validation(lib):
@@ -89,11 +95,17 @@ def test_table_bytes_and_config_validation(lib):
     # a dense key array costs 8 bytes per slot more than keys inside the slot records
     dense = lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=16, key_layout=1)))
     assert dense == n16 + (1 << 16) * 8  # the automatic choice keeps a 2^16 table's keys inline
+    # the SH payload: 192-byte records and a dense key array
+    sh = lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=16, payload=1)))
+    assert sh == n16 + (1 << 16) * (192 + 8 - 64)
     big = [lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=23, key_layout=k))) for k in (0, 1, 2)]
     assert big[0] == big[1] == big[2] + (1 << 23) * 8  # and uses the dense array from 2^23 slots
     for bad in (dict(log2_capacity=3), dict(log2_capacity=31), dict(dir_bits=6), dict(pos_bits=21),
                 dict(frac_bits=7), dict(frac_bits=33), dict(alpha_min=1.5), dict(alpha_min=-0.1),
-                dict(blend_mode=2), dict(beta=float("nan")), dict(key_layout=3)):
+                dict(blend_mode=2), dict(beta=float("nan")), dict(key_layout=3), dict(payload=2),
+                dict(payload=1, cache_fp16=True), dict(payload=1, levels=2), dict(payload=1, key_layout=2),
+                dict(payload=1, sh_ridge=-1.0), dict(payload=1, sh_ridge=float("inf")),
+                dict(payload=1, sh_ridge=float("nan"))):
         assert lib.psf_table_bytes(ctypes.byref(_abi.make_config(**bad))) == 0, bad
     assert lib.psf_table_bytes(None) == 0
 
@@ -117,7 +129,7 @@ def test_host_detected_argument_errors(lib):
     assert lib.psf_insert_slots(None, None, 1, 1, None, None) == _abi.PSF_ERR_INVALID_ARG
     assert lib.psf_query_cv_slots(None, None, None, 1, 1, None, None) == _abi.PSF_ERR_INVALID_ARG
     assert lib.psf_destroy(None) == _abi.PSF_OK
-    assert lib.psf_abi_version() == 6
+    assert lib.psf_abi_version() == 7
 
 
 def test_product_package_does_not_touch_the_oracle():

@@ -375,3 +375,59 @@ def test_many_tables_reuse_pooled_status_words(psf_mod):
         assert t.stats()["status"] == 0
     for t in alive:
         t.close()
+
+
+@pytest.mark.parametrize("n", [65535, 65536])
+def test_sum_range_status_and_wrapped_sums(psf_mod, oracle_mod, n):
+    """At F = 32 every code is at most 2^47, so sums are exact below 2^16 vertices per
+    iteration; at that count PSF_STATUS_SUM_RANGE is set and a sum that leaves the int64 range
+    wraps modulo 2^64 -- on the GPU exactly as in the oracle, whatever the order of additions."""
+    import torch
+
+    recs = [vertex((0.3, 0.3, 0.3), w=1.0, L=(32768.0, -32768.0, 1.0))] * n
+    v = stack(recs)
+    cfg = psf_mod.make_config(log2_capacity=8, pos_bits=2, dir_bits=1, frac_bits=32)
+    table = psf_mod.Table(cfg)
+    ora = _oracle_for(oracle_mod, cfg)
+    table.insert(torch.from_numpy(v).cuda())
+    st = ora.insert(v)
+    check_after_insert(table.export(), ora.export())
+    stats = table.stats()
+    assert bool(stats["status"] & psf_mod.STATUS_SUM_RANGE) == bool(st & oracle_mod.STATUS_SUM_RANGE) == (n >= 65536)
+    assert table.update() & psf_mod.STATUS_SUM_RANGE == (psf_mod.STATUS_SUM_RANGE if n >= 65536 else 0)
+    ora.update()
+    check_after_update(table.export(), ora.export())
+    table.close()
+
+
+@pytest.mark.parametrize("field", [0, 1])
+def test_progressive_value_saturates_like_the_oracle(psf_mod, oracle_mod, field):
+    """Progressive values at and past |w value| = 2^15 are saturated on both sides (keys,
+    counters and dropped counts exact), and a record outside the range rule is dropped by
+    its own emission even where its progressive value is small."""
+    import torch
+
+    C = 32767.0
+    first = stack([vertex((0.53, 0.53, 0.53), L=(C, C, C))])
+    paths = []
+    for t0, le0 in ((1.0, 1.0), (1.0000001, 1.0), (2.0, 1.0), (1e30, 0.5), (0.5, 40000.0), (float("nan"), 1.0)):
+        paths.append((vertex((0.03, 0.03, 0.03), L=(le0, le0, le0), t=(t0, t0, t0)), vertex((0.53, 0.53, 0.53))))
+    P, D = len(paths), 2
+    v = stack([p[0] for p in paths] + [p[1] for p in paths])
+    cfg = psf_mod.make_config(log2_capacity=8, pos_bits=4, dir_bits=2)
+    table = psf_mod.Table(cfg)
+    ora = _oracle_for(oracle_mod, cfg)
+    table.insert(torch.from_numpy(first).cuda())
+    table.update()
+    ora.insert(first)
+    ora.update()
+    table.insert_progressive(torch.from_numpy(v).cuda(), P, D, field)
+    st = ora.insert_progressive(v, P, D, field)
+    g, r = table.export(), ora.export()
+    assert np.array_equal(g["key"], r["key"]) and np.array_equal(g["c_new"], r["c_new"])
+    stats = table.stats()
+    assert (stats["dropped_vertices"], stats["zero_weight_vertices"]) == ora.counters()
+    assert stats["status"] == st == psf_mod.STATUS_RANGE
+    # the saturated cell sums agree up to the FP32 rounding of the values below the bound
+    assert np.all(np.abs(g["sum"].astype(np.float64) - r["sum"]) <= 1e-6 * np.abs(r["sum"]) + 2 * P)
+    table.close()

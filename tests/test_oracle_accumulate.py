@@ -237,3 +237,36 @@ def test_counter_saturates(oracle_mod):
     r = o.export()[0]
     assert int(r["c_old"]) == np.iinfo(np.int64).max
     assert math.isclose(float(r["L"][0]), 0.9 * 2.0 + 0.1 * 1.0, rel_tol=1e-12)  # alpha = alpha_min
+
+
+@pytest.mark.parametrize("n,wraps", [(65535, False), (65536, True)])
+def test_sum_range_rule_and_modular_sums(oracle_mod, n, wraps):
+    """Sum range: with F = 32 every code is at most 2^47 in magnitude, so sums are exact while
+    fewer than 2^(48-32) = 65536 vertices reach the table in one iteration; at that count the
+    status bit is set, and sums that leave the int64 range wrap modulo 2^64 (two's complement).
+    Here every vertex adds +2^47 (red), -2^47 (green) and 2^32 (weight) to one cell."""
+    v = stack([vertex((0.3, 0.3, 0.3), w=1.0, L=(32768.0, -32768.0, 1.0))] * n)
+    o = oracle_mod.Oracle(pos_bits=2, dir_bits=1, frac_bits=32)
+    st = o.insert(v)
+    assert bool(st & oracle_mod.STATUS_SUM_RANGE) == wraps
+    r = o.export()[0]
+
+    def as_int64(x):
+        x %= 1 << 64
+        return x - (1 << 64) if x >= 1 << 63 else x
+
+    assert int(r["sum"][0]) == as_int64(n << 47)  # 2^63 wraps to -2^63
+    assert int(r["sum"][1]) == as_int64(-(n << 47))  # -2^63 is still representable
+    assert int(r["c_new"]) == n << 32
+    o.update()
+    assert o.insert(v[:1]) == 0  # the update starts a new count
+
+
+def test_sum_range_counts_every_insert_of_the_iteration(oracle_mod):
+    """The count covers all vertices handed to the inserts between two updates, dropped ones too."""
+    bad = vertex((0.3, 0.3, 0.3), w=-1.0)  # dropped by the range rule, still counted
+    good = vertex((0.3, 0.3, 0.3))
+    o = oracle_mod.Oracle(pos_bits=2, dir_bits=1, frac_bits=32)
+    assert o.insert(stack([bad] * 40000)) == oracle_mod.STATUS_RANGE
+    assert o.insert(stack([good] * 25535)) == 0
+    assert o.insert(stack([good])) == oracle_mod.STATUS_SUM_RANGE

@@ -88,12 +88,20 @@ MUTANTS = {
                               'sh_rgb(it->second.coef, verts + 16 * i + 8, C);'),
     "sh_band1_not_blended": ('for (int k = 0; k < 6; ++k) cell.coef[k] = (1.0 - alpha) * cell.coef[k] + alpha * fit[k];',
                             'for (int k = 0; k < 6; ++k) cell.coef[k] = (k >= 1 && k <= 3) ? fit[k] : (1.0 - alpha) * cell.coef[k] + alpha * fit[k];'),
-    "sh_luminance_moment_uses_weight": ('cell.s[7 + k] += fx(wY * nr[k]);',
-                                       'cell.s[7 + k] += fx(m[k]);'),
-    "sh_normal_bound_exclusive": ('ok = std::fabs(nr[k]) <= 2.0f;',
-                                 'ok = std::fabs(nr[k]) < 2.0f;'),
+    "sh_luminance_moment_uses_weight": ('fx(wY * nr[0]), fx(wY * nr[1]), fx(wY * nr[2]),',
+                                       'fx(m[0]), fx(m[1]), fx(m[2]),'),
+    "sh_normal_bound_exclusive": ('ok = std::fabs(nr[k]) <= 1.0009765625f;',
+                                 'ok = std::fabs(nr[k]) < 1.0009765625f;'),
     "sh_cv_sign_of_control": ('(L - c.beta * (t[ch] * C[3 * (idx + P) + ch]) + c.beta * C[3 * idx + ch])',
                              '(L + c.beta * (t[ch] * C[3 * (idx + P) + ch]) + c.beta * C[3 * idx + ch])'),
+    "progressive_value_not_saturated": ("prod[ch] = std::min(std::max(prod[ch], -32768.0), 32768.0);",
+                                        "(void)prod[ch];"),
+    "progressive_record_rule_missing": ("ok = std::isfinite(own) && std::fabs(own) <= 32768.0f && std::isfinite(v[ch == 0 ? 7 : ch == 1 ? 11 : 15]);",
+                                        "ok = std::isfinite(own) || true;"),
+    "sums_saturate_instead_of_wrapping": ("return static_cast<int64_t>(static_cast<uint64_t>(a) + static_cast<uint64_t>(b));",
+                                          "return (b > 0 && a > INT64_MAX - b) ? INT64_MAX : (b < 0 && a < INT64_MIN - b) ? INT64_MIN : a + b;"),
+    "sum_range_count_off_by_one": ("return *iter_vertices >= (uint64_t{1} << (48u - frac_bits - extra_bits)) ? ST_SUM_RANGE : 0u;",
+                                   "return *iter_vertices > (uint64_t{1} << (48u - frac_bits - extra_bits)) ? ST_SUM_RANGE : 0u;"),
     "progressive_alg2_without_throughput": (PROG, PROG.replace("t[ch] * (Le_next[ch] + C_next[ch])",
                                                                "(Le_next[ch] + C_next[ch])")),
 }

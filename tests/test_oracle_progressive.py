@@ -105,8 +105,8 @@ def test_progressive_counters_match_plain_insert(oracle_mod):
 
 
 def test_progressive_weight_range_edges(oracle_mod):
-    """The progressive insert applies the range rule to w and to w * value: w = 2^15 with a
-    value of 1 is accepted, w just above 2^15 is dropped (a one-vertex path: the Alg. 1 value
+    """The progressive insert applies the range rule to the vertex's own record: w = 2^15 with an
+    emission of 1 is accepted, w just above 2^15 is dropped (a one-vertex path: the Alg. 1 value
     is the vertex's own emission)."""
     for w, accepted in ((32768.0, True), (32768.0078125, False), (0.0, True)):
         o = oracle_mod.Oracle(pos_bits=4, dir_bits=2)
@@ -119,3 +119,43 @@ def test_progressive_weight_range_edges(oracle_mod):
             assert status == 0 and zero_w == 1 and len(o) == 0
         else:
             assert status != 0 and dropped == 1 and len(o) == 0
+
+
+def _two_cell_path(oracle_mod, C_next, Le0, t0, w0=1.0, Le1=0.0):
+    """An oracle whose cell B holds the approximant C_next, and one path A -> B."""
+    o = oracle_mod.Oracle(pos_bits=4, dir_bits=2)
+    o.insert(vertex(CELLS[1], L=(C_next, C_next, C_next))[None, :])
+    o.update()
+    v = np.stack([vertex(CELLS[0], w=w0, L=(Le0, Le0, Le0), t=(t0, t0, t0)),
+                  vertex(CELLS[1], L=(Le1, Le1, Le1))]).astype(np.float32)
+    return o, v
+
+
+def _cell_A(o):
+    return [r for r in o.export() if r["key"] == __import__("oracle").vertex_key(o.cfg, vertex(CELLS[0]))]
+
+
+@pytest.mark.parametrize("field", [0, 1])
+@pytest.mark.parametrize("t0", [1.0, 2.0, 1e30])
+def test_progressive_value_saturates_at_the_bound(oracle_mod, field, t0):
+    """A progressive value past |w * value| = 2^15 is saturated there, not dropped: with
+    C(B) = 32767 and L_e = 1 (field 0) the value 1 + t * 32767 is 32768 at t = 1 (exactly the
+    bound) and beyond it for larger t; field 1's t * (0 + 32767) likewise.  The vertex keeps
+    its weight in c_new and nothing is counted as dropped."""
+    o, v = _two_cell_path(oracle_mod, 32767.0, 1.0 if field == 0 else 0.0, t0)
+    st = o.insert_progressive(v, 1, 2, field=field)
+    assert st == 0 and o.counters() == (0, 0)
+    a = _cell_A(o)[0]
+    want = min(32768.0, (1.0 if field == 0 else 0.0) + t0 * 32767.0)
+    assert int(a["sum"][0]) == int(round(want * 2 ** 24)) and int(a["c_new"]) == 1 << 24
+
+
+def test_progressive_drops_by_the_record_not_by_the_value(oracle_mod):
+    """A record that fails the plain range rule is dropped even if its progressive value is
+    small (field 1 does not contain the vertex's own emission); a NaN throughput drops too."""
+    o, v = _two_cell_path(oracle_mod, 1.0, 40000.0, 0.5)
+    assert o.insert_progressive(v, 1, 2, field=1) == oracle_mod.STATUS_RANGE
+    assert o.counters()[0] == 1 and not _cell_A(o)
+    o, v = _two_cell_path(oracle_mod, 1.0, 1.0, float("nan"))
+    assert o.insert_progressive(v, 1, 2, field=0) == oracle_mod.STATUS_RANGE
+    assert o.counters()[0] == 1 and not _cell_A(o)

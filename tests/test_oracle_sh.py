@@ -261,8 +261,8 @@ def test_cv_reads_each_vertex_at_its_own_normal(oracle_mod):
 
 
 def test_range_rule_on_the_normal_and_counters(oracle_mod):
-    recs = [vertex((0.3, 0.3, 0.3), n=(0.0, 0.0, 1.0)), vertex((0.3, 0.3, 0.3), n=(0.0, 2.0, 0.0)),
-            vertex((0.3, 0.3, 0.3), n=(0.0, 0.0, -2.5)), vertex((0.3, 0.3, 0.3), w=2.0 ** -30),
+    recs = [vertex((0.3, 0.3, 0.3), n=(0.0, 0.0, 1.0)), vertex((0.3, 0.3, 0.3), n=(0.0, 1.0009765625, 0.0)),
+            vertex((0.3, 0.3, 0.3), n=(0.0, 0.0, -1.001)), vertex((0.3, 0.3, 0.3), w=2.0 ** -30),
             vertex((0.3, 0.3, 0.3), L=(1.0, np.nan, 1.0))]
     o = oracle_mod.ShOracle(pos_bits=2, dir_bits=1, ridge=0.01, use_normal=False)
     st = o.insert(stack(recs))
