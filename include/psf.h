@@ -266,6 +266,36 @@ int psf_export(psf_table* t, psf_cell_record* h_out, size_t cap, size_t* n_out, 
  * PSF_ERR_INVALID_ARG.  Same conventions as psf_export. */
 int psf_export_sh(psf_table* t, psf_sh_cell_record* h_out, size_t cap, size_t* n_out, void* stream);
 
+/* ------------------------------------------------------------------------------------
+ * A session sharded across ranks (one GPU each).  Each rank pre-aggregates its share of the
+ * vertices in a scratch table and exports the touched cells' fixed-point records; the
+ * records travel to the rank that owns their key (owner = (fmix64(key) >> 32) mod ranks);
+ * the owner adds them to its table (psf_insert_records; integer sums, so the merged cells
+ * are exact under any split of the vertices), blends with psf_update, and the blended cells'
+ * approximants travel to the other ranks, which write them into their tables
+ * (psf_set_approximant) before answering their own paths' queries.  The arithmetic is that of
+ * eq. (5)-(6) and (10)-(11) on one table; only where the additions happen changes.
+ * ------------------------------------------------------------------------------------ */
+
+/* One cell's contribution of one iteration: the exported key, sums and c_new of a cell. */
+typedef struct {
+    uint64_t key;
+    int64_t sum[3];
+    int64_t c_new;
+} psf_record;
+
+/* Add n records (device array, 8-byte aligned, any order; a key may repeat) to the table's
+ * current iteration: each key's cell is found or claimed, its sums and c_new are added and
+ * it is marked touched, as if the vertices behind the records had been inserted here.  A
+ * key with bit 63 set is dropped with PSF_STATUS_RANGE; a full table sets
+ * PSF_STATUS_TABLE_FULL.  RGB payload only. */
+int psf_insert_records(psf_table* t, const psf_record* d_records, uint64_t n, void* stream);
+
+/* Write the approximant of n cells (d_keys: n uint64, d_L: n*3 float32, device arrays) into
+ * the table, finding or claiming each key's cell; counters and sums are left as they are,
+ * and the FP16 copy is rewritten when the table keeps one.  Errors as psf_insert_records. */
+int psf_set_approximant(psf_table* t, const uint64_t* d_keys, const float* d_L, uint64_t n, void* stream);
+
 /* Synchronised statistics and sticky status.  Synchronises `stream`. */
 int psf_get_stats(psf_table* t, psf_stats* out, void* stream);
 

@@ -127,6 +127,9 @@ class BatchConfig(ctypes.Structure):
 CELL_DTYPE = np.dtype([("key", "<u8"), ("sum", "<i8", (3,)), ("c_new", "<i8"), ("c_old", "<i8"),
                        ("L", "<f4", (3,)), ("L_fp16", "<u2", (3,)), ("pad", "<u2")], align=True)
 assert CELL_DTYPE.itemsize == 72
+# psf_record (40 bytes): one cell's contribution of one iteration
+RECORD_DTYPE = np.dtype([("key", "<u8"), ("sum", "<i8", (3,)), ("c_new", "<i8")])
+assert RECORD_DTYPE.itemsize == 40
 # psf_sh_cell_record (168 bytes)
 SH_CELL_DTYPE = np.dtype([("key", "<u8"), ("sum", "<i8", (16,)), ("c_old", "<i8"), ("coef", "<f4", (6,))], align=True)
 assert SH_CELL_DTYPE.itemsize == 168
@@ -147,6 +150,8 @@ SIGNATURES = {
     "psf_reset": (_i, [_vp, _vp]),
     "psf_export": (_i, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _vp]),
     "psf_export_sh": (_i, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _vp]),
+    "psf_insert_records": (_i, [_vp, _vp, _u64, _vp]),
+    "psf_set_approximant": (_i, [_vp, _vp, _vp, _u64, _vp]),
     "psf_get_stats": (_i, [_vp, ctypes.POINTER(Stats), _vp]),
     "psf_destroy": (_i, [_vp]),
     "psf_set_launch_config": (_i, [_vp, ctypes.POINTER(LaunchConfig)]),

@@ -570,6 +570,86 @@ __global__ void __launch_bounds__(kThreads) k_export_sh(TableView t, unsigned lo
     }
 }
 
+// Pre-aggregated records of other tables (a sharded session's exchange) added to this
+// table: one record per thread, the warp probing together; each record's three sums and
+// counter are added with 64-bit atomics and the cell is marked touched.  A record whose key
+// has bit 63 set is not a cell key: it is dropped with PSF_STATUS_RANGE.
+__global__ void __launch_bounds__(kThreads) k_insert_records(TableView t, const psf_record* __restrict__ r,
+                                                             unsigned long long n) {
+    __shared__ unsigned s_max_probe;
+    if (threadIdx.x == 0) s_max_probe = 0;
+    __syncthreads();
+    unsigned max_len = 0;
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+    for (unsigned long long base = static_cast<unsigned long long>(blockIdx.x) * blockDim.x; base < n; base += stride) {
+        const unsigned long long i = base + threadIdx.x;
+        psf_record rec{};
+        bool need = false;
+        if (i < n) {
+            rec = r[i];
+            need = (rec.key >> 63) == 0;
+            if (!need) {
+                atomicOr(&t.hdr->status, psf::kStatusRange);
+                atomicAdd(&t.hdr->dropped, 1ull);
+            }
+        }
+        long long slot;
+        unsigned len;
+        psf::probe_warp(t, need, rec.key, &slot, &len);
+        if (need) {
+            max_len = len > max_len ? len : max_len;
+            if (slot < 0) {
+                atomicOr(&t.hdr->status, psf::kStatusTableFull);
+                atomicAdd(&t.hdr->dropped, 1ull);
+            } else {
+                Slot* a = t.slots + slot;
+                atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[0]), static_cast<unsigned long long>(rec.sum[0]));
+                atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[1]), static_cast<unsigned long long>(rec.sum[1]));
+                atomicAdd(reinterpret_cast<unsigned long long*>(&a->s[2]), static_cast<unsigned long long>(rec.sum[2]));
+                atomicAdd(reinterpret_cast<unsigned long long*>(&a->c), static_cast<unsigned long long>(rec.c_new));
+                atomicOr(t.dirty + (slot >> 5), 1u << (slot & 31));
+            }
+        }
+    }
+    if (max_len) atomicMax(&s_max_probe, max_len);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_max_probe) atomicMax(&t.hdr->max_probe, s_max_probe);
+}
+
+// The approximant of the given cells written into this table (a sharded session's replica of
+// cells other ranks own): each key is found or claimed and its FP32 approximant (and FP16
+// copy) set; the cell's counters are left as they are.
+__global__ void __launch_bounds__(kThreads) k_set_approximant(TableView t, const unsigned long long* __restrict__ keys,
+                                                              const float* __restrict__ L, unsigned long long n) {
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+    for (unsigned long long base = static_cast<unsigned long long>(blockIdx.x) * blockDim.x; base < n; base += stride) {
+        const unsigned long long i = base + threadIdx.x;
+        const unsigned long long key = i < n ? keys[i] : 0ull;
+        const bool need = i < n && (key >> 63) == 0;
+        if (i < n && !need) {
+            atomicOr(&t.hdr->status, psf::kStatusRange);
+            atomicAdd(&t.hdr->dropped, 1ull);
+        }
+        long long slot;
+        unsigned len;
+        psf::probe_warp(t, need, key, &slot, &len);
+        if (need) {
+            if (slot < 0) {
+                atomicOr(&t.hdr->status, psf::kStatusTableFull);
+                atomicAdd(&t.hdr->dropped, 1ull);
+            } else {
+                const float x = L[3 * i], y = L[3 * i + 1], z = L[3 * i + 2];
+                float4 cur = t.slots[slot].L;
+                cur.x = x;
+                cur.y = y;
+                cur.z = z;
+                t.slots[slot].L = cur;
+                if (t.mirror) t.mirror[slot] = psf::pack_half4(x, y, z);
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_count_live(TableView t, unsigned long long* count) {
     __shared__ unsigned long long s_count;
     if (threadIdx.x == 0) s_count = 0;
@@ -938,6 +1018,25 @@ int psf_step(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, floa
     rc = psf_update(t, stream);
     if (rc < 0) return rc;
     return psf_query_cv(t, d_vertices, P, D, d_out_rgb, stream);
+}
+
+int psf_insert_records(psf_table* t, const psf_record* d_records, uint64_t n, void* stream) {
+    if (!t || t->view.payload != psf::kPayloadRGB) return PSF_ERR_INVALID_ARG;
+    if (n == 0) return PSF_OK;
+    if (!d_records || (reinterpret_cast<uintptr_t>(d_records) & 7u)) return PSF_ERR_INVALID_ARG;
+    launch_sized(t, k_insert_records, n, static_cast<cudaStream_t>(stream), t->view, d_records,
+                 static_cast<unsigned long long>(n));
+    return cuda_ok(cudaGetLastError(), "k_insert_records") ? PSF_OK : PSF_ERR_CUDA;
+}
+
+int psf_set_approximant(psf_table* t, const uint64_t* d_keys, const float* d_L, uint64_t n, void* stream) {
+    if (!t || t->view.payload != psf::kPayloadRGB) return PSF_ERR_INVALID_ARG;
+    if (n == 0) return PSF_OK;
+    if (!d_keys || !d_L || (reinterpret_cast<uintptr_t>(d_keys) & 7u) || (reinterpret_cast<uintptr_t>(d_L) & 3u))
+        return PSF_ERR_INVALID_ARG;
+    launch_sized(t, k_set_approximant, n, static_cast<cudaStream_t>(stream), t->view,
+                 reinterpret_cast<const unsigned long long*>(d_keys), d_L, static_cast<unsigned long long>(n));
+    return cuda_ok(cudaGetLastError(), "k_set_approximant") ? PSF_OK : PSF_ERR_CUDA;
 }
 
 int psf_reset(psf_table* t, void* stream) {

@@ -135,6 +135,28 @@ class Table:
                    "psf_step")
         return out
 
+    def insert_records(self, records, stream=None) -> None:
+        """Add pre-aggregated cell records (a (n, 5) int64 CUDA tensor laid out as psf_record:
+        key, three sums, c_new) to this iteration, as a sharded session's owner does."""
+        import torch
+
+        if not isinstance(records, torch.Tensor) or not records.is_cuda or records.dtype != torch.int64 or \
+                records.dim() != 2 or records.shape[1] != 5 or not records.is_contiguous():
+            raise ValueError("insert_records: records must be a contiguous (n, 5) int64 CUDA tensor")
+        _abi.check(_abi.load().psf_insert_records(self._h, records.data_ptr(), records.shape[0], _stream_handle(stream)),
+                   "psf_insert_records")
+
+    def set_approximant(self, keys, L, stream=None) -> None:
+        """Write the approximant of the given cells (keys: (n,) int64 CUDA tensor holding the
+        uint64 keys, L: (n, 3) float32 CUDA tensor)."""
+        import torch
+
+        if keys.dtype != torch.int64 or L.dtype != torch.float32 or tuple(L.shape) != (keys.shape[0], 3) or \
+                not (keys.is_cuda and L.is_cuda and keys.is_contiguous() and L.is_contiguous()):
+            raise ValueError("set_approximant: (n,) int64 keys and (n, 3) float32 values on the device")
+        _abi.check(_abi.load().psf_set_approximant(self._h, keys.data_ptr(), L.data_ptr(), keys.shape[0],
+                                                   _stream_handle(stream)), "psf_set_approximant")
+
     def reset(self, stream=None) -> None:
         _abi.check(_abi.load().psf_reset(self._h, _stream_handle(stream)), "psf_reset")
 
