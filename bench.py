@@ -766,8 +766,11 @@ def measure_sessions(args, gen: dict, local: int) -> dict:
     V = sum(s["width"] * s["height"] * s["depth"] for s in sessions)
     dev = [[torch.from_numpy(v).cuda() for v in gen["host"][k]] for k in range(len(sessions))]
 
-    def cfg_of(s):
-        return psf.make_config(log2_capacity=s["log2_capacity"], pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
+    def cfg_of(s, bits=1):
+        # the load factor: 2^(ceil(log2 V) + bits) slots (the workload's own sizing is bits = 1);
+        # the cell grid q stays the session's, so every choice gives the same cells
+        log2cap = int(math.ceil(math.log2(s["width"] * s["height"] * s["depth"]))) + bits
+        return psf.make_config(log2_capacity=log2cap, pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
                                alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"])
 
     outs = [torch.empty((d[0].shape[0], 3), device="cuda") for d in dev]
@@ -787,9 +790,11 @@ def measure_sessions(args, gen: dict, local: int) -> dict:
         else:
             table.step(v, P, D, out=outs[i])
 
-    tuned = autotune.tune_batch(lambda: entries([psf.Table(cfg_of(s)) for s in sessions], 0), len(sessions))
-    knobs = tuned["best"]
-    tables = [psf.Table(cfg_of(s)) for s in sessions]
+    tuned = autotune.tune_batch(lambda bits=1: entries([psf.Table(cfg_of(s, bits)) for s in sessions], 0),
+                                len(sessions), space={**autotune.BATCH_SPACE, "capacity_bits": (1, 2)})
+    knobs = dict(tuned["best"])
+    bits = knobs.pop("capacity_bits")
+    tables = [psf.Table(cfg_of(s, bits)) for s in sessions]
     batches = [psf.Batch(len(sessions), **knobs) for _ in range(pool)]
     for it, b in enumerate(batches):
         b.set(entries(tables, it))
@@ -818,14 +823,14 @@ def measure_sessions(args, gen: dict, local: int) -> dict:
         t_batch, per_batch = timed(lambda k: graphs[k % pool].replay(), args.warmup, args.steps)
     status = max(b.status() for b in batches)
 
-    plain_tables = [psf.Table(cfg_of(s)) for s in sessions]
+    plain_tables = [psf.Table(cfg_of(s, bits)) for s in sessions]
 
     def plain(k):
         for i, s in enumerate(sessions):
             plain_step(plain_tables[i], i, dev[i][k % pool], s["width"] * s["height"], s["depth"])
 
     t_plain, per_plain = timed(plain, args.warmup, args.steps)
-    graph_tables = [psf.Table(cfg_of(s)) for s in sessions]
+    graph_tables = [psf.Table(cfg_of(s, bits)) for s in sessions]
     plain_graphs = []
     for it in range(pool):
         g = torch.cuda.CUDAGraph()
@@ -849,7 +854,7 @@ def measure_sessions(args, gen: dict, local: int) -> dict:
         touched = st["touched_cells"] / its
         groups += st["leader_groups"] / its
         touched_all += touched
-        slot_bytes += 64 << s["log2_capacity"]
+        slot_bytes += 64 << int(plain_tables[i].cfg.log2_capacity)
         for k, b in algorithmic_bytes(s["width"] * s["height"] * s["depth"], touched, bool(s["cache_fp16"]),
                                       bool(args.slot_cache)).items():
             bytes_phase[k] += b
@@ -877,6 +882,7 @@ def measure_sessions(args, gen: dict, local: int) -> dict:
         "workload": f"{len(sessions)} sessions, width log-uniform 128..1280, 16:9, depth U{{2..6}}, FP16 cache",
         "value": rate(t_batch), "unit": UNIT, "ms_per_step": t_batch / args.steps, "vertices_per_step": V,
         "steps": args.steps, "warmup": args.warmup, "pool": pool, "batch_knobs": knobs,
+        "capacity": f"2^(ceil(log2 V) + {bits}) slots per session (autotuned load factor)",
         "slot_cache": bool(args.slot_cache),
         "l2": f"inputs larger than L2: {pool} distinct iterations of {V * 64 / 1e9:.1f} GB",
         "latency_ms": {"p50": float(np.percentile(per_batch, 50)), "p99": float(np.percentile(per_batch, 99))},
@@ -1002,7 +1008,8 @@ def run_serving(args) -> None:
     reqs = [src.fit(r) for r in reqs]
     reports = {}
     for mode in ("batched", "plain"):
-        srv = Server(src, budget_bytes=args.budget_gb * 1e9, mode=mode, slot_cache=bool(args.slot_cache))
+        srv = Server(src, budget_bytes=args.budget_gb * 1e9, mode=mode, slot_cache=bool(args.slot_cache),
+                     capacity_bits=args.capacity_bits)
         with ClockSampler(local) as clocks:
             rep = srv.run(reqs, args.duration)
         rep["clocks"] = clocks.summary()
@@ -1047,6 +1054,8 @@ def main(argv=None) -> None:
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=60.0, help="serving: device memory for tables")
+    ap.add_argument("--capacity-bits", type=int, default=1,
+                    help="serving: tables of 2^(ceil(log2 V) + bits) slots (the load factor the batched tuner picks)")
     ap.add_argument("--payload", default="rgb", choices=["rgb", "sh"],
                     help="cell payload: RGB, or YCoCg with luminance in two SH bands over the normal")
     ap.add_argument("--sh-ridge", type=float, default=0.01, help="SH payload: ridge on band 1")

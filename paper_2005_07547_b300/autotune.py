@@ -3,11 +3,20 @@
 Every knob changes only the order of the integer additions (or the table's slot
 layout), never a result, so candidates are timed on scratch tables fed the caller's
 own device-resident vertex batches and the fastest is returned.  Timing uses CUDA
-events on the current stream after warm-up iterations.
+events on the current stream after warm-up iterations.  With verify=True the tuner also
+checks that premise: every candidate has run the same iterations, and its tables' cell
+maps (exported in key order) must be identical, bit for bit.
 
-  tune_table(cfg, batches, P, D)   -> insert mode and per-kernel grid caps for psf_step
+  tune_table(cfg, batches, P, D)   -> insert mode, vertex staging, sum path and per-kernel
+                                      grid caps for psf_step
   tune_capacity(cfg, batches, P, D)-> log2 capacity (load factor) for a session size
-  tune_batch(entries_fn)           -> insert mode and blocks/SM for the batched kernel
+  tune_batch(make_entries, n)      -> insert mode, blocks/SM and, when the space holds
+                                      "capacity_bits", the sessions' load factor
+                                      (2^(ceil(log2 V) + bits) slots) for the batched kernel
+
+The probe window is not a knob: every probe visits one slot per step.  Windows of two and
+four consecutive slots per step were measured on the B300 (1280x720, depth 4: 117 and
+143 us against 112 us for the insert) and lost to the extra loads and registers.
 """
 
 from __future__ import annotations
@@ -52,14 +61,34 @@ def _clone_config(cfg: _abi.Config, **over) -> _abi.Config:
     return c
 
 
+class _Same:
+    """Holds the first candidate's exported tables and checks every later one against them."""
+
+    def __init__(self, enabled: bool):
+        self.enabled = enabled
+        self.ref = None
+        self.checked = 0
+
+    def __call__(self, tables, knobs) -> None:
+        if not self.enabled:
+            return
+        got = [t.export().tobytes() for t in tables]
+        if self.ref is None:
+            self.ref = got
+        elif got != self.ref:
+            raise AssertionError(f"autotune: candidate {knobs} changed the tables")
+        self.checked += 1
+
+
 def tune_table(cfg: _abi.Config, batches, P: int, D: int, space: dict | None = None, warmup: int = 2,
-               iters: int = 4) -> dict:
+               iters: int = 4, verify: bool = False) -> dict:
     """Fastest psf_step launch knobs for this configuration and input (list of (P*D, 16) tensors)."""
     import torch
 
     space = space or TABLE_SPACE
     out = torch.empty((P * D, 3), dtype=torch.float32, device=batches[0].device)
     results = []
+    same = _Same(verify)
     keys = list(space)
     for values in itertools.product(*(space[k] for k in keys)):
         knobs = dict(zip(keys, values))
@@ -68,14 +97,16 @@ def tune_table(cfg: _abi.Config, batches, P: int, D: int, space: dict | None = N
         for k in range(warmup):
             t.step(batches[k % len(batches)], P, D, out=out)
         ms = _time_ms(lambda k: t.step(batches[(warmup + k) % len(batches)], P, D, out=out), iters)
+        same([t], knobs)
         t.close()
         results.append((ms, knobs))
     results.sort(key=lambda r: r[0])
-    return {"best": results[0][1], "best_ms": results[0][0], "all": [{"ms": ms, **k} for ms, k in results]}
+    return {"best": results[0][1], "best_ms": results[0][0], "all": [{"ms": ms, **k} for ms, k in results],
+            "verified": same.checked}
 
 
 def tune_capacity(cfg: _abi.Config, batches, P: int, D: int, extra_bits=(1, 2), warmup: int = 2,
-                  iters: int = 4) -> dict:
+                  iters: int = 4, verify: bool = False) -> dict:
     """Load factor: capacity 2^(ceil(log2 V) + e) for each e, timed; returns the fastest
     and its table bytes (more slots cost memory, fewer cost longer probes)."""
     import torch
@@ -83,6 +114,7 @@ def tune_capacity(cfg: _abi.Config, batches, P: int, D: int, extra_bits=(1, 2), 
     V = P * D
     out = torch.empty((V, 3), dtype=torch.float32, device=batches[0].device)
     res = []
+    same = _Same(verify)
     for e in extra_bits:
         log2cap = max(4, int(math.ceil(math.log2(max(V, 2)))) + e)
         c = _clone_config(cfg, log2_capacity=log2cap)
@@ -91,20 +123,26 @@ def tune_capacity(cfg: _abi.Config, batches, P: int, D: int, extra_bits=(1, 2), 
             t.step(batches[k % len(batches)], P, D, out=out)
         ms = _time_ms(lambda k: t.step(batches[(warmup + k) % len(batches)], P, D, out=out), iters)
         res.append({"log2_capacity": log2cap, "ms": ms, "table_bytes": t.nbytes, "max_probe": t.stats()["max_probe"]})
+        same([t], {"log2_capacity": log2cap})
         t.close()
     best = min(res, key=lambda r: r["ms"])
-    return {"best": best["log2_capacity"], "all": res}
+    return {"best": best["log2_capacity"], "all": res, "verified": same.checked}
 
 
-def tune_batch(make_entries, n_items: int, space: dict | None = None, warmup: int = 2, iters: int = 3) -> dict:
-    """Fastest batched-kernel knobs.  make_entries() must return fresh (table, vertices, out, P, D)
-    entries (scratch tables) for each candidate."""
+def tune_batch(make_entries, n_items: int, space: dict | None = None, warmup: int = 2, iters: int = 3,
+               verify: bool = False) -> dict:
+    """Fastest batched-kernel knobs.  make_entries() must return fresh (table, vertices, out, P, D
+    [, slots]) entries (scratch tables) for each candidate; when the space holds
+    "capacity_bits", make_entries(capacity_bits) sizes each session's table at
+    2^(ceil(log2 V) + capacity_bits) slots."""
     space = space or BATCH_SPACE
     keys = list(space)
     results = []
+    same = _Same(verify)
     for values in itertools.product(*(space[k] for k in keys)):
         knobs = dict(zip(keys, values))
-        entries = make_entries()
+        bits = knobs.pop("capacity_bits", None)
+        entries = make_entries(bits) if bits is not None else make_entries()
         b = Batch(n_items, **knobs)
         b.set(entries)
         for _ in range(warmup):
@@ -112,9 +150,13 @@ def tune_batch(make_entries, n_items: int, space: dict | None = None, warmup: in
         ms = _time_ms(lambda k: b.launch(), iters)
         if b.status() != 0:
             ms = float("inf")
+        if bits is not None:
+            knobs["capacity_bits"] = bits
+        same([e[0] for e in entries], knobs)
         b.close()
         for e in entries:
             e[0].close()
         results.append((ms, knobs))
     results.sort(key=lambda r: r[0])
-    return {"best": results[0][1], "best_ms": results[0][0], "all": [{"ms": ms, **k} for ms, k in results]}
+    return {"best": results[0][1], "best_ms": results[0][0], "all": [{"ms": ms, **k} for ms, k in results],
+            "verified": same.checked}
