@@ -403,7 +403,11 @@ int psf_batch_destroy(psf_batch* b);
  *     cleared at the start of each call, the descriptors overwritten.  Calls whose work
  *     could overlap on the GPU (different streams without ordering between them) race on
  *     it; order them on one stream or with events.
- *   - A barrier that gives up sets PSF_STATUS_TIMEOUT in every item's table. */
+ *   - A barrier that gives up sets PSF_STATUS_TIMEOUT in every item's table.
+ *   - The descriptors are built in a thread-local host buffer and copied from that pageable
+ *     memory; to stage such a copy CUDA may wait for earlier work on the stream, so a call
+ *     can block the host until that work has finished (psf_batch_set copies from pinned
+ *     memory and does not). */
 #define PSF_NOALLOC_MAX_ITEMS 64u
 int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, const psf_batch_config* cfg, void* stream);
 

@@ -69,10 +69,14 @@ def check_estimator(out_gpu, out_ref, verts, C_ref, P, D, a, b, c, j_begin, j_en
     fl = _floor(ref_L_all)
     bound = tol * (np.where(on, abs(a), 1.0) * np.abs(L)
                    + on * (abs(b) * np.abs(t) * (np.abs(C_next.reshape(-1, 3)) + fl) + abs(c) * (np.abs(C_ref) + fl)))
-    # non-finite inputs propagate identically on both sides
+    # non-finite inputs propagate identically on both sides: NaN where the oracle has NaN, and
+    # the same signed infinity where it has one
     assert np.array_equal(np.isnan(out_gpu), np.isnan(out_ref))
+    assert np.array_equal(np.isinf(out_gpu), np.isinf(out_ref))
+    inf = np.isinf(out_ref)
+    assert np.array_equal(out_gpu[inf], out_ref[inf])
     err = np.abs(out_gpu - out_ref)
-    err[np.isnan(out_ref)] = 0.0
+    err[np.isnan(out_ref) | inf] = 0.0
     bad = err > bound
     assert not np.any(bad), (np.argwhere(bad)[:5], out_gpu[bad][:5], out_ref[bad][:5])
     # vertices without an estimator are copied exactly
