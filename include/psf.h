@@ -307,7 +307,8 @@ int psf_destroy(psf_table* t);
 
 /* Launch knobs of a table's kernels (the autotuner's search space).  Results do not
  * depend on them: the integer sums are order-independent.  psf_create starts from
- * {0, 0, 0, 0, 0, 0} (warp merge, occupancy-limited grids, direct vertex loads, bulk sums);
+ * {0, 0, 0, 0, 0, 0, 0} (warp merge, occupancy-limited grids, direct vertex loads, bulk sums,
+ * depth-split queries);
  * a zero grid cap means the occupancy limit.  A batch (psf_batch_set) copies each table's
  * sum_reduction when its descriptors are set. */
 typedef struct {
@@ -323,6 +324,11 @@ typedef struct {
     uint32_t sum_reduction;        /* how an insert adds a group's three sums and counter to its cell:
                                       0 = one 32-byte bulk reduction from shared memory (TMA),
                                       1 = four 64-bit atomic reductions */
+    uint32_t query_layout;         /* how the queries map vertices to threads: 0 = split by depth, one
+                                      thread per vertex of a tile of 256 / D paths at all D depths,
+                                      C_{j+1} passed through shared memory (when D <= 256); 1 = one
+                                      thread per path, its vertices walked last to first (also the
+                                      staged query of vertex_staging bit 1) */
 } psf_launch_config;
 
 /* Set / read the launch knobs of a table (host-side only; affects later calls). */

@@ -96,6 +96,7 @@ class LaunchConfig(ctypes.Structure):
         ("query_blocks_per_sm", ctypes.c_uint32),
         ("vertex_staging", ctypes.c_uint32),
         ("sum_reduction", ctypes.c_uint32),
+        ("query_layout", ctypes.c_uint32),
     ]
 
 

@@ -36,6 +36,7 @@ TABLE_SPACE = {
     "insert_blocks_per_sm": (0, 4, 2),
     "query_blocks_per_sm": (0, 4),
     "update_blocks_per_sm": (0, 2),
+    "query_layout": (0, 1),
 }
 BATCH_SPACE = {"insert_mode": (0, 1), "blocks_per_sm": (0, 3, 2)}
 

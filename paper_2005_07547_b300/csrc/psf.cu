@@ -500,6 +500,69 @@ __global__ void __launch_bounds__(kThreads) k_query(TableView t, psf::Estimator 
         psf::query_path<kSlots, kSH>(t, e, v, P, D, p, out, slots);
 }
 
+// The query split by depth: a block takes a tile of T = 256 / D paths at all D depths, one
+// thread per vertex (thread k: depth k / T, path p0 + k % T), so every vertex's record, slot
+// and approximant loads are in flight at once instead of one dependent chain per path.  Each
+// thread's C_j goes through shared memory to the thread of vertex j - 1 of the same path,
+// which combines it as C_{j+1}.  Requires D <= 256.
+template <bool kSlots, bool kSH>
+__global__ void __launch_bounds__(kThreads) k_query_tiled(TableView t, psf::Estimator e, const float4* __restrict__ v,
+                                                          unsigned P, unsigned D, float* __restrict__ out,
+                                                          const unsigned* __restrict__ slots) {
+    __shared__ float s_c[3][kThreads];
+    const unsigned T = kThreads / D;
+    const unsigned j = threadIdx.x / T, q = threadIdx.x - j * T;
+    const unsigned long long ntiles = (static_cast<unsigned long long>(P) + T - 1) / T;
+    for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const unsigned long long p = tile * T + q;
+        const bool act = j < D && p < P;
+        float3 c = make_float3(0.0f, 0.0f, 0.0f);
+        float4 v1 = make_float4(0, 0, 0, 0), v2 = v1, v3 = v1;
+        unsigned long long i = 0;
+        if (act) {
+            i = static_cast<unsigned long long>(j) * P + p;
+            const float4* r = v + 4 * i;  // streamed once: evict-first
+            if constexpr (kSlots) {
+                const unsigned sl = __ldcs(slots + i);
+                v1 = __ldcs(r + 1);
+                v2 = __ldcs(r + 2);
+                v3 = __ldcs(r + 3);
+                if (sl != psf::kNoSlot)
+                    c = psf::value_at(t, sl);
+                else
+                    c = psf::cell_value(t, __ldcs(r), v1, v2, false, psf::read_level(t, j));
+            } else {
+                const float4 v0 = __ldcs(r);
+                v1 = __ldcs(r + 1);
+                v2 = __ldcs(r + 2);
+                v3 = __ldcs(r + 3);
+                if constexpr (kSH)
+                    c = psf::cell_value_sh(t, v0, v1, v2);
+                else
+                    c = psf::cell_value(t, v0, v1, v2, false, psf::read_level(t, j));
+            }
+        }
+        s_c[0][threadIdx.x] = c.x;
+        s_c[1][threadIdx.x] = c.y;
+        s_c[2][threadIdx.x] = c.z;
+        __syncthreads();
+        if (act) {
+            float o0 = v3.x, o1 = v3.y, o2 = v3.z;
+            if (j + 1 < D && j >= e.j_begin && j < e.j_end) {
+                const unsigned nb = threadIdx.x + T;  // vertex j + 1 of the same path
+                o0 = psf::combine(e, v3.x, v1.w, s_c[0][nb], c.x);
+                o1 = psf::combine(e, v3.y, v2.w, s_c[1][nb], c.y);
+                o2 = psf::combine(e, v3.z, v3.w, s_c[2][nb], c.z);
+            }
+            float* o = out + 3 * i;
+            o[0] = o0;
+            o[1] = o1;
+            o[2] = o2;
+        }
+        __syncthreads();  // the tile's values are read before the next tile overwrites them
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_export(TableView t, unsigned long long s0, unsigned long long s1,
                                                      psf_cell_record* out, unsigned* count) {
     const unsigned lane = threadIdx.x & 31u;
@@ -738,6 +801,18 @@ void launch_insert_slots(const psf_table* t, const float4* v, uint32_t P, uint32
         launch_sized(t, k_insert<psf::kAggWarp, kHier, true>, n, st, t->view, v, n, P, slots);
 }
 
+// The depth-split query: one tile of 256 / D paths per block iteration, grid-stride over the
+// tiles, sized by the kernel's own resident-block count.
+template <bool kSlots, bool kSH>
+void launch_tiled_query(const psf_table* t, const psf::Estimator& e, const float4* v, uint32_t P, uint32_t D, float* out,
+                        const unsigned* slots, cudaStream_t st) {
+    const unsigned T = kThreads / D;
+    const unsigned long long tiles = (static_cast<unsigned long long>(P) + T - 1) / T;
+    const int grid = grid_for(t, resident_blocks(t, reinterpret_cast<const void*>(k_query_tiled<kSlots, kSH>)),
+                              tiles * kThreads, t->launch.query_blocks_per_sm);
+    k_query_tiled<kSlots, kSH><<<grid, kThreads, 0, st>>>(t->view, e, v, P, D, out, slots);
+}
+
 template <bool kHier>
 void launch_insert_progressive(const psf_table* t, const float4* v, uint32_t P, uint32_t D, uint32_t field,
                                cudaStream_t st) {
@@ -845,7 +920,7 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     *t->h_status = 0;
     // direct vertex loads (measured: with bulk sums the TMA-staged tiles are slower, 133 vs
     // 120 us on 1280x720x4, as both go through the TMA unit), bulk sums
-    t->launch = psf_launch_config{0u, 0u, 0u, 0u, 0u, 0u};
+    t->launch = psf_launch_config{0u, 0u, 0u, 0u, 0u, 0u, 0u};
     t->view.sum_path = psf::kSumsBulk;
     char* base = static_cast<char*>(d_mem);
     TableView& v = t->view;
@@ -953,7 +1028,12 @@ int launch_query(psf_table* t, const psf::Estimator& e, const float* d_vertices,
         return PSF_ERR_INVALID_ARG;
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->view.payload == psf::kPayloadSH) {
+    if (t->launch.query_layout == 0 && D <= kThreads) {
+        if (t->view.payload == psf::kPayloadSH)
+            launch_tiled_query<false, true>(t, e, v, P, D, d_out_rgb, nullptr, st);
+        else
+            launch_tiled_query<false, false>(t, e, v, P, D, d_out_rgb, nullptr, st);
+    } else if (t->view.payload == psf::kPayloadSH) {
         const int grid = grid_for(t, resident_blocks(t, reinterpret_cast<const void*>(k_query<false, true>)), P,
                                   t->launch.query_blocks_per_sm);
         k_query<false, true><<<grid, kThreads, 0, st>>>(t->view, e, v, P, D, d_out_rgb);
@@ -1006,9 +1086,13 @@ int psf_query_cv_slots(psf_table* t, const float* d_vertices, const uint32_t* d_
         return PSF_ERR_INVALID_ARG;
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int grid = grid_for(t, resident_blocks(t, reinterpret_cast<const void*>(k_query<true>)), P,
-                              t->launch.query_blocks_per_sm);
-    k_query<true><<<grid, kThreads, 0, st>>>(t->view, psf::cv_estimator(t->view), v, P, D, d_out_rgb, d_slots);
+    if (t->launch.query_layout == 0 && D <= kThreads) {
+        launch_tiled_query<true, false>(t, psf::cv_estimator(t->view), v, P, D, d_out_rgb, d_slots, st);
+    } else {
+        const int grid = grid_for(t, resident_blocks(t, reinterpret_cast<const void*>(k_query<true>)), P,
+                                  t->launch.query_blocks_per_sm);
+        k_query<true><<<grid, kThreads, 0, st>>>(t->view, psf::cv_estimator(t->view), v, P, D, d_out_rgb, d_slots);
+    }
     return cuda_ok(cudaGetLastError(), "k_query") ? PSF_OK : PSF_ERR_CUDA;
 }
 
@@ -1047,7 +1131,8 @@ int psf_reset(psf_table* t, void* stream) {
 }
 
 int psf_set_launch_config(psf_table* t, const psf_launch_config* c) {
-    if (!t || !c || c->insert_mode > 1 || c->vertex_staging > 3 || c->sum_reduction > 1) return PSF_ERR_INVALID_ARG;
+    if (!t || !c || c->insert_mode > 1 || c->vertex_staging > 3 || c->sum_reduction > 1 || c->query_layout > 1)
+        return PSF_ERR_INVALID_ARG;
     t->launch = *c;
     t->view.sum_path = c->sum_reduction;
     return PSF_OK;

@@ -184,9 +184,10 @@ class Table:
         return st.as_dict()
 
     def set_launch(self, insert_mode: int = 0, insert_blocks_per_sm: int = 0, update_blocks_per_sm: int = 0,
-                   query_blocks_per_sm: int = 0, vertex_staging: int = 0, sum_reduction: int = 0) -> None:
+                   query_blocks_per_sm: int = 0, vertex_staging: int = 0, sum_reduction: int = 0,
+                   query_layout: int = 0) -> None:
         lc = _abi.LaunchConfig(insert_mode, insert_blocks_per_sm, update_blocks_per_sm, query_blocks_per_sm,
-                               vertex_staging, sum_reduction)
+                               vertex_staging, sum_reduction, query_layout)
         _abi.check(_abi.load().psf_set_launch_config(self._h, ctypes.byref(lc)), "psf_set_launch_config")
 
     def get_launch(self) -> dict:

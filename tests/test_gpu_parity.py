@@ -220,7 +220,9 @@ def test_deterministic_tables_and_outputs(psf_mod):
                                                               query_blocks_per_sm=1),
                                    dict(insert_mode=1, insert_blocks_per_sm=2), dict(vertex_staging=3),
                                    dict(sum_reduction=1), dict(sum_reduction=1, insert_mode=1, vertex_staging=0),
-                                   dict(vertex_staging=3, insert_mode=1, insert_blocks_per_sm=1, query_blocks_per_sm=1)])
+                                   dict(vertex_staging=3, insert_mode=1, insert_blocks_per_sm=1, query_blocks_per_sm=1),
+                                   dict(query_layout=1), dict(query_layout=1, vertex_staging=2),
+                                   dict(query_layout=0, query_blocks_per_sm=1)])
 def test_launch_knobs_do_not_change_results(psf_mod, knobs):
     """Aggregation mode and grid shape change only the order of the integer additions."""
     import torch
@@ -301,7 +303,8 @@ def test_progressive_insert(psf_mod, oracle_mod, field, fp16):
     table.close()
 
 
-@pytest.mark.parametrize("P,D", [(1, 1), (255, 2), (257, 3), (4103, 2), (70001, 1), (33, 6)])
+@pytest.mark.parametrize("P,D", [(1, 1), (255, 2), (257, 3), (4103, 2), (70001, 1), (33, 6), (3, 257), (2, 256),
+                                 (1000, 7)])
 def test_staged_vertex_tiles_with_ragged_tails(psf_mod, P, D):
     """Bulk-copied vertex tiles (256 records) give the same tables and outputs as direct
     loads, including partial last tiles of every depth row."""
@@ -314,7 +317,7 @@ def test_staged_vertex_tiles_with_ragged_tails(psf_mod, P, D):
     res = []
     for staging in (0, 3):
         t = psf_mod.Table(cfg)
-        t.set_launch(vertex_staging=staging)
+        t.set_launch(vertex_staging=staging, query_layout=1 if staging else 0)  # the staged query walks paths
         outs = [t.step(dv, P, D).cpu().numpy() for _ in range(2)]
         outs.append(t.query_biased(dv, P, D, 0.5).cpu().numpy())
         res.append((t.export().tobytes(), np.concatenate(outs).tobytes(), t.stats()["status"]))
