@@ -325,10 +325,10 @@ typedef struct {
                                       0 = one 32-byte bulk reduction from shared memory (TMA),
                                       1 = four 64-bit atomic reductions */
     uint32_t query_layout;         /* how the queries map vertices to threads: 0 = split by depth, one
-                                      thread per vertex of a tile of 256 / D paths at all D depths,
-                                      C_{j+1} passed through shared memory (when D <= 256); 1 = one
-                                      thread per path, its vertices walked last to first (also the
-                                      staged query of vertex_staging bit 1) */
+                                      lane per vertex of a warp tile of 32 / D paths at all D depths,
+                                      C_{j+1} passed by a warp shuffle (when D <= 32, else as 1);
+                                      1 = one thread per path, its vertices walked last to first
+                                      (also the staged query of vertex_staging bit 1) */
 } psf_launch_config;
 
 /* Set / read the launch knobs of a table (host-side only; affects later calls). */

@@ -500,20 +500,21 @@ __global__ void __launch_bounds__(kThreads) k_query(TableView t, psf::Estimator 
         psf::query_path<kSlots, kSH>(t, e, v, P, D, p, out, slots);
 }
 
-// The query split by depth: a block takes a tile of T = 256 / D paths at all D depths, one
-// thread per vertex (thread k: depth k / T, path p0 + k % T), so every vertex's record, slot
-// and approximant loads are in flight at once instead of one dependent chain per path.  Each
-// thread's C_j goes through shared memory to the thread of vertex j - 1 of the same path,
-// which combines it as C_{j+1}.  Requires D <= 256.
+// The query split by depth: a warp takes a tile of T = 32 / D paths at all D depths, one lane
+// per vertex (lane k: depth k / T, path p0 + k % T), so every vertex's record, slot and
+// approximant loads are in flight at once instead of one dependent chain per path.  Lane k
+// receives C_{j+1} of its path from lane k + T with one shuffle.  Requires D <= 32.
 template <bool kSlots, bool kSH>
 __global__ void __launch_bounds__(kThreads) k_query_tiled(TableView t, psf::Estimator e, const float4* __restrict__ v,
                                                           unsigned P, unsigned D, float* __restrict__ out,
                                                           const unsigned* __restrict__ slots) {
-    __shared__ float s_c[3][kThreads];
-    const unsigned T = kThreads / D;
-    const unsigned j = threadIdx.x / T, q = threadIdx.x - j * T;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned T = 32u / D;
+    const unsigned j = lane / T, q = lane - j * T;
     const unsigned long long ntiles = (static_cast<unsigned long long>(P) + T - 1) / T;
-    for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const unsigned long long warp = (static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = (static_cast<unsigned long long>(gridDim.x) * blockDim.x) >> 5;
+    for (unsigned long long tile = warp; tile < ntiles; tile += nwarps) {
         const unsigned long long p = tile * T + q;
         const bool act = j < D && p < P;
         float3 c = make_float3(0.0f, 0.0f, 0.0f);
@@ -542,24 +543,24 @@ __global__ void __launch_bounds__(kThreads) k_query_tiled(TableView t, psf::Esti
                     c = psf::cell_value(t, v0, v1, v2, false, psf::read_level(t, j));
             }
         }
-        s_c[0][threadIdx.x] = c.x;
-        s_c[1][threadIdx.x] = c.y;
-        s_c[2][threadIdx.x] = c.z;
-        __syncthreads();
+        // vertex j + 1 of the same path is lane + T (a lane past the warp reads its own value,
+        // which no active lane uses)
+        const unsigned src = lane + T < 32u ? lane + T : lane;
+        const float n0 = __shfl_sync(psf::kFull, c.x, src);
+        const float n1 = __shfl_sync(psf::kFull, c.y, src);
+        const float n2 = __shfl_sync(psf::kFull, c.z, src);
         if (act) {
             float o0 = v3.x, o1 = v3.y, o2 = v3.z;
             if (j + 1 < D && j >= e.j_begin && j < e.j_end) {
-                const unsigned nb = threadIdx.x + T;  // vertex j + 1 of the same path
-                o0 = psf::combine(e, v3.x, v1.w, s_c[0][nb], c.x);
-                o1 = psf::combine(e, v3.y, v2.w, s_c[1][nb], c.y);
-                o2 = psf::combine(e, v3.z, v3.w, s_c[2][nb], c.z);
+                o0 = psf::combine(e, v3.x, v1.w, n0, c.x);
+                o1 = psf::combine(e, v3.y, v2.w, n1, c.y);
+                o2 = psf::combine(e, v3.z, v3.w, n2, c.z);
             }
             float* o = out + 3 * i;
             o[0] = o0;
             o[1] = o1;
             o[2] = o2;
         }
-        __syncthreads();  // the tile's values are read before the next tile overwrites them
     }
 }
 
@@ -801,15 +802,15 @@ void launch_insert_slots(const psf_table* t, const float4* v, uint32_t P, uint32
         launch_sized(t, k_insert<psf::kAggWarp, kHier, true>, n, st, t->view, v, n, P, slots);
 }
 
-// The depth-split query: one tile of 256 / D paths per block iteration, grid-stride over the
-// tiles, sized by the kernel's own resident-block count.
+// The depth-split query: one warp per tile of 32 / D paths, grid-stride over the tiles, sized
+// by the kernel's own resident-block count.
 template <bool kSlots, bool kSH>
 void launch_tiled_query(const psf_table* t, const psf::Estimator& e, const float4* v, uint32_t P, uint32_t D, float* out,
                         const unsigned* slots, cudaStream_t st) {
-    const unsigned T = kThreads / D;
+    const unsigned T = 32u / D;
     const unsigned long long tiles = (static_cast<unsigned long long>(P) + T - 1) / T;
     const int grid = grid_for(t, resident_blocks(t, reinterpret_cast<const void*>(k_query_tiled<kSlots, kSH>)),
-                              tiles * kThreads, t->launch.query_blocks_per_sm);
+                              tiles * 32ull, t->launch.query_blocks_per_sm);
     k_query_tiled<kSlots, kSH><<<grid, kThreads, 0, st>>>(t->view, e, v, P, D, out, slots);
 }
 
@@ -1028,7 +1029,7 @@ int launch_query(psf_table* t, const psf::Estimator& e, const float* d_vertices,
         return PSF_ERR_INVALID_ARG;
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->launch.query_layout == 0 && D <= kThreads) {
+    if (t->launch.query_layout == 0 && D <= 32u) {
         if (t->view.payload == psf::kPayloadSH)
             launch_tiled_query<false, true>(t, e, v, P, D, d_out_rgb, nullptr, st);
         else
@@ -1086,7 +1087,7 @@ int psf_query_cv_slots(psf_table* t, const float* d_vertices, const uint32_t* d_
         return PSF_ERR_INVALID_ARG;
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->launch.query_layout == 0 && D <= kThreads) {
+    if (t->launch.query_layout == 0 && D <= 32u) {
         launch_tiled_query<true, false>(t, psf::cv_estimator(t->view), v, P, D, d_out_rgb, d_slots, st);
     } else {
         const int grid = grid_for(t, resident_blocks(t, reinterpret_cast<const void*>(k_query<true>)), P,

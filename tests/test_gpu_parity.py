@@ -303,8 +303,8 @@ def test_progressive_insert(psf_mod, oracle_mod, field, fp16):
     table.close()
 
 
-@pytest.mark.parametrize("P,D", [(1, 1), (255, 2), (257, 3), (4103, 2), (70001, 1), (33, 6), (3, 257), (2, 256),
-                                 (1000, 7)])
+@pytest.mark.parametrize("P,D", [(1, 1), (255, 2), (257, 3), (4103, 2), (70001, 1), (33, 6), (3, 33), (2, 32),
+                                 (1000, 7), (77, 17)])
 def test_staged_vertex_tiles_with_ragged_tails(psf_mod, P, D):
     """Bulk-copied vertex tiles (256 records) give the same tables and outputs as direct
     loads, including partial last tiles of every depth row."""
