@@ -500,68 +500,17 @@ __global__ void __launch_bounds__(kThreads) k_query(TableView t, psf::Estimator 
         psf::query_path<kSlots, kSH>(t, e, v, P, D, p, out, slots);
 }
 
-// The query split by depth: a warp takes a tile of T = 32 / D paths at all D depths, one lane
-// per vertex (lane k: depth k / T, path p0 + k % T), so every vertex's record, slot and
-// approximant loads are in flight at once instead of one dependent chain per path.  Lane k
-// receives C_{j+1} of its path from lane k + T with one shuffle.  Requires D <= 32.
+// The query split by depth (psf::query_tile): one warp per tile of 32 / D paths, grid-stride
+// over the tiles.  Requires D <= 32.
 template <bool kSlots, bool kSH>
 __global__ void __launch_bounds__(kThreads) k_query_tiled(TableView t, psf::Estimator e, const float4* __restrict__ v,
                                                           unsigned P, unsigned D, float* __restrict__ out,
                                                           const unsigned* __restrict__ slots) {
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned T = 32u / D;
-    const unsigned j = lane / T, q = lane - j * T;
-    const unsigned long long ntiles = (static_cast<unsigned long long>(P) + T - 1) / T;
+    const unsigned long long ntiles = psf::query_tiles(P, D);
     const unsigned long long warp = (static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nwarps = (static_cast<unsigned long long>(gridDim.x) * blockDim.x) >> 5;
-    for (unsigned long long tile = warp; tile < ntiles; tile += nwarps) {
-        const unsigned long long p = tile * T + q;
-        const bool act = j < D && p < P;
-        float3 c = make_float3(0.0f, 0.0f, 0.0f);
-        float4 v1 = make_float4(0, 0, 0, 0), v2 = v1, v3 = v1;
-        unsigned long long i = 0;
-        if (act) {
-            i = static_cast<unsigned long long>(j) * P + p;
-            const float4* r = v + 4 * i;  // streamed once: evict-first
-            if constexpr (kSlots) {
-                const unsigned sl = __ldcs(slots + i);
-                v1 = __ldcs(r + 1);
-                v2 = __ldcs(r + 2);
-                v3 = __ldcs(r + 3);
-                if (sl != psf::kNoSlot)
-                    c = psf::value_at(t, sl);
-                else
-                    c = psf::cell_value(t, __ldcs(r), v1, v2, false, psf::read_level(t, j));
-            } else {
-                const float4 v0 = __ldcs(r);
-                v1 = __ldcs(r + 1);
-                v2 = __ldcs(r + 2);
-                v3 = __ldcs(r + 3);
-                if constexpr (kSH)
-                    c = psf::cell_value_sh(t, v0, v1, v2);
-                else
-                    c = psf::cell_value(t, v0, v1, v2, false, psf::read_level(t, j));
-            }
-        }
-        // vertex j + 1 of the same path is lane + T (a lane past the warp reads its own value,
-        // which no active lane uses)
-        const unsigned src = lane + T < 32u ? lane + T : lane;
-        const float n0 = __shfl_sync(psf::kFull, c.x, src);
-        const float n1 = __shfl_sync(psf::kFull, c.y, src);
-        const float n2 = __shfl_sync(psf::kFull, c.z, src);
-        if (act) {
-            float o0 = v3.x, o1 = v3.y, o2 = v3.z;
-            if (j + 1 < D && j >= e.j_begin && j < e.j_end) {
-                o0 = psf::combine(e, v3.x, v1.w, n0, c.x);
-                o1 = psf::combine(e, v3.y, v2.w, n1, c.y);
-                o2 = psf::combine(e, v3.z, v3.w, n2, c.z);
-            }
-            float* o = out + 3 * i;
-            o[0] = o0;
-            o[1] = o1;
-            o[2] = o2;
-        }
-    }
+    for (unsigned long long tile = warp; tile < ntiles; tile += nwarps)
+        psf::query_tile<kSlots, kSH>(t, e, v, P, D, tile, out, slots);
 }
 
 __global__ void __launch_bounds__(kThreads) k_export(TableView t, unsigned long long s0, unsigned long long s1,

@@ -1049,4 +1049,67 @@ __device__ __forceinline__ void query_path(const TableView& t, const Estimator& 
     }
 }
 
+// The query split by depth: a warp takes tile `tile` of T = 32 / D paths at all D depths, one
+// lane per vertex (lane k: depth k / T, path tile * T + k % T), so every vertex's record, slot
+// and approximant loads are in flight at once instead of one dependent chain per path.  Lane
+// k receives C_{j+1} of its path from lane k + T with one shuffle.  The whole warp calls it;
+// requires 1 <= D <= 32.  With kSlots a vertex whose slot the insert noted reads the
+// approximant there; kSH reads the SH payload's fit at the vertex's normal.
+__host__ __device__ __forceinline__ unsigned long long query_tiles(unsigned P, unsigned D) {
+    const unsigned T = 32u / D;
+    return (static_cast<unsigned long long>(P) + T - 1) / T;
+}
+
+template <bool kSlots, bool kSH = false>
+__device__ __forceinline__ void query_tile(const TableView& t, const Estimator& e, const float4* __restrict__ v,
+                                           unsigned P, unsigned D, unsigned long long tile, float* __restrict__ out,
+                                           const unsigned* __restrict__ slots) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned T = 32u / D;
+    const unsigned j = lane / T, q = lane - j * T;
+    const unsigned long long p = tile * T + q;
+    const bool act = j < D && p < P;
+    float3 c = make_float3(0.0f, 0.0f, 0.0f);
+    float4 v1 = make_float4(0, 0, 0, 0), v2 = v1, v3 = v1;
+    unsigned long long i = 0;
+    if (act) {
+        i = static_cast<unsigned long long>(j) * P + p;
+        const float4* r = v + 4 * i;  // streamed once: evict-first
+        if constexpr (kSlots) {
+            const unsigned sl = __ldcs(slots + i);
+            v1 = __ldcs(r + 1);
+            v2 = __ldcs(r + 2);
+            v3 = __ldcs(r + 3);
+            c = sl != kNoSlot ? value_at(t, sl) : cell_value(t, __ldcs(r), v1, v2, false, read_level(t, j));
+        } else {
+            const float4 v0 = __ldcs(r);
+            v1 = __ldcs(r + 1);
+            v2 = __ldcs(r + 2);
+            v3 = __ldcs(r + 3);
+            if constexpr (kSH)
+                c = cell_value_sh(t, v0, v1, v2);
+            else
+                c = cell_value(t, v0, v1, v2, false, read_level(t, j));
+        }
+    }
+    // vertex j + 1 of the same path is lane + T (a lane past the warp reads its own value, which
+    // no active lane uses)
+    const unsigned src = lane + T < 32u ? lane + T : lane;
+    const float n0 = __shfl_sync(kFull, c.x, src);
+    const float n1 = __shfl_sync(kFull, c.y, src);
+    const float n2 = __shfl_sync(kFull, c.z, src);
+    if (act) {
+        float o0 = v3.x, o1 = v3.y, o2 = v3.z;
+        if (j + 1 < D && j >= e.j_begin && j < e.j_end) {
+            o0 = combine(e, v3.x, v1.w, n0, c.x);
+            o1 = combine(e, v3.y, v2.w, n1, c.y);
+            o2 = combine(e, v3.z, v3.w, n2, c.z);
+        }
+        float* o = out + 3 * i;
+        o[0] = o0;
+        o[1] = o1;
+        o[2] = o2;
+    }
+}
+
 }  // namespace psf
