@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_query_staged(TableView t, psf::
 }
 
 template <bool kSH = false>
-__global__ void __launch_bounds__(kThreads, 4) k_update(TableView t) {
+__global__ void __launch_bounds__(kThreads, kSH ? 3 : 4) k_update(TableView t) {
     __shared__ unsigned long long s_touched;
     if (threadIdx.x == 0) s_touched = 0;
     __syncthreads();
