@@ -658,7 +658,7 @@ def run_psf(args) -> None:
                          "a different one every step",
                    "insert_mode": args.insert_mode, "vertex_staging": args.staging,
                    "sum_reduction": {0: "bulk (TMA) 32-B reduction", 1: "4 x red.add.u64"}[args.sum_reduction],
-                   "query_layout": {0: "depth-split warp tiles", 1: "one thread per path"}[args.query_layout],
+                   "query_layout": {0: "one thread per path", 1: "depth-split warp tiles"}[args.query_layout],
                    "slot_cache": bool(args.slot_cache),
                    "key_layout": {0: "auto", 1: "dense key array", 2: "keys in slot records"}[args.key_layout],
                    "payload": ("YCoCg two-band SH over the normal, ridge %g, 5-d key" % args.sh_ridge) if sh else "RGB",
@@ -1061,7 +1061,7 @@ def main(argv=None) -> None:
     ap.add_argument("--capacity-bits", type=int, default=1,
                     help="serving: tables of 2^(ceil(log2 V) + bits) slots (the load factor the batched tuner picks)")
     ap.add_argument("--query-layout", type=int, default=0,
-                    help="0: depth-split warp tiles (C_{j+1} by shuffle); 1: one thread per path")
+                    help="0: one thread per path; 1: depth-split warp tiles (C_{j+1} by shuffle)")
     ap.add_argument("--payload", default="rgb", choices=["rgb", "sh"],
                     help="cell payload: RGB, or YCoCg with luminance in two SH bands over the normal")
     ap.add_argument("--sh-ridge", type=float, default=0.01, help="SH payload: ridge on band 1")

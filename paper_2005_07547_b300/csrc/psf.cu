@@ -978,7 +978,7 @@ int launch_query(psf_table* t, const psf::Estimator& e, const float* d_vertices,
         return PSF_ERR_INVALID_ARG;
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->launch.query_layout == 0 && D <= 32u) {
+    if (t->launch.query_layout == 1 && D <= 32u) {
         if (t->view.payload == psf::kPayloadSH)
             launch_tiled_query<false, true>(t, e, v, P, D, d_out_rgb, nullptr, st);
         else
@@ -1036,7 +1036,7 @@ int psf_query_cv_slots(psf_table* t, const float* d_vertices, const uint32_t* d_
         return PSF_ERR_INVALID_ARG;
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->launch.query_layout == 0 && D <= 32u) {
+    if (t->launch.query_layout == 1 && D <= 32u) {
         launch_tiled_query<true, false>(t, psf::cv_estimator(t->view), v, P, D, d_out_rgb, d_slots, st);
     } else {
         const int grid = grid_for(t, resident_blocks(t, reinterpret_cast<const void*>(k_query<true>)), P,

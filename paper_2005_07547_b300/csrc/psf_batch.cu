@@ -99,13 +99,6 @@ __device__ __forceinline__ void load_begin(unsigned long long* s_begin, const un
     __syncthreads();
 }
 
-// Warp units of an item's query phase: warp tiles of 32 / D paths (depth-split) when D <= 32,
-// else 32 paths per warp, one lane each.
-unsigned long long query_units(uint32_t P, uint32_t D) {
-    if (P == 0 || D == 0) return 0;
-    return D <= 32u ? psf::query_tiles(P, D) : (static_cast<unsigned long long>(P) + 31) / 32;
-}
-
 // Table owning warp unit u: the last i with begin[i] <= u (tables without units are skipped).
 __device__ __forceinline__ unsigned find_item(const unsigned long long* s_begin, unsigned n, unsigned long long u) {
     unsigned lo = 0, hi = n;
@@ -186,13 +179,6 @@ __global__ void __launch_bounds__(kThreads)
     for (unsigned long long u = warp; u < h->units[2]; u += nwarps) {
         const unsigned it = find_item(s_begin, n, u);
         const BatchItemDev& b = items[it];
-        if (b.D <= 32u) {  // depth-split: the unit is a warp tile of 32 / D paths (warp-uniform branch)
-            if (b.slots)
-                psf::query_tile<true>(b.t, psf::cv_estimator(b.t), b.v, b.P, b.D, u - s_begin[it], b.out, b.slots);
-            else
-                psf::query_tile<false>(b.t, psf::cv_estimator(b.t), b.v, b.P, b.D, u - s_begin[it], b.out, nullptr);
-            continue;
-        }
         const unsigned long long p = (u - s_begin[it]) * 32ull + lane;
         if (p < b.P) {
             if (b.slots)
@@ -299,7 +285,8 @@ int psf_batch_set(psf_batch* b, const psf_batch_item* items, uint32_t n, void* s
         d.D = it.D;
         d.nverts = static_cast<unsigned long long>(it.P) * it.D;
         const unsigned long long nwords = ((1ull << it.table->cfg.log2_capacity) + 31ull) >> 5;
-        const unsigned long long units[3] = {(d.nverts + 31) / 32, (nwords + 31) / 32, query_units(it.P, it.D)};
+        const unsigned long long units[3] = {(d.nverts + 31) / 32, (nwords + 31) / 32,
+                                             (static_cast<unsigned long long>(it.P) + 31) / 32};
         for (int ph = 0; ph < 3; ++ph) {
             begin[ph * (kMaxItems + 1) + i] = acc[ph];
             acc[ph] += units[ph];
@@ -460,7 +447,8 @@ extern "C" int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, c
         d.D = it.D;
         d.nverts = static_cast<unsigned long long>(it.P) * it.D;
         const unsigned long long nwords = ((1ull << it.table->cfg.log2_capacity) + 31ull) >> 5;
-        const unsigned long long units[3] = {(d.nverts + 31) / 32, (nwords + 31) / 32, query_units(it.P, it.D)};
+        const unsigned long long units[3] = {(d.nverts + 31) / 32, (nwords + 31) / 32,
+                                             (static_cast<unsigned long long>(it.P) + 31) / 32};
         for (int ph = 0; ph < 3; ++ph) {
             begin[ph * (kMaxItems + 1) + i] = acc[ph];
             acc[ph] += units[ph];

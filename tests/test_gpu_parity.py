@@ -221,8 +221,8 @@ def test_deterministic_tables_and_outputs(psf_mod):
                                    dict(insert_mode=1, insert_blocks_per_sm=2), dict(vertex_staging=3),
                                    dict(sum_reduction=1), dict(sum_reduction=1, insert_mode=1, vertex_staging=0),
                                    dict(vertex_staging=3, insert_mode=1, insert_blocks_per_sm=1, query_blocks_per_sm=1),
-                                   dict(query_layout=1), dict(query_layout=1, vertex_staging=2),
-                                   dict(query_layout=0, query_blocks_per_sm=1)])
+                                   dict(query_layout=1), dict(query_layout=0, vertex_staging=2),
+                                   dict(query_layout=1, query_blocks_per_sm=1)])
 def test_launch_knobs_do_not_change_results(psf_mod, knobs):
     """Aggregation mode and grid shape change only the order of the integer additions."""
     import torch
@@ -317,7 +317,7 @@ def test_staged_vertex_tiles_with_ragged_tails(psf_mod, P, D):
     res = []
     for staging in (0, 3):
         t = psf_mod.Table(cfg)
-        t.set_launch(vertex_staging=staging, query_layout=1 if staging else 0)  # the staged query walks paths
+        t.set_launch(vertex_staging=staging, query_layout=0 if staging else 1)  # against the depth-split query
         outs = [t.step(dv, P, D).cpu().numpy() for _ in range(2)]
         outs.append(t.query_biased(dv, P, D, 0.5).cpu().numpy())
         res.append((t.export().tobytes(), np.concatenate(outs).tobytes(), t.stats()["status"]))
