@@ -97,10 +97,7 @@ typedef struct {
     uint32_t cv_max_depth;  /* the CV is applied to vertices j < cv_max_depth only */
     uint32_t frac_bits;     /* F: fixed-point fraction bits of the accumulators, 8..32 */
     uint32_t cache_fp16;    /* 1: the update also writes an 8-byte FP16 copy of L~ and queries read it
-                               (the blend always keeps the FP32 master, which queries read otherwise).
-                               The copy is dense: entry i belongs to the i-th cell claimed in the table
-                               (a 4-byte index per slot maps a slot to its entry), so the copies of the
-                               live cells share few cache lines (measured: see the design notes) */
+                               (the blend always keeps the FP32 master, which queries read otherwise) */
     uint32_t blend_mode;    /* 0: eq. (11) square-root blend; 1: constant alpha = alpha_min */
     uint32_t key_layout;    /* where the cell keys live: 1 = a dense 8-byte array, 2 = inside each 64-byte
                                slot record (an FP32 query reads key and approximant from one sector),
@@ -294,10 +291,9 @@ typedef struct {
  * PSF_STATUS_TABLE_FULL.  RGB payload only. */
 int psf_insert_records(psf_table* t, const psf_record* d_records, uint64_t n, void* stream);
 
-/* Write the approximant of n cells (d_keys: n distinct uint64 keys, d_L: n*3 float32, device
- * arrays) into the table, finding or claiming each key's cell; counters and sums are left as
- * they are, and the FP16 copy is rewritten when the table keeps one.  Errors as
- * psf_insert_records. */
+/* Write the approximant of n cells (d_keys: n uint64, d_L: n*3 float32, device arrays) into
+ * the table, finding or claiming each key's cell; counters and sums are left as they are,
+ * and the FP16 copy is rewritten when the table keeps one.  Errors as psf_insert_records. */
 int psf_set_approximant(psf_table* t, const uint64_t* d_keys, const float* d_L, uint64_t n, void* stream);
 
 /* Synchronised statistics and sticky status.  Synchronises `stream`. */

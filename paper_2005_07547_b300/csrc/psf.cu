@@ -91,7 +91,7 @@ void status_give(const StatusWord& w) {
 }
 
 struct Layout {
-    size_t hdr, keys, slots, mirror, index, dirty, total;
+    size_t hdr, keys, slots, mirror, dirty, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -133,8 +133,6 @@ Layout layout_of(const psf_config* c) {
     off = align256(off + cap * (c->payload == psf::kPayloadSH ? sizeof(psf::SlotSH) : sizeof(Slot)));
     L.mirror = off;
     if (c->cache_fp16) off = align256(off + cap * sizeof(uint2));
-    L.index = off;
-    if (c->cache_fp16) off = align256(off + cap * sizeof(unsigned));
     L.dirty = off;
     off = align256(off + ((cap + 31) / 32) * sizeof(unsigned));
     L.total = off;
@@ -543,7 +541,7 @@ __global__ void __launch_bounds__(kThreads) k_export(TableView t, unsigned long 
         r.L[1] = L.y;
         r.L[2] = L.z;
         if (t.mirror) {
-            const uint2 h = t.mirror[t.cell_index[s]];
+            const uint2 h = t.mirror[s];
             r.L_fp16[0] = static_cast<uint16_t>(h.x & 0xffffu);
             r.L_fp16[1] = static_cast<uint16_t>(h.x >> 16);
             r.L_fp16[2] = static_cast<uint16_t>(h.y & 0xffffu);
@@ -659,7 +657,7 @@ __global__ void __launch_bounds__(kThreads) k_set_approximant(TableView t, const
                 cur.y = y;
                 cur.z = z;
                 t.slots[slot].L = cur;
-                if (t.mirror) t.mirror[t.cell_index[slot]] = psf::pack_half4(x, y, z);
+                if (t.mirror) t.mirror[slot] = psf::pack_half4(x, y, z);
             }
         }
     }
@@ -887,7 +885,6 @@ int psf_create(const psf_config* cfg, void* d_mem, size_t bytes, void* stream, p
     }
     v.slots = reinterpret_cast<Slot*>(base + L.slots);
     v.mirror = cfg->cache_fp16 ? reinterpret_cast<uint2*>(base + L.mirror) : nullptr;
-    v.cell_index = cfg->cache_fp16 ? reinterpret_cast<unsigned*>(base + L.index) : nullptr;
     v.dirty = reinterpret_cast<unsigned*>(base + L.dirty);
     v.h_status = word.dev;
     t->d_status = word.dev;

@@ -7,9 +7,7 @@
 //   slots  Slot[cap]  (64 B)        sums + c_new (bytes 0-31), key (32-39, when inside),
 //                                   c_old (40-47), approximant L~ (48-63): one aligned
 //                                   64-byte block per cell
-//   mirror uint2[cap] (8 B)         FP16 copy of L~ read by queries (cache_fp16 = 1), dense:
-//                                   entry i belongs to the i-th cell claimed in the table
-//   index  u32[cap]                 slot -> that compact index (cache_fp16 = 1)
+//   mirror uint2[cap] (8 B)         FP16 copy of L~ read by queries (cache_fp16 = 1)
 //   dirty  u32[cap/32]              one bit per slot: touched this iteration
 // Tables with the YCoCg two-band SH payload keep dense keys and 192-byte SlotSH records
 // (sixteen 64-bit sums, c_old, six coefficients) instead of Slot and the FP16 copy.
@@ -43,8 +41,7 @@ struct DevHeader {
     unsigned long long leaders;  // (warp, key) groups scattered by all inserts so far
     unsigned int barrier_count;  // grid barrier of the batched kernel
     unsigned int barrier_gen;
-    unsigned int cells;  // cells claimed so far: the next compact index of the FP16 copy
-    unsigned int pad[49];
+    unsigned int pad[50];
 };
 static_assert(sizeof(DevHeader) == 256, "header is one 256-byte block");
 
@@ -68,8 +65,7 @@ struct TableView {
     unsigned long long* keys;  // key of slot s at keys[s * key_stride]
     unsigned key_stride;       // 1: dense key array; 8: the key field of the 64-byte slot records
     Slot* slots;
-    uint2* mirror;         // FP16 query copy (cache_fp16), indexed by the cell's compact index, else nullptr
-    unsigned* cell_index;  // cache_fp16: slot -> compact index of its cell (allocated when it is claimed)
+    uint2* mirror;  // FP16 query copy (cache_fp16), else nullptr
     unsigned* dirty;
     unsigned* h_status;  // host-mapped copy of the status word (may be nullptr)
     uint32_t log2cap;
@@ -334,7 +330,6 @@ __device__ __forceinline__ void probe_warp(const TableView& t, bool need, unsign
     unsigned n = 0;
     long long found = -1;
     while (__any_sync(kFull, need)) {
-        bool claimed = false;
         if (need) {
             ++n;
             unsigned long long* kp = t.keys + static_cast<unsigned long long>(s) * t.key_stride;
@@ -342,8 +337,7 @@ __device__ __forceinline__ void probe_warp(const TableView& t, bool need, unsign
             bool hit = k == key;
             if (!hit && k == kEmpty) {
                 const unsigned long long old = atomicCAS(kp, kEmpty, key);
-                claimed = old == kEmpty;
-                hit = claimed || old == key;
+                hit = old == kEmpty || old == key;
             }
             if (hit) {
                 found = s;
@@ -352,19 +346,6 @@ __device__ __forceinline__ void probe_warp(const TableView& t, bool need, unsign
                 need = false;
             } else {
                 s = (s + 1) & mask;
-            }
-        }
-        if (t.cell_index) {
-            // a new cell takes the next compact index of the FP16 copy: one returning atomic per
-            // warp and step, and only where a lane claimed a slot
-            const unsigned won = __ballot_sync(kFull, claimed);
-            if (won) {
-                const unsigned lane = threadIdx.x & 31u;
-                const int leader = __ffs(won) - 1;
-                unsigned first = 0;
-                if (static_cast<int>(lane) == leader) first = atomicAdd(&t.hdr->cells, static_cast<unsigned>(__popc(won)));
-                first = __shfl_sync(kFull, first, leader);
-                if (claimed) t.cell_index[s] = first + __popc(won & ((1u << lane) - 1u));
             }
         }
     }
@@ -888,7 +869,7 @@ __device__ __forceinline__ void blend_store(const TableView& t, unsigned long lo
         d.L.z = fmaf(alpha, __fdiv_rn(__ll2float_rn(d.a23.x), fcn), keep * d.L.z);
         __stcg(p + 2, make_longlong2(d.kc.x, ctot));  // the key field is written back unchanged
         __stcg(reinterpret_cast<float4*>(p + 3), d.L);
-        if (t.mirror) t.mirror[__ldcg(t.cell_index + s)] = pack_half4(d.L.x, d.L.y, d.L.z);
+        if (t.mirror) t.mirror[s] = pack_half4(d.L.x, d.L.y, d.L.z);
     }
     __stcg(p, z);
     __stcg(p + 1, z);
@@ -956,7 +937,7 @@ __device__ __forceinline__ unsigned update_words(const TableView& t, unsigned lo
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float3 value_at(const TableView& t, unsigned long long s, bool fp32_master = false) {
     if (t.mirror && !fp32_master) {
-        const uint2 h = __ldcg(t.mirror + __ldcg(t.cell_index + s));
+        const uint2 h = __ldcg(t.mirror + s);
         return make_float3(__half2float(__ushort_as_half(static_cast<unsigned short>(h.x & 0xffffu))),
                            __half2float(__ushort_as_half(static_cast<unsigned short>(h.x >> 16))),
                            __half2float(__ushort_as_half(static_cast<unsigned short>(h.y & 0xffffu))));

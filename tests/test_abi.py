@@ -89,8 +89,8 @@ def test_table_bytes_and_config_validation(lib):
     # header + 64-byte slot record (key inside, the automatic choice at 2^16 slots) + dirty bits
     assert n16 >= (1 << 16) * 64 + (1 << 16) // 8
     assert n16 % 256 == 0
-    fp16 = _abi.make_config(log2_capacity=16, cache_fp16=True)  # plus the FP16 copy, its index and dense keys
-    assert lib.psf_table_bytes(ctypes.byref(fp16)) == n16 + (1 << 16) * (8 + 8 + 4)
+    fp16 = _abi.make_config(log2_capacity=16, cache_fp16=True)  # plus the FP16 copy and dense keys
+    assert lib.psf_table_bytes(ctypes.byref(fp16)) == n16 + (1 << 16) * (8 + 8)
     assert lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=17))) > 2 * n16 - 4096
     # a dense key array costs 8 bytes per slot more than keys inside the slot records
     dense = lib.psf_table_bytes(ctypes.byref(_abi.make_config(log2_capacity=16, key_layout=1)))
