@@ -557,13 +557,33 @@ def run_psf(args) -> None:
                                levels=args.levels, payload=1 if sh else 0, sh_ridge=args.sh_ridge,
                                use_normal=not sh)
 
+    base_knobs = dict(insert_mode=args.insert_mode, vertex_staging=args.staging, sum_reduction=args.sum_reduction,
+                      query_layout=args.query_layout, insert_blocks_per_sm=args.insert_blocks,
+                      query_blocks_per_sm=args.query_blocks, update_blocks_per_sm=args.update_blocks)
+    dev = [torch.from_numpy(v).cuda() for v in host]
+    tuned = {}
+
+    def knobs_for(cache_fp16):
+        """The launch knobs: the flags' values, or with --tune the autotuner's pick (grid caps and
+        query layout timed on this workload's first batches with the benchmark's own calls)."""
+        if not args.tune:
+            return dict(base_knobs)
+        if cache_fp16 not in tuned:
+            from paper_2005_07547_b300 import autotune
+
+            space = {"insert_blocks_per_sm": (0, 4), "query_blocks_per_sm": (0, 4, 2),
+                     "update_blocks_per_sm": (0, 2, 1), "query_layout": (0, 1)}
+            res = autotune.tune_table(make_cfg(cache_fp16), dev[:min(6, len(dev))], P, D, space=space, warmup=2,
+                                      iters=4, slot_cache=bool(args.slot_cache))
+            tuned[cache_fp16] = {"best": {**base_knobs, **res["best"]}, "best_ms": res["best_ms"],
+                                 "candidates": len(res["all"])}
+        return dict(tuned[cache_fp16]["best"])
+
     def new_table(cache_fp16):
         t = psf.Table(make_cfg(cache_fp16))
-        t.set_launch(insert_mode=args.insert_mode, vertex_staging=args.staging, sum_reduction=args.sum_reduction,
-                     query_layout=args.query_layout)
+        t.set_launch(**knobs_for(cache_fp16))
         return t
 
-    dev = [torch.from_numpy(v).cuda() for v in host]
     table = new_table(fp16)
     m = time_single(psf, table, dev, P, D, args.steps, args.warmup, bool(args.slot_cache), local, world)
     table.close()
@@ -586,7 +606,7 @@ def run_psf(args) -> None:
         other = {"value": V * args.steps / (m2["elapsed_ms"] / 1e3), "ms_per_step": m2["elapsed_ms"] / args.steps,
                  "kernels_avg_ms": {k: sum(x) / len(x) for k, x in m2["kernel_ms"].items()},
                  "p50": float(np.percentile(m2["step_ms"], 50)), "p99": float(np.percentile(m2["step_ms"], 99)),
-                 "clocks": m2["clocks"]}
+                 "clocks": m2["clocks"], "launch_knobs": knobs_for(not fp16)}
 
     # end to end through the public API: pinned host vertices in, host CV outputs back,
     # copies inside the timed region, H2D of step k+1 overlapped with compute of step k
@@ -658,7 +678,10 @@ def run_psf(args) -> None:
                          "a different one every step",
                    "insert_mode": args.insert_mode, "vertex_staging": args.staging,
                    "sum_reduction": {0: "bulk (TMA) 32-B reduction", 1: "4 x red.add.u64"}[args.sum_reduction],
-                   "query_layout": {0: "one thread per path", 1: "depth-split warp tiles"}[args.query_layout],
+                   "launch_knobs": knobs_for(fp16),
+                   "autotune": ({"space": "insert / query / update blocks per SM x query layout",
+                                 "candidates": tuned[fp16]["candidates"], "tuned_ms": tuned[fp16]["best_ms"]}
+                                if args.tune else None),
                    "slot_cache": bool(args.slot_cache),
                    "key_layout": {0: "auto", 1: "dense key array", 2: "keys in slot records"}[args.key_layout],
                    "payload": ("YCoCg two-band SH over the normal, ridge %g, 5-d key" % args.sh_ridge) if sh else "RGB",
@@ -1060,6 +1083,11 @@ def main(argv=None) -> None:
     ap.add_argument("--budget-gb", type=float, default=60.0, help="serving: device memory for tables")
     ap.add_argument("--capacity-bits", type=int, default=1,
                     help="serving: tables of 2^(ceil(log2 V) + bits) slots (the load factor the batched tuner picks)")
+    ap.add_argument("--tune", type=int, default=1,
+                    help="1: pick grid caps and query layout with the autotuner before timing; 0: the flags' knobs")
+    ap.add_argument("--insert-blocks", type=int, default=0, help="cap on resident insert blocks per SM (0: occupancy)")
+    ap.add_argument("--query-blocks", type=int, default=0, help="cap on resident query blocks per SM (0: occupancy)")
+    ap.add_argument("--update-blocks", type=int, default=0, help="cap on resident blend blocks per SM (0: occupancy)")
     ap.add_argument("--query-layout", type=int, default=0,
                     help="0: one thread per path; 1: depth-split warp tiles (C_{j+1} by shuffle)")
     ap.add_argument("--payload", default="rgb", choices=["rgb", "sh"],

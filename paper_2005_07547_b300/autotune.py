@@ -82,22 +82,34 @@ class _Same:
 
 
 def tune_table(cfg: _abi.Config, batches, P: int, D: int, space: dict | None = None, warmup: int = 2,
-               iters: int = 4, verify: bool = False) -> dict:
-    """Fastest psf_step launch knobs for this configuration and input (list of (P*D, 16) tensors)."""
+               iters: int = 4, verify: bool = False, slot_cache: bool = False) -> dict:
+    """Fastest launch knobs of one iteration (psf_step, or with slot_cache the slot-cache insert,
+    the blend and the slot-cache query) for this configuration and input (list of (P*D, 16)
+    tensors)."""
     import torch
 
     space = space or TABLE_SPACE
     out = torch.empty((P * D, 3), dtype=torch.float32, device=batches[0].device)
+    slots = torch.empty(P * D, dtype=torch.int32, device=batches[0].device) if slot_cache else None
     results = []
     same = _Same(verify)
     keys = list(space)
+
+    def step(t, v):
+        if slots is None:
+            t.step(v, P, D, out=out)
+        else:
+            t.insert_slots(v, P, D, slots=slots)
+            t.update()
+            t.query_cv_slots(v, slots, P, D, out=out)
+
     for values in itertools.product(*(space[k] for k in keys)):
         knobs = dict(zip(keys, values))
         t = Table(cfg)
         t.set_launch(**knobs)
         for k in range(warmup):
-            t.step(batches[k % len(batches)], P, D, out=out)
-        ms = _time_ms(lambda k: t.step(batches[(warmup + k) % len(batches)], P, D, out=out), iters)
+            step(t, batches[k % len(batches)])
+        ms = _time_ms(lambda k: step(t, batches[(warmup + k) % len(batches)]), iters)
         same([t], knobs)
         t.close()
         results.append((ms, knobs))
