@@ -30,8 +30,14 @@ def test_committed_traffic_applies_to_its_own_setup_only():
     setup = {k: cap[k] for k in ("workload", "cache", "levels", "log2_capacity", "slot_cache")}
     got = bench.load_traffic("k_insert", False, setup)
     assert got == cap["kernels"]["k_insert"]["bytes_per_launch"] and got > 0
-    for key, other in (("workload", "1920x1080_d5"), ("cache", "other"), ("levels", 7), ("log2_capacity", 3),
+    for key, other in (("workload", "64x64_d3"), ("cache", "other"), ("levels", 7), ("log2_capacity", 3),
                        ("slot_cache", not setup["slot_cache"])):
         assert bench.load_traffic("k_insert", False, dict(setup, **{key: other})) is None, key
     # the staged insert is a different kernel: only its own capture counts
     assert bench.load_traffic("k_insert", True, setup) == cap["kernels"].get("k_insert_staged", {}).get("bytes_per_launch")
+
+
+def test_sh_payload_bytes_per_launch():
+    V, C = 1000, 300
+    assert bench.algorithmic_bytes(V, C, cache_fp16=False, payload=1) == {
+        "k_insert": 64 * V + 264 * C, "k_update": 320 * C, "k_query": 76 * V + 32 * C}
