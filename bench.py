@@ -89,10 +89,10 @@ def algorithmic_bytes(V: int, touched: float, cache_fp16: bool, slot_cache: bool
     them and reads and writes c_old and the 24-B coefficients (320), the query reads the key
     and the coefficients (8 + 24).
     """
-    if payload == 1:
-        return {"k_insert": 64.0 * V + 264.0 * touched, "k_update": 320.0 * touched,
-                "k_query": 76.0 * V + 32.0 * touched}
     extra = 4.0 * V if slot_cache else 0.0
+    if payload == 1:
+        return {"k_insert": 64.0 * V + 264.0 * touched + extra, "k_update": 320.0 * touched,
+                "k_query": 76.0 * V + 32.0 * touched + extra}
     return {
         "k_insert": 64.0 * V + 72.0 * touched + extra,
         "k_update": (120.0 if cache_fp16 else 112.0) * touched,
@@ -547,9 +547,8 @@ def run_psf(args) -> None:
     fp16 = bool(args.fp16 or w["cache_fp16"])
 
     sh = args.payload == "sh"
-    if sh:  # the SH payload keeps no FP16 copy and no slot cache; the paper's 5-d key
+    if sh:  # the SH payload keeps no FP16 copy; the paper's 5-d key
         fp16 = False
-        args.slot_cache = 0
 
     def make_cfg(cache_fp16):
         return psf.make_config(log2_capacity=log2cap, pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],

@@ -127,9 +127,10 @@ typedef struct {
                                cache_fp16 = 0, levels <= 1 and key_layout != 2; its cells are 192-byte
                                records plus a dense 8-byte key; it adds |n_k| <= 1 + 2^-10 (unit
                                normals) to the range rule;
-                               psf_insert_slots, psf_query_cv_slots, psf_insert_progressive, psf_export
-                               and the batched calls reject it (PSF_ERR_INVALID_ARG), psf_export_sh
-                               exports it. */
+                               psf_insert_progressive, psf_export, psf_insert_records,
+                               psf_set_approximant and the batched calls reject it
+                               (PSF_ERR_INVALID_ARG), psf_export_sh exports it; the slot-cache calls
+                               take it (the query then reads the fit at the noted slot). */
     float sh_ridge;         /* payload 1: ridge weight on band 1 relative to the cell's weight, >= 0 and
                                finite (0.01 suggested; 0 allows an unregularised fit, and an iteration
                                whose normal moments leave the system singular then keeps band 1 at 0) */

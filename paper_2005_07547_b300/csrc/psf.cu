@@ -213,9 +213,11 @@ __global__ void __launch_bounds__(kThreads, kHier ? 4 : 0) k_insert(TableView t,
 }
 
 // k_insert for a table with the SH payload (flat tables; the next grid-stride tile's records
-// are loaded while the current one probes and adds).
-template <int kMode>
-__global__ void __launch_bounds__(kThreads) k_insert_sh(TableView t, const float4* __restrict__ v, unsigned long long n) {
+// are loaded while the current one probes and adds).  With kSlots it also notes each vertex's
+// slot for the query (slots[i]).
+template <int kMode, bool kSlots = false>
+__global__ void __launch_bounds__(kThreads) k_insert_sh(TableView t, const float4* __restrict__ v, unsigned long long n,
+                                                       unsigned* __restrict__ slots = nullptr) {
     __shared__ unsigned s_max_probe;
     __shared__ unsigned long long s_leaders;
     __shared__ psf::ShSums s_stage[kThreads];
@@ -246,7 +248,10 @@ __global__ void __launch_bounds__(kThreads) k_insert_sh(TableView t, const float
             n2 = __ldcs(r + 2);
             n3 = __ldcs(r + 3);
         }
-        psf::insert_warp_sh<kMode>(t, base + threadIdx.x < n, v0, v1, v2, v3, &max_len, stage, &leaders);
+        const unsigned noted = psf::insert_warp_sh<kMode>(t, base + threadIdx.x < n, v0, v1, v2, v3, &max_len, stage,
+                                                           &leaders);
+        if constexpr (kSlots)
+            if (base + threadIdx.x < n) slots[base + threadIdx.x] = noted;
         v0 = n0;
         v1 = n1;
         v2 = n2;
@@ -929,9 +934,9 @@ int psf_insert(psf_table* t, const float* d_vertices, uint64_t n, void* stream) 
     psf_count_iteration_vertices(t, n);
     if (t->view.payload == psf::kPayloadSH) {
         if (t->launch.insert_mode == 1)
-            launch_sized(t, k_insert_sh<psf::kAggNone>, n, st, t->view, v, n);
+            launch_sized(t, k_insert_sh<psf::kAggNone>, n, st, t->view, v, n, static_cast<unsigned*>(nullptr));
         else
-            launch_sized(t, k_insert_sh<psf::kAggWarp>, n, st, t->view, v, n);
+            launch_sized(t, k_insert_sh<psf::kAggWarp>, n, st, t->view, v, n, static_cast<unsigned*>(nullptr));
     } else if (t->view.levels > 1) {
         launch_insert<true>(t, v, n, st);
     } else {
@@ -1011,7 +1016,7 @@ int psf_query_biased(psf_table* t, const float* d_vertices, uint32_t P, uint32_t
 }
 
 int psf_insert_slots(psf_table* t, const float* d_vertices, uint32_t P, uint32_t D, uint32_t* d_slots, void* stream) {
-    if (!t || t->view.payload != psf::kPayloadRGB) return PSF_ERR_INVALID_ARG;
+    if (!t) return PSF_ERR_INVALID_ARG;
     const unsigned long long n = static_cast<unsigned long long>(P) * D;
     if (n == 0) return PSF_OK;
     if (!d_vertices || !d_slots || (reinterpret_cast<uintptr_t>(d_vertices) & 15u) ||
@@ -1020,7 +1025,12 @@ int psf_insert_slots(psf_table* t, const float* d_vertices, uint32_t P, uint32_t
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     psf_count_iteration_vertices(t, n);
-    if (t->view.levels > 1)
+    if (t->view.payload == psf::kPayloadSH) {
+        if (t->launch.insert_mode == 1)
+            launch_sized(t, k_insert_sh<psf::kAggNone, true>, n, st, t->view, v, n, d_slots);
+        else
+            launch_sized(t, k_insert_sh<psf::kAggWarp, true>, n, st, t->view, v, n, d_slots);
+    } else if (t->view.levels > 1)
         launch_insert_slots<true>(t, v, P, D, d_slots, st);
     else
         launch_insert_slots<false>(t, v, P, D, d_slots, st);
@@ -1029,14 +1039,18 @@ int psf_insert_slots(psf_table* t, const float* d_vertices, uint32_t P, uint32_t
 
 int psf_query_cv_slots(psf_table* t, const float* d_vertices, const uint32_t* d_slots, uint32_t P, uint32_t D,
                        float* d_out_rgb, void* stream) {
-    if (!t || t->view.payload != psf::kPayloadRGB) return PSF_ERR_INVALID_ARG;
+    if (!t) return PSF_ERR_INVALID_ARG;
     if (P == 0 || D == 0) return PSF_OK;
     if (!d_vertices || !d_slots || !d_out_rgb || (reinterpret_cast<uintptr_t>(d_vertices) & 15u) ||
         (reinterpret_cast<uintptr_t>(d_slots) & 3u) || (reinterpret_cast<uintptr_t>(d_out_rgb) & 3u))
         return PSF_ERR_INVALID_ARG;
     const float4* v = reinterpret_cast<const float4*>(d_vertices);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (t->launch.query_layout == 1 && D <= 32u) {
+    if (t->view.payload == psf::kPayloadSH) {
+        const int grid = grid_for(t, resident_blocks(t, reinterpret_cast<const void*>(k_query<true, true>)), P,
+                                  t->launch.query_blocks_per_sm);
+        k_query<true, true><<<grid, kThreads, 0, st>>>(t->view, psf::cv_estimator(t->view), v, P, D, d_out_rgb, d_slots);
+    } else if (t->launch.query_layout == 1 && D <= 32u) {
         launch_tiled_query<true, false>(t, psf::cv_estimator(t->view), v, P, D, d_out_rgb, d_slots, st);
     } else {
         const int grid = grid_for(t, resident_blocks(t, reinterpret_cast<const void*>(k_query<true>)), P,

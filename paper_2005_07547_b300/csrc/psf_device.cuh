@@ -635,11 +635,12 @@ __device__ __forceinline__ int sh_values(const TableView& t, const float4& v0, c
 // One warp's worth of vertices into an SH table (flat tables only): classify, merge runs of
 // adjacent lanes on one key (kAggWarp, the segmented shuffle reduction of insert_warp over
 // the sixteen sums), then one head per group probes and adds the group's sums to the
-// slot's first 128 bytes with one bulk reduction.
+// slot's first 128 bytes with one bulk reduction.  Returns the slot of this lane's cell for
+// the slot cache (kNoSlot where the vertex was not added).
 template <int kMode>
-__device__ __forceinline__ void insert_warp_sh(const TableView& t, bool valid, const float4& v0, const float4& v1,
-                                               const float4& v2, const float4& v3, unsigned* max_len, ShSums* stage,
-                                               unsigned* leaders) {
+__device__ __forceinline__ unsigned insert_warp_sh(const TableView& t, bool valid, const float4& v0, const float4& v1,
+                                                   const float4& v2, const float4& v3, unsigned* max_len, ShSums* stage,
+                                                   unsigned* leaders) {
     const unsigned lane = threadIdx.x & 31u;
     unsigned long long key = 0;
     long long own[kShSums];
@@ -664,10 +665,11 @@ __device__ __forceinline__ void insert_warp_sh(const TableView& t, bool valid, c
     }
     bool head = cls == 1;
     unsigned members = 1u << lane;
+    unsigned joined = 0;
     if (kMode == kAggWarp) {
         const unsigned long long prev = __shfl_up_sync(kFull, key, 1);
         const bool joins = cls == 1 && lane > 0 && ((accepted >> (lane - 1)) & 1u) && prev == key;
-        const unsigned joined = __ballot_sync(kFull, joins);
+        joined = __ballot_sync(kFull, joins);
         if (joined) {
             const unsigned heads = ~joined;
 #pragma unroll
@@ -706,6 +708,10 @@ __device__ __forceinline__ void insert_warp_sh(const TableView& t, bool valid, c
         }
     }
     *leaders += __popc(__ballot_sync(kFull, head));
+    // a lane's head: the last lane at or before it that does not continue a run
+    const unsigned upto = lane == 31 ? kFull : ((2u << lane) - 1u);
+    const long long hs = __shfl_sync(kFull, head ? slot : -1ll, 31 - __clz(~joined & upto));
+    return cls == 1 && hs >= 0 ? static_cast<unsigned>(hs) : kNoSlot;
 }
 
 // A signed 128-bit integer rounded to the nearest float: the bits below the top 64 are
@@ -1036,7 +1042,12 @@ __device__ __forceinline__ void query_path(const TableView& t, const Estimator& 
         const float4 v0 = __ldcs(r), v1 = __ldcs(r + 1), v2 = __ldcs(r + 2), v3 = __ldcs(r + 3);
         float3 c;
         if constexpr (kSH) {
-            c = cell_value_sh(t, v0, v1, v2);
+            if constexpr (kSlots) {
+                const unsigned sl = __ldcs(slots + i);
+                c = sl != kNoSlot ? sh_eval(t, sl, v1) : cell_value_sh(t, v0, v1, v2);
+            } else {
+                c = cell_value_sh(t, v0, v1, v2);
+            }
         } else if constexpr (kSlots) {
             const unsigned sl = __ldcs(slots + i);
             c = sl != kNoSlot ? value_at(t, sl) : cell_value(t, v0, v1, v2, false, read_level(t, static_cast<unsigned>(j)));

@@ -192,8 +192,6 @@ def test_sh_tables_are_rejected_where_the_payload_does_not_apply(psf_mod):
     slots = torch.zeros(4, dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
     bad = _abi.PSF_ERR_INVALID_ARG
-    assert lib.psf_insert_slots(t.handle, dv.data_ptr(), 4, 1, slots.data_ptr(), s) == bad
-    assert lib.psf_query_cv_slots(t.handle, dv.data_ptr(), slots.data_ptr(), 4, 1, out.data_ptr(), s) == bad
     assert lib.psf_insert_progressive(t.handle, dv.data_ptr(), 4, 1, 0, s) == bad
     n = ctypes.c_size_t()
     assert lib.psf_export(t.handle, None, 0, ctypes.byref(n), s) == bad
@@ -207,3 +205,34 @@ def test_sh_tables_are_rejected_where_the_payload_does_not_apply(psf_mod):
     assert lib.psf_export_sh(rgb.handle, None, 0, ctypes.byref(n), s) == bad
     rgb.close()
     t.close()
+
+
+@pytest.mark.parametrize("insert_mode", [0, 1])
+def test_sh_slot_cache_gives_the_same_tables_and_outputs(psf_mod, insert_mode):
+    """The slot-cache insert leaves the same table as the plain insert, and the query that reads
+    each vertex's fit at its noted slot returns the probing query's outputs bit for bit
+    (vertices that were not added -- range rule, zero weight -- fall back to probing)."""
+    import torch
+
+    rng = np.random.default_rng(7)
+    P, D = 3001, 3
+    v = random_vertices(rng, P * D, q=3, cells_per_axis=4, zero_weight_fraction=0.05)
+    v[::97, 4] = 2.0  # a few normals outside the unit-normal range rule
+    dv = torch.from_numpy(v).cuda()
+    cfg = psf_mod.make_config(log2_capacity=14, pos_bits=3, dir_bits=2, use_normal=False, payload=1, sh_ridge=0.02)
+    a, b = psf_mod.Table(cfg), psf_mod.Table(cfg)
+    a.set_launch(insert_mode=insert_mode)
+    b.set_launch(insert_mode=insert_mode)
+    for it in range(3):
+        a.insert(dv)
+        slots = b.insert_slots(dv, P, D)
+        assert a.export().tobytes() == b.export().tobytes()
+        a.update()
+        b.update()
+        want = a.query_cv(dv, P, D).cpu().numpy()
+        got = b.query_cv_slots(dv, slots, P, D).cpu().numpy()
+        assert np.array_equal(want, got, equal_nan=True), it
+        assert (slots.cpu().numpy() == -1).sum() > 0  # some vertices were not added
+    assert a.stats()["status"] == b.stats()["status"] == psf_mod.STATUS_RANGE
+    a.close()
+    b.close()
