@@ -8,7 +8,11 @@
 //   k_update  one warp per 1024 slots of the dirty bitmap, set bits compacted across
 //             the warp, one lane per touched cell applies eq. (10)-(11)
 //   k_query   one thread per path, walking its vertices from the last to the first,
-//             one probe per vertex (Section "Control variates", CVEstimator)
+//             one probe per vertex, or none with the slot cache (Section "Control
+//             variates", CVEstimator); k_query_tiled splits it by depth (a launch knob)
+// Also here: the progressive and staged inserts, the YCoCg two-band SH payload's insert
+// (k_insert_sh; its blend and query are k_update<true> and k_query<., true>), the sharded
+// session's record merge and approximant copy, export, reset and statistics.
 // Grids are persistent (grid-stride) and sized as a multiple of the SM count.
 
 #include <cuda_runtime.h>
