@@ -145,7 +145,8 @@ def test_bench_aggregates_max_over_ranks():
     assert res[0][2] != res[1][2]  # ranks render different sessions
 
 
-def test_sharded_session_matches_one_table(oracle_mod):
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_session_matches_one_table(oracle_mod, world):
     """Owners' cells equal the whole-session oracle's bit for bit (keys, c_old and the FP64
     blend of identical integer sums) after every iteration; each rank's control-variate
     outputs for its own paths equal the whole session's within the FP32 tolerance (cells a
@@ -153,7 +154,6 @@ def test_sharded_session_matches_one_table(oracle_mod):
     from parity import check_cv
     from synth.scene import iteration_vertices, workload
 
-    world = 2
     res = _run(_shard_worker, world)
     w = workload("64x64_d3")
     P, D = w["width"] * w["height"], w["depth"]
