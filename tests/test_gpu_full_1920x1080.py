@@ -9,8 +9,11 @@ counters exactly; the FP32 approximant within 1e-5, the FP16 copy within 2e-3 re
 after the insert (exact sums) on frames 0, 8 and 15, and their control-variate outputs
 on every 16th path, all depths (tolerance 1e-5 or 2e-3 norm-wise).  The moving camera
 keeps bringing new cells into the table while old ones age, so live and touched cells
-differ from frame to frame.
+differ from frame to frame.  The same comparison over all 64 frames of the workload runs
+when PSF_ALL_FRAMES=1 is set (about 15 minutes, most of it the oracle).
 """
+
+import os
 
 import numpy as np
 import pytest
@@ -24,6 +27,16 @@ NAME, FRAMES, STRIDE = "1920x1080_d5", 16, 16
 
 
 def test_1920x1080_depth5_moving_camera_fp32_and_fp16(psf_mod, oracle_mod):
+    _run(psf_mod, oracle_mod, FRAMES)
+
+
+@pytest.mark.skipif(not os.environ.get("PSF_ALL_FRAMES"), reason="all 64 frames take ~15 min: set PSF_ALL_FRAMES=1")
+def test_1920x1080_depth5_all_64_frames(psf_mod, oracle_mod):
+    """The workload's whole length: 64 frames, the camera crossing 0.64 of the scene."""
+    _run(psf_mod, oracle_mod, 64)
+
+
+def _run(psf_mod, oracle_mod, frames):
     import torch
 
     from synth.scene import workload
@@ -37,12 +50,12 @@ def test_1920x1080_depth5_moving_camera_fp32_and_fp16(psf_mod, oracle_mod):
     slots = {fp16: torch.empty(P * D, dtype=torch.int32, device="cuda") for fp16 in tables}
     outs = {fp16: torch.empty((P * D, 3), dtype=torch.float32, device="cuda") for fp16 in tables}
     live = []
-    for f, v in enumerate(fullsize.named_iterations(NAME, FRAMES)):
+    for f, v in enumerate(fullsize.named_iterations(NAME, frames)):
         dv = torch.from_numpy(v).cuda()
         for fp16, t in tables.items():
             t.insert_slots(dv, P, D, slots=slots[fp16])
         st = ora.insert(v)
-        if f in (0, 8, FRAMES - 1):
+        if f in (0, 8, frames - 1):
             ref = ora.export()
             for t in tables.values():
                 check_after_insert(t.export(), ref)
