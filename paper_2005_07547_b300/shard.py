@@ -180,6 +180,8 @@ class TableShard:
         return rec
 
     def merge_and_blend(self, records: np.ndarray) -> np.ndarray:
+        """Add the received records, blend, and return the blended cells' approximants (read
+        from a full export of the table: host-side, O(live cells) per iteration)."""
         import torch
 
         if len(records):
