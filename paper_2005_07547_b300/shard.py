@@ -18,8 +18,8 @@ large for one GPU splits its paths across ranks, and every iteration runs four s
 The per-rank work sits behind a small backend interface (contributions, merge_and_blend,
 set_approximant, query_cv): `TableShard` runs it on the GPU library through the C ABI
 (psf_insert, psf_export, psf_insert_records, psf_update, psf_set_approximant, psf_query_cv).
-`step` drives one iteration over torch.distributed (any backend with all_to_all_single and
-all_gather, gloo included); `step_in_process` runs the same four steps for several ranks in
+`step` drives one iteration over torch.distributed (gloo with host tensors, NCCL with device
+tensors); `step_in_process` runs the same four steps for several ranks in
 one process, one rank after the other, with the exchanges done by array slicing.
 """
 
@@ -91,21 +91,32 @@ def _as_i64(a: np.ndarray):
     return torch.from_numpy(np.ascontiguousarray(a).view(np.int64).reshape(-1))
 
 
+def _device(group):
+    """Where the collectives' tensors live: NCCL exchanges device tensors, gloo host ones."""
+    import torch
+    import torch.distributed as dist
+
+    return torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" \
+        else torch.device("cpu")
+
+
 def all_to_all_records(parts: list[np.ndarray], group=None) -> list[np.ndarray]:
     """parts[r] goes to rank r; returns the parts every rank sent here (in rank order)."""
     import torch
     import torch.distributed as dist
 
     world = dist.get_world_size(group)
+    dev = _device(group)
     words = RECORD.itemsize // 8
-    send_counts = torch.tensor([len(p) for p in parts], dtype=torch.int64)
-    recv_counts = torch.empty(world, dtype=torch.int64)
+    send_counts = torch.tensor([len(p) for p in parts], dtype=torch.int64, device=dev)
+    recv_counts = torch.empty(world, dtype=torch.int64, device=dev)
     dist.all_to_all_single(recv_counts, send_counts, group=group)
-    send = _as_i64(np.concatenate(parts) if sum(len(p) for p in parts) else np.zeros(0, RECORD))
-    recv = torch.empty(int(recv_counts.sum()) * words, dtype=torch.int64)
+    recv_counts = recv_counts.cpu()
+    send = _as_i64(np.concatenate(parts) if sum(len(p) for p in parts) else np.zeros(0, RECORD)).to(dev)
+    recv = torch.empty(int(recv_counts.sum()) * words, dtype=torch.int64, device=dev)
     dist.all_to_all_single(recv, send, output_split_sizes=[int(c) * words for c in recv_counts],
-                           input_split_sizes=[int(c) * words for c in send_counts], group=group)
-    flat = recv.numpy().view(RECORD)
+                           input_split_sizes=[int(c) * words for c in send_counts.cpu()], group=group)
+    flat = recv.cpu().numpy().view(RECORD)
     offs = np.concatenate([[0], np.cumsum(recv_counts.numpy())])
     return [flat[offs[r]:offs[r + 1]] for r in range(world)]
 
@@ -116,17 +127,19 @@ def all_gather_cells(cells: np.ndarray, group=None) -> list[np.ndarray]:
     import torch.distributed as dist
 
     world = dist.get_world_size(group)
-    n = torch.tensor([len(cells)], dtype=torch.int64)
-    sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+    dev = _device(group)
+    n = torch.tensor([len(cells)], dtype=torch.int64, device=dev)
+    sizes = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(world)]
     dist.all_gather(sizes, n, group=group)
-    top = max(int(s.item()) for s in sizes)
+    sizes = [int(x.item()) for x in sizes]
+    top = max(sizes)
     buf = np.zeros(top, dtype=CELL)
     buf[:len(cells)] = cells
     words = CELL.itemsize // 4
-    mine = torch.from_numpy(buf.view(np.int32).reshape(-1).copy())
-    got = [torch.zeros(top * words, dtype=torch.int32) for _ in range(world)]
+    mine = torch.from_numpy(buf.view(np.int32).reshape(-1).copy()).to(dev)
+    got = [torch.zeros(top * words, dtype=torch.int32, device=dev) for _ in range(world)]
     dist.all_gather(got, mine, group=group)
-    return [g.numpy().view(CELL)[:int(s.item())] for g, s in zip(got, sizes)]
+    return [g.cpu().numpy().view(CELL)[:k] for g, k in zip(got, sizes)]
 
 
 def step(backend, vertices, P: int, D: int, group=None):
