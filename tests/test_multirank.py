@@ -215,3 +215,17 @@ def test_owner_partition_is_total_and_balanced():
         counts = np.bincount(own, minlength=world)
         assert counts.sum() == len(keys)
         assert counts.min() > 0.9 * len(keys) / world
+
+
+def test_exchange_tensors_follow_the_backend(monkeypatch):
+    """NCCL exchanges device tensors, gloo host ones."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2005_07547_b300 import shard
+
+    monkeypatch.setattr(dist, "get_backend", lambda group=None: "gloo")
+    assert shard._device(None) == torch.device("cpu")
+    monkeypatch.setattr(dist, "get_backend", lambda group=None: "nccl")
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 3)
+    assert shard._device(None) == torch.device("cuda", 3)
