@@ -371,6 +371,10 @@ typedef struct {
     uint32_t barrier_timeout_us;  /* bound on each grid-barrier wait (0 = 2,000,000) */
     uint32_t test_phantom_blocks; /* testing only: each barrier also waits for this many blocks that
                                      do not exist, so every wait runs out (0 in normal use) */
+    uint32_t phase_blocks_per_sm[3]; /* blocks per SM that work in the insert, blend and query phases
+                                        (0 = every resident block; the others wait at the next
+                                        barrier): fewer warps on a scattered phase contend less for
+                                        the same lines.  Results do not depend on them. */
 } psf_batch_config;
 
 typedef struct psf_batch psf_batch;

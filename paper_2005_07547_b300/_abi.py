@@ -121,6 +121,7 @@ class BatchConfig(ctypes.Structure):
         ("blocks_per_sm", ctypes.c_uint32),
         ("barrier_timeout_us", ctypes.c_uint32),
         ("test_phantom_blocks", ctypes.c_uint32),
+        ("phase_blocks_per_sm", ctypes.c_uint32 * 3),
     ]
 
 

@@ -38,7 +38,8 @@ TABLE_SPACE = {
     "update_blocks_per_sm": (0, 2),
     "query_layout": (0, 1),
 }
-BATCH_SPACE = {"insert_mode": (0, 1), "blocks_per_sm": (0, 3, 2)}
+BATCH_SPACE = {"insert_mode": (0, 1), "blocks_per_sm": (0, 3, 2), "update_blocks_per_sm": (0, 2),
+               "query_blocks_per_sm": (0, 2)}
 
 
 def _time_ms(fn, iters: int) -> float:

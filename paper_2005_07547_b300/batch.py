@@ -15,9 +15,14 @@ from .table import _check_vertices, _stream_handle
 
 class Batch:
     def __init__(self, max_items: int, insert_mode: int = 0, blocks_per_sm: int = 0, barrier_timeout_us: int = 0,
-                 test_phantom_blocks: int = 0):
+                 test_phantom_blocks: int = 0, insert_blocks_per_sm: int = 0, update_blocks_per_sm: int = 0,
+                 query_blocks_per_sm: int = 0):
+        """insert/update/query_blocks_per_sm: how many of the resident blocks per SM work in that
+        phase of the fused kernel (0: all of them)."""
         self.max_items = max_items
-        self.cfg = _abi.BatchConfig(insert_mode, blocks_per_sm, barrier_timeout_us, test_phantom_blocks)
+        self.cfg = _abi.BatchConfig(insert_mode, blocks_per_sm, barrier_timeout_us, test_phantom_blocks,
+                                    (ctypes.c_uint32 * 3)(insert_blocks_per_sm, update_blocks_per_sm,
+                                                          query_blocks_per_sm))
         h = ctypes.c_void_p()
         _abi.check(_abi.load().psf_batch_create(max_items, ctypes.byref(self.cfg), ctypes.byref(h)), "psf_batch_create")
         self._h = h

@@ -47,7 +47,9 @@ struct BatchHdr {  // written by psf_batch_set
     unsigned phantom;
     unsigned long long timeout_ns;
     unsigned long long units[3];  // warp units per phase
-    unsigned long long pad[27];
+    unsigned active_blocks[3];    // blocks that work in each phase (the first ones: a few per SM)
+    unsigned pad2;
+    unsigned long long pad[25];
 };
 static_assert(sizeof(BatchHdr) == 256, "batch header is 256 bytes");
 
@@ -99,6 +101,15 @@ __device__ __forceinline__ void load_begin(unsigned long long* s_begin, const un
     __syncthreads();
 }
 
+// Blocks that work in each phase: cap blocks per SM (of the per_sm resident ones) times the SMs,
+// or 0 (all of them) when there is no cap below per_sm.
+void phase_blocks(const psf_batch_config& c, int sms, int per_sm, unsigned out[3]) {
+    for (int ph = 0; ph < 3; ++ph) {
+        const unsigned cap = c.phase_blocks_per_sm[ph];
+        out[ph] = cap && static_cast<int>(cap) < per_sm ? cap * static_cast<unsigned>(sms) : 0u;
+    }
+}
+
 // Table owning warp unit u: the last i with begin[i] <= u (tables without units are skipped).
 __device__ __forceinline__ unsigned find_item(const unsigned long long* s_begin, unsigned n, unsigned long long u) {
     unsigned lo = 0, hi = n;
@@ -123,11 +134,17 @@ __global__ void __launch_bounds__(kThreads)
     if (n == 0) return;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long warp = (static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const unsigned long long nwarps = (static_cast<unsigned long long>(gridDim.x) * blockDim.x) >> 5;
+    // a phase runs on its first active_blocks[p] blocks (all when 0); the others go straight to
+    // the barrier that ends it
+    auto phase_warps = [h](int p) {
+        const unsigned a = h->active_blocks[p] && h->active_blocks[p] < gridDim.x ? h->active_blocks[p] : gridDim.x;
+        return (static_cast<unsigned long long>(a) * blockDim.x) >> 5;
+    };
+    unsigned long long nwarps = phase_warps(0);
 
     // phase 1: scatter every table's vertices
     load_begin(s_begin, begin, n);
-    for (unsigned long long u = warp; u < h->units[0]; u += nwarps) {
+    for (unsigned long long u = warp; warp < nwarps && u < h->units[0]; u += nwarps) {
         const unsigned it = find_item(s_begin, n, u);
         const BatchItemDev& b = items[it];
         const unsigned long long i = (u - s_begin[it]) * 32ull + lane;
@@ -160,7 +177,8 @@ __global__ void __launch_bounds__(kThreads)
 
     // phase 2: blend every table's touched cells
     load_begin(s_begin, begin + (kMaxItems + 1), n);
-    for (unsigned long long u = warp; u < h->units[1]; u += nwarps) {
+    nwarps = phase_warps(1);
+    for (unsigned long long u = warp; warp < nwarps && u < h->units[1]; u += nwarps) {
         const unsigned it = find_item(s_begin, n, u);
         const BatchItemDev& b = items[it];
         const unsigned long long w0 = (u - s_begin[it]) * 32ull;
@@ -176,7 +194,8 @@ __global__ void __launch_bounds__(kThreads)
 
     // phase 3: every table's control-variate query
     load_begin(s_begin, begin + 2 * (kMaxItems + 1), n);
-    for (unsigned long long u = warp; u < h->units[2]; u += nwarps) {
+    nwarps = phase_warps(2);
+    for (unsigned long long u = warp; warp < nwarps && u < h->units[2]; u += nwarps) {
         const unsigned it = find_item(s_begin, n, u);
         const BatchItemDev& b = items[it];
         const unsigned long long p = (u - s_begin[it]) * 32ull + lane;
@@ -201,6 +220,7 @@ struct psf_batch {
     int device;
     int sms;
     int per_sm[2];
+    unsigned phase_active[3];  // blocks that work in each phase (0: all)
 };
 
 extern "C" {
@@ -211,7 +231,7 @@ int psf_batch_create(uint32_t max_items, const psf_batch_config* cfg, psf_batch*
     psf_batch* b = new (std::nothrow) psf_batch();
     if (!b) return PSF_ERR_NO_MEM;
     b->max_items = max_items;
-    b->cfg = cfg ? *cfg : psf_batch_config{0u, 0u, 0u, 0u};
+    b->cfg = cfg ? *cfg : psf_batch_config{};
     if (b->cfg.insert_mode > 1) {
         delete b;
         return PSF_ERR_INVALID_ARG;
@@ -248,6 +268,9 @@ int psf_batch_create(uint32_t max_items, const psf_batch_config* cfg, psf_batch*
         delete b;
         return PSF_ERR_CUDA;
     }
+    int per_sm = b->per_sm[b->cfg.insert_mode == 1 ? 1 : 0];
+    if (b->cfg.blocks_per_sm && static_cast<int>(b->cfg.blocks_per_sm) < per_sm) per_sm = static_cast<int>(b->cfg.blocks_per_sm);
+    phase_blocks(b->cfg, b->sms, per_sm, b->phase_active);
     *out = b;
     return PSF_OK;
 }
@@ -269,6 +292,7 @@ int psf_batch_set(psf_batch* b, const psf_batch_item* items, uint32_t n, void* s
     BatchItemDev* dev = reinterpret_cast<BatchItemDev*>(b->h_stage + sizeof(BatchCtl) + sizeof(BatchHdr) + kBeginBytes);
     h->n = n;
     h->phantom = b->cfg.test_phantom_blocks;
+    for (int ph = 0; ph < 3; ++ph) h->active_blocks[ph] = b->phase_active[ph];
     h->timeout_ns = 1000ull * (b->cfg.barrier_timeout_us ? b->cfg.barrier_timeout_us : 2000000u);
     unsigned long long acc[3] = {0, 0, 0};
     for (uint32_t i = 0; i < n; ++i) {
@@ -407,7 +431,7 @@ extern "C" int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, c
         return PSF_ERR_TOO_MANY;
     }
     if (n && !items) return PSF_ERR_INVALID_ARG;
-    const psf_batch_config c = cfg ? *cfg : psf_batch_config{0u, 0u, 0u, 0u};
+    const psf_batch_config c = cfg ? *cfg : psf_batch_config{};
     if (c.insert_mode > 1) return PSF_ERR_INVALID_ARG;
     for (uint32_t i = 0; i < n; ++i) {
         const psf_batch_item& it = items[i];
@@ -431,6 +455,11 @@ extern "C" int psf_batch_step_noalloc(const psf_batch_item* items, uint32_t n, c
     std::memset(h, 0, sizeof(BatchHdr));
     h->n = n;
     h->phantom = c.test_phantom_blocks;
+    {
+        int per_sm = g_noalloc_per_sm[dev][c.insert_mode == 1 ? 1 : 0];
+        if (c.blocks_per_sm && static_cast<int>(c.blocks_per_sm) < per_sm) per_sm = static_cast<int>(c.blocks_per_sm);
+        phase_blocks(c, g_noalloc_sms[dev], per_sm, h->active_blocks);
+    }
     h->timeout_ns = 1000ull * (c.barrier_timeout_us ? c.barrier_timeout_us : 2000000u);
     unsigned long long acc[3] = {0, 0, 0};
     for (uint32_t i = 0; i < n; ++i) {

@@ -62,6 +62,8 @@ int main(void) {
   printf("shrec %zu %zu %zu\n", sizeof(psf_sh_cell_record), offsetof(psf_sh_cell_record, c_old),
          offsetof(psf_sh_cell_record, coef));
   printf("config2 %zu %zu\n", offsetof(psf_config, payload), offsetof(psf_config, sh_ridge));
+  printf("batchcfg %zu %zu\n", sizeof(psf_batch_config), offsetof(psf_batch_config, phase_blocks_per_sm));
+  printf("launch %zu %zu\n", sizeof(psf_launch_config), offsetof(psf_launch_config, query_layout));
   return 0;
 }
 """)
@@ -79,6 +81,10 @@ int main(void) {
     h = _abi.SH_CELL_DTYPE
     assert lines["shrec"].split() == [str(x) for x in (h.itemsize, h.fields["c_old"][1], h.fields["coef"][1])]
     assert lines["config2"].split() == [str(x) for x in (C.payload.offset, C.sh_ridge.offset)]
+    B = _abi.BatchConfig
+    assert lines["batchcfg"].split() == [str(x) for x in (ctypes.sizeof(B), B.phase_blocks_per_sm.offset)]
+    Lc = _abi.LaunchConfig
+    assert lines["launch"].split() == [str(x) for x in (ctypes.sizeof(Lc), Lc.query_layout.offset)]
 
 
 def test_table_bytes_and_config_validation(lib):
