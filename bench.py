@@ -392,6 +392,52 @@ def _oracle_leg(job: dict) -> dict:
     }
 
 
+def _oracle_sessions_worker(args):
+    """One host core's share of the batched sessions: generate their first iteration, wait for
+    every worker, then run the oracle's insert + update + query on each (timed)."""
+    sessions, barrier, out = args
+    import oracle
+    from synth.scene import iteration_vertices
+
+    data = [iteration_vertices(s, 0) for s in sessions]
+    barrier.wait()
+    t0 = time.time()
+    n = 0
+    for s, v in zip(sessions, data):
+        o = oracle.Oracle(pos_bits=s["pos_bits"], dir_bits=s["dir_bits"], alpha_min=float(np.float32(s["alpha_min"])))
+        o.insert(v)
+        o.update()
+        o.query_cv(v, s["width"] * s["height"], s["depth"])
+        n += v.shape[0]
+    out.put((n, t0, time.time()))
+
+
+def oracle_sessions_aggregate(sessions: list[dict], procs: int) -> dict:
+    """The oracle over independent sessions on all host cores (one iteration of every session,
+    dealt to `procs` spawned workers largest first, each to the least loaded): vertices over the
+    wall time from the common start to the last worker's end."""
+    ctx = mp.get_context("spawn")
+    shares: list[list[dict]] = [[] for _ in range(max(1, min(procs, len(sessions))))]
+    load = [0] * len(shares)
+    for s in sorted(sessions, key=lambda s: -s["width"] * s["height"] * s["depth"]):
+        k = load.index(min(load))  # longest job first onto the least loaded worker
+        shares[k].append(s)
+        load[k] += s["width"] * s["height"] * s["depth"]
+    barrier = ctx.Barrier(len(shares))
+    out = ctx.Queue()
+    workers = [ctx.Process(target=_oracle_sessions_worker, args=((sh, barrier, out),)) for sh in shares]
+    for w in workers:
+        w.start()
+    res = [out.get() for _ in workers]
+    for w in workers:
+        w.join()
+    n = sum(r[0] for r in res)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    return {"value": n / wall, "unit": UNIT, "cores": len(shares), "kind": "oracle",
+            "sample": f"iteration 0 of all {len(sessions)} sessions ({n} vertices), std::map oracle, insert+update+query, "
+                      f"sessions dealt to {len(shares)} processes largest first onto the least loaded, {wall:.1f} s wall"}
+
+
 def precision_report(psf, make_cfg, dev: list, P: int, D: int, leg: dict, slot_cache: bool) -> dict:
     """Each query cache's error against the FP64 oracle after the oracle leg's iterations: fresh
     tables run the same batches with the benchmark's calls; keys and counters must match
@@ -697,6 +743,8 @@ def run_psf(args) -> None:
         line["fp32_cache" if fp16 else "fp16_cache"] = other
     if sessions_host is not None:
         line["batched_sessions"] = measure_sessions(args, sessions_host, local)
+        line["batched_sessions"]["cpu_baseline"] = oracle_sessions_aggregate(sessions_host["sessions"],
+                                                                             min(os.cpu_count() or 1, 32))
     if leg_proc is not None:
         leg = leg_proc.get()
         leg_pool.close()
@@ -950,6 +998,8 @@ def run_sessions(args) -> None:
     line.update({k: r[k] for k in ("latency_ms", "plain_loop", "plain_graph", "speedup_vs_plain_loop",
                                    "speedup_vs_plain_graph", "roofline", "identical_to_plain", "status", "autotune",
                                    "gpu_launches", "clocks")})
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sessions_aggregate(gen["sessions"], min(os.cpu_count() or 1, 32))
     if rank == 0:
         print(json.dumps(line), flush=True)
 

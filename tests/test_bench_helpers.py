@@ -41,3 +41,15 @@ def test_sh_payload_bytes_per_launch():
     V, C = 1000, 300
     assert bench.algorithmic_bytes(V, C, cache_fp16=False, payload=1) == {
         "k_insert": 64 * V + 264 * C, "k_update": 320 * C, "k_query": 76 * V + 32 * C}
+
+
+def test_oracle_sessions_aggregate_counts_every_vertex():
+    """The batched line's CPU baseline runs every session once across spawned workers."""
+    import bench
+
+    ses = [dict(name=f"s{k}", width=w, height=(9 * w) // 16, depth=d, iterations=1, log2_capacity=16, pos_bits=6,
+                dir_bits=3, alpha_min=0.1, radiance="glossy", seed=77 + k, camera_step=0.0, camera_x0=0.5,
+                cache_fp16=True, vertices=w * ((9 * w) // 16) * d) for k, (w, d) in enumerate([(64, 2), (48, 3), (32, 4)])]
+    r = bench.oracle_sessions_aggregate(ses, 2)
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["value"] > 0
+    assert f"({sum(s['vertices'] for s in ses)} vertices)" in r["sample"]
