@@ -66,9 +66,9 @@ def aggregate(per_rank_ms: list[float], vertices_per_step_per_rank: int, steps: 
     return {"ms_per_step": t_ms / steps, "value": total / (t_ms / 1e3)}
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in sources or KERNEL_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -111,16 +111,20 @@ def load_peaks() -> dict:
 
 def load_traffic(kernel: str, staged: bool, setup: dict) -> float | None:
     """DRAM bytes per launch from the committed ncu summary, if it was captured on the same
-    kernels (source hash) and the same setup (workload, cache, levels, capacity); the insert
-    with staged vertex tiles is the kernel k_insert_staged."""
+    kernels (source hash: the file's own, or a capture's own over the sources it lists) and the
+    same setup (workload, cache, levels, capacity, knobs); the insert with staged vertex tiles
+    is the kernel k_insert_staged."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("kernel_source_hash") != kernel_source_hash():
-        return None
     for cap in d.get("captures", []):
+        if "sources" in cap:  # captured on other kernels (e.g. the fused batched one): its own hash
+            if cap.get("source_hash") != kernel_source_hash(cap["sources"]):
+                continue
+        elif d.get("kernel_source_hash") != kernel_source_hash():
+            continue
         if all(cap.get(k) == v for k, v in setup.items()):
             name = kernel + "_staged" if staged and kernel in ("k_insert", "k_query") else kernel
             k = cap.get("kernels", {}).get(name)
@@ -823,7 +827,7 @@ def generate_sessions(sessions: list[dict], pool: int) -> dict:
             "host": [[flat[it * len(sessions) + k] for it in range(pool)] for k in range(len(sessions))]}
 
 
-def measure_sessions(args, gen: dict, local: int) -> dict:
+def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
     """Uneven render sessions: one fused persistent launch per iteration (graph-replayed)
     against the plain per-session loop (three launches per session), eager and
     graph-captured, on the same resident iterations.  The fused kernel's roofline: its
@@ -864,10 +868,18 @@ def measure_sessions(args, gen: dict, local: int) -> dict:
         else:
             table.step(v, P, D, out=outs[i])
 
-    tuned = autotune.tune_batch(lambda bits=1: entries([psf.Table(cfg_of(s, bits)) for s in sessions], 0),
-                                len(sessions), space={**autotune.BATCH_SPACE, "capacity_bits": (1, 2)})
-    knobs = dict(tuned["best"])
-    bits = knobs.pop("capacity_bits")
+    if tune:
+        tuned = autotune.tune_batch(lambda bits=1: entries([psf.Table(cfg_of(s, bits)) for s in sessions], 0),
+                                    len(sessions), space={**autotune.BATCH_SPACE, "capacity_bits": (1, 2)})
+        knobs = dict(tuned["best"])
+        bits = knobs.pop("capacity_bits")
+    else:  # the flags' knobs (fixed launches, e.g. for a profiler capture)
+        tuned = {"all": None}
+        knobs = {"insert_mode": args.insert_mode, "blocks_per_sm": args.batch_blocks,
+                 "update_blocks_per_sm": args.update_blocks, "query_blocks_per_sm": args.query_blocks}
+        if args.insert_blocks:
+            knobs["insert_blocks_per_sm"] = args.insert_blocks
+        bits = args.capacity_bits
     tables = [psf.Table(cfg_of(s, bits)) for s in sessions]
     batches = [psf.Batch(len(sessions), **knobs) for _ in range(pool)]
     for it, b in enumerate(batches):
@@ -939,8 +951,12 @@ def measure_sessions(args, gen: dict, local: int) -> dict:
                "k_update": bytes_phase["k_update"] / hbm, "k_query": bytes_phase["k_query"] / hbm}
     step_s = t_batch / args.steps / 1e3
     total_bytes = sum(bytes_phase.values())
+    setup = {"workload": f"sessions_{len(sessions)}", "slot_cache": bool(args.slot_cache), "capacity_bits": bits,
+             "batch_knobs": knobs}
     roofline = {"kernel": "k_batch", "bound": "hbm+l2_atomic (phase sum)",
                 "frac": sum(floor_s.values()) / step_s,
+                "traffic": load_traffic("k_batch", False, setup),
+                "algorithmic_bytes_per_launch": total_bytes,
                 "floor_ms": {k: 1e3 * v for k, v in floor_s.items()},
                 "hbm": {"achieved": total_bytes / step_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": total_bytes / step_s / hbm, "algorithmic_bytes_per_step": total_bytes,
@@ -987,7 +1003,7 @@ def run_sessions(args) -> None:
     import torch
 
     torch.cuda.set_device(local)
-    r = measure_sessions(args, gen, local)
+    r = measure_sessions(args, gen, local, tune=bool(args.tune))
     line = {
         "metric": METRIC + ", 64 batched sessions", "value": r["value"] * world, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
@@ -1131,9 +1147,11 @@ def main(argv=None) -> None:
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=60.0, help="serving: device memory for tables")
     ap.add_argument("--capacity-bits", type=int, default=1,
-                    help="serving: tables of 2^(ceil(log2 V) + bits) slots (the load factor the batched tuner picks)")
+                    help="serving, and sessions with --tune 0: tables of 2^(ceil(log2 V) + bits) slots")
     ap.add_argument("--tune", type=int, default=1,
                     help="1: pick grid caps and query layout with the autotuner before timing; 0: the flags' knobs")
+    ap.add_argument("--batch-blocks", type=int, default=0,
+                    help="sessions with --tune 0: resident blocks per SM of the fused kernel (0: occupancy)")
     ap.add_argument("--insert-blocks", type=int, default=0, help="cap on resident insert blocks per SM (0: occupancy)")
     ap.add_argument("--query-blocks", type=int, default=0, help="cap on resident query blocks per SM (0: occupancy)")
     ap.add_argument("--update-blocks", type=int, default=0, help="cap on resident blend blocks per SM (0: occupancy)")

@@ -53,3 +53,22 @@ def test_oracle_sessions_aggregate_counts_every_vertex():
     r = bench.oracle_sessions_aggregate(ses, 2)
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["value"] > 0
     assert f"({sum(s['vertices'] for s in ses)} vertices)" in r["sample"]
+
+
+def test_capture_with_its_own_sources_is_keyed_to_them(tmp_path, monkeypatch):
+    """A capture of another kernel (the fused batched one) carries the hash of its own sources:
+    it applies while they are unchanged, whatever the single-session kernels' hash says."""
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "k.cu").write_text("kernel v1")
+    setup = {"workload": "sessions_64", "slot_cache": True, "capacity_bits": 1,
+             "batch_knobs": {"insert_mode": 0, "blocks_per_sm": 0}}
+    d = {"kernel_source_hash": "stale", "captures": [
+        dict(setup, sources=["k.cu"], source_hash=bench.kernel_source_hash(["k.cu"]),
+             kernels={"k_batch": {"bytes_per_launch": 123.0}})]}
+    (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(d))
+    assert bench.load_traffic("k_batch", False, setup) == 123.0
+    assert bench.load_traffic("k_batch", False, dict(setup, capacity_bits=2)) is None
+    assert bench.load_traffic("k_batch", False, dict(setup, batch_knobs={"insert_mode": 1, "blocks_per_sm": 0})) is None
+    (tmp_path / "k.cu").write_text("kernel v2")
+    assert bench.load_traffic("k_batch", False, setup) is None
