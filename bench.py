@@ -1081,6 +1081,63 @@ def make_templates(depths=(2, 3, 4, 5, 6), widths=TEMPLATE_WIDTHS, iterations=2)
     return out
 
 
+def template_stats(src: "TemplateSource", reqs: list[dict]) -> dict:
+    """Touched cells and (warp, key) groups of every template iteration the trace reads, keyed
+    (width, depth, iteration mod n_iter): both depend only on the batch (its keys and their
+    order), not on the table's history or capacity, so one plain table per template counts
+    them (untimed, after the served runs)."""
+    import paper_2005_07547_b300 as psf
+    from paper_2005_07547_b300.serve import table_config
+
+    out = {}
+    for (w, d), its in src.templates.items():
+        r = next((q for q in reqs if (q["width"], q["depth"]) == (w, d)), None)
+        if r is None:
+            continue
+        t = psf.Table(table_config(r))
+        prev = {"touched_cells": 0, "leader_groups": 0}
+        for k, v in enumerate(its):
+            t.insert(v)
+            t.update()
+            st = t.stats()
+            out[(w, d, k)] = (st["touched_cells"] - prev["touched_cells"], st["leader_groups"] - prev["leader_groups"])
+            prev = st
+        t.close()
+    return out
+
+
+def served_roofline(tick_log: list, stats: dict, n_iter: int, hbm_bps: float, group_peak: float,
+                    fused: bool, slot_cache: bool) -> dict:
+    """Roofline of a served run from its completed ticks.  A tick's floor: fused (one kernel,
+    phases back to back) the sum over phases of that phase's floor over the tick's sessions;
+    plain (three kernels per session) the sum of every launch's own floor.  A phase's floor is
+    its algorithmic bytes at the HBM rate, and for the insert at least its (warp, key) groups at
+    the bulk-reduction probe's rate.  frac = total floor / total device time of the ticks;
+    device_busy = device time over the wall time is reported by the caller."""
+    floor = dev_ms = total_bytes = groups_all = 0.0
+    for tick in tick_log:
+        dev_ms += tick["ms"]
+        ph = {"k_insert": 0.0, "k_update": 0.0, "k_query": 0.0}
+        groups = 0.0
+        for req, it, _ in tick["items"]:
+            touched, g = stats[(req["width"], req["depth"], it % n_iter)]
+            b = algorithmic_bytes(req["width"] * req["height"] * req["depth"], touched, True, slot_cache)
+            if fused:
+                for k in ph:
+                    ph[k] += b[k]
+                groups += g
+            else:
+                floor += max(b["k_insert"] / hbm_bps, g / group_peak) + (b["k_update"] + b["k_query"]) / hbm_bps
+            total_bytes += sum(b.values())
+            groups_all += g
+        if fused:
+            floor += max(ph["k_insert"] / hbm_bps, groups / group_peak) + (ph["k_update"] + ph["k_query"]) / hbm_bps
+    dev_s = dev_ms / 1e3
+    return {"frac": floor / dev_s if dev_s > 0 else None, "floor_ms": 1e3 * floor, "device_ms": dev_ms,
+            "ticks": len(tick_log), "algorithmic_bytes": total_bytes, "groups": groups_all,
+            "hbm_achieved_GBps": total_bytes / dev_s / 1e9 if dev_s > 0 else None}
+
+
 def run_serving(args) -> None:
     """Poisson arrivals at --rate per second for --duration seconds, 60 GB table budget:
     the continuous-batching server against the plain per-session loop on the same trace."""
@@ -1098,16 +1155,38 @@ def run_serving(args) -> None:
     psf.load()
     src = TemplateSource(templates)
     reqs = [src.fit(r) for r in reqs]
-    reports = {}
+    reports, logs = {}, {}
     for mode in ("batched", "plain"):
         srv = Server(src, budget_bytes=args.budget_gb * 1e9, mode=mode, slot_cache=bool(args.slot_cache),
-                     capacity_bits=args.capacity_bits)
+                     capacity_bits=args.capacity_bits, log_ticks=True)
         with ClockSampler(local) as clocks:
             rep = srv.run(reqs, args.duration)
         rep["clocks"] = clocks.summary()
+        logs[mode] = srv.tick_log
         srv.close()
         torch.cuda.synchronize()
         reports[mode] = rep
+    # the rooflines (untimed): every template iteration's touched cells and groups, and the
+    # bulk-reduction probe on the batched run's mean live footprint
+    stats = template_stats(src, reqs)
+    n_iter = len(next(iter(templates.values())))
+    ticks = logs["batched"] or logs["plain"]
+    slot_bytes = sum(sum(64 << c for _, _, c in t["items"]) for t in ticks) / max(1, len(ticks))
+    touched = sum(sum(stats[(q["width"], q["depth"], it % n_iter)][0] for q, it, _ in t["items"]) for t in ticks) \
+        / max(1, len(ticks))
+    probe = atomic_probe_rates(modes=(4,), n_words=max(1 << 20, int(slot_bytes) // 8), n_distinct=max(1, int(touched)))
+    group_peak = probe["insert_pattern_bulk32_1or"] / 5.0
+    hbm = load_peaks()["hbm_gbs"] * 1e9
+    for mode, rep in reports.items():
+        rl = served_roofline(logs[mode], stats, n_iter, hbm, group_peak, mode == "batched", bool(args.slot_cache))
+        rl.update({"kernel": "k_batch" if mode == "batched" else "k_insert + k_update + k_query per session",
+                   "bound": "hbm+l2_atomic (phase sum per tick)" if mode == "batched" else
+                            "hbm+l2_atomic (sum over launches)",
+                   "device_busy": rl["device_ms"] / 1e3 / rep["wall_s"] if rep["wall_s"] else None,
+                   "peak_note": f"of measured (MEASURED_PEAKS.json hbm_gbs; live bulk-reduction probe "
+                                f"{group_peak / 1e9:.1f} G groups/s on the mean live footprint, "
+                                f"{int(touched)} distinct sectors of {slot_bytes / 1e9:.1f} GB)"})
+        rep["roofline"] = rl
     b, p = reports["batched"], reports["plain"]
     line = {
         "metric": METRIC + ", served sessions", "value": b["vertices_per_s"] * world, "unit": UNIT, "n_gpus": world,
@@ -1117,7 +1196,7 @@ def run_serving(args) -> None:
         "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.duration} s, sessions of 16..128 iterations, "
                                "width log-uniform 128..1280 mapped to the nearest template, depth U{2..6}",
                    "requests": len(reqs), "budget_gb": args.budget_gb, "templates": len(templates)},
-        "batched": b, "plain": p,
+        "batched": b, "plain": p, "roofline": b["roofline"],
         "throughput_ratio_batched_over_plain": b["vertices_per_s"] / p["vertices_per_s"] if p["vertices_per_s"] else None,
     }
     if rank == 0:

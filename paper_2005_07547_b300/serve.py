@@ -72,13 +72,16 @@ def table_bytes(req: dict, capacity_bits: int | None = None) -> int:
 class Server:
     def __init__(self, vertex_source, budget_bytes: float = 60e9, max_live: int = _abi.MAX_BATCH,
                  mode: str = "batched", use_graph: bool = True, batch_knobs: dict | None = None,
-                 on_retire=None, slot_cache: bool = True, capacity_bits: int | None = None):
+                 on_retire=None, slot_cache: bool = True, capacity_bits: int | None = None,
+                 log_ticks: bool = False):
         """vertex_source(request, iteration) -> (P*D, 16) float32 CUDA tensor of that iteration;
         on_retire(session), if given, sees each session (table still open) before it is freed;
         slot_cache: each session's insert notes its vertices' slots and its query reads them
         (psf_insert_slots / psf_query_cv_slots, or the batch item's slots), in both modes;
         capacity_bits: each session's table gets 2^(ceil(log2 V) + capacity_bits) slots (the
-        load factor, e.g. autotune.tune_batch's choice) instead of its request's log2_capacity."""
+        load factor, e.g. autotune.tune_batch's choice) instead of its request's log2_capacity;
+        log_ticks: keep, per completed tick, its device time and the (request, iteration, log2
+        capacity) of every session it ran (`tick_log`, for a roofline of the served form)."""
         if mode not in ("batched", "plain"):
             raise ValueError("mode must be 'batched' or 'plain'")
         self.source = vertex_source
@@ -97,7 +100,8 @@ class Server:
         self.on_retire = on_retire
         self.slot_cache = slot_cache
         self.capacity_bits = capacity_bits
-        self._inflight: deque = deque()  # (start event, end event(s), sessions, retiring sessions)
+        self._inflight: deque = deque()  # (start event, end event(s), sessions, retiring sessions, items)
+        self.tick_log: list | None = [] if log_ticks else None
 
     # -- membership ---------------------------------------------------------------------
     def _admit(self, queue: deque, now: float) -> bool:
@@ -139,8 +143,10 @@ class Server:
         """Wait for all but the newest `keep` ticks; record their latencies and free the
         tables of the sessions they retired."""
         while len(self._inflight) > keep:
-            start, ends, sessions, retiring = self._inflight.popleft()
+            start, ends, sessions, retiring, items = self._inflight.popleft()
             ends[-1].synchronize()
+            if self.tick_log is not None:
+                self.tick_log.append({"ms": start.elapsed_time(ends[-1]), "items": items})
             for s, e in zip(sessions, ends if len(ends) == len(sessions) else [ends[-1]] * len(sessions)):
                 s.latencies_ms.append(start.elapsed_time(e))
             for s in retiring:
@@ -192,11 +198,13 @@ class Server:
                 e = torch.cuda.Event(enable_timing=True)
                 e.record()
                 ends.append(e)
+        items = [(s.request, s.done, int(s.table.cfg.log2_capacity)) for s in sessions] \
+            if self.tick_log is not None else None
         for s in sessions:
             s.done += 1
             self.vertices += s.P * s.D
         self.ticks += 1
-        self._inflight.append((start, ends, sessions, self._retire()))
+        self._inflight.append((start, ends, sessions, self._retire(), items))
         self._complete(keep=1)
 
     # -- driver ---------------------------------------------------------------------------

@@ -72,3 +72,30 @@ def test_capture_with_its_own_sources_is_keyed_to_them(tmp_path, monkeypatch):
     assert bench.load_traffic("k_batch", False, dict(setup, batch_knobs={"insert_mode": 1, "blocks_per_sm": 0})) is None
     (tmp_path / "k.cu").write_text("kernel v2")
     assert bench.load_traffic("k_batch", False, setup) is None
+
+
+def test_served_roofline_floors():
+    """The served form's floor per tick: fused, the phase sums over the tick's sessions; plain,
+    the sum of every launch's own floor (never below the fused one)."""
+    a = dict(width=4, height=2, depth=2)  # V = 16
+    b = dict(width=8, height=2, depth=1)  # V = 16
+    stats = {(4, 2, 0): (10, 1000), (4, 2, 1): (12, 1000), (8, 1, 0): (6, 2), (8, 1, 1): (6, 2)}
+    log = [{"ms": 2.0, "items": [(a, 0, 8), (b, 0, 8)]}, {"ms": 1.0, "items": [(a, 3, 8)]}]
+    hbm, gp = 1e3, 1e3  # bytes/s, groups/s
+    fused = bench.served_roofline(log, stats, 2, hbm, gp, True, True)
+    plain = bench.served_roofline(log, stats, 2, hbm, gp, False, True)
+
+    def ab(V, C):
+        return bench.algorithmic_bytes(V, C, True, True)
+
+    a0, b0, a1 = ab(16, 10), ab(16, 6), ab(16, 12)
+    t0 = max((a0["k_insert"] + b0["k_insert"]) / hbm, 1002 / gp) + (a0["k_update"] + b0["k_update"] + a0["k_query"]
+                                                                   + b0["k_query"]) / hbm
+    t1 = max(a1["k_insert"] / hbm, 1000 / gp) + (a1["k_update"] + a1["k_query"]) / hbm
+    assert fused["floor_ms"] == pytest.approx(1e3 * (t0 + t1))
+    assert fused["frac"] == pytest.approx((t0 + t1) / 3e-3)
+    p0 = (max(a0["k_insert"] / hbm, 1000 / gp) + (a0["k_update"] + a0["k_query"]) / hbm
+          + max(b0["k_insert"] / hbm, 2 / gp) + (b0["k_update"] + b0["k_query"]) / hbm)
+    assert plain["floor_ms"] == pytest.approx(1e3 * (p0 + t1))
+    assert plain["floor_ms"] >= fused["floor_ms"]
+    assert fused["groups"] == plain["groups"] == 2002 and fused["device_ms"] == 3.0

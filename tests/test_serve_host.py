@@ -43,6 +43,7 @@ class FakeTable:
     peak_bytes = 0
 
     def __init__(self, cfg):
+        self.cfg = cfg
         self.nbytes = 1000 * cfg.log2_capacity
         self.closed = False
         self.last_event = None  # the end event of the tick that last used this table
@@ -151,3 +152,22 @@ def test_batched_ticks_carry_every_live_session_and_its_slots(fakes):
     srv.close()
     assert counts and all(n == 6 for tick in counts for _, n in tick)  # slot cache: 6-element entries
     assert len(counts[0]) == len(reqs)  # all admitted at once under an ample budget
+
+
+@pytest.mark.parametrize("mode", ["batched", "plain"])
+def test_tick_log_records_every_iteration_once(fakes, mode):
+    """With log_ticks, every completed tick carries its device time and the (request,
+    iteration, log2 capacity) of each session it ran: every iteration of every session
+    appears exactly once, in order."""
+    reqs = _requests(5)
+    srv = _Server(lambda r, k: None, budget_bytes=1e9, mode=mode, use_graph=False, log_ticks=True)
+    srv.run(reqs, duration_s=60.0, drain=True)
+    assert len(srv.tick_log) == srv.ticks
+    seen = {}
+    for tick in srv.tick_log:
+        assert tick["ms"] > 0
+        for req, it, log2cap in tick["items"]:
+            assert log2cap == req["log2_capacity"]
+            assert it == seen.get(req["name"], -1) + 1
+            seen[req["name"]] = it
+    assert seen == {r["name"]: r["iterations"] - 1 for r in reqs}
