@@ -258,6 +258,7 @@ def atomic_probe_rates(modes=(0, 1, 2, 3, 4, 5), n_words: int = 1 << 25, reps: i
     lib.atomic_probe.restype = ctypes.c_int
     lib.atomic_probe.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_void_p]
+    n_words = max(128, int(n_words) // 128 * 128)  # whole 1-KB blocks (the probe wants a multiple of 4 words)
     buf = torch.zeros(n_words * 8 + (n_words // 128) * 4, dtype=torch.uint8, device="cuda")
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     stream = torch.cuda.current_stream()
@@ -698,6 +699,11 @@ def run_psf(args) -> None:
              "slot_cache": bool(args.slot_cache)}
     if sh:
         setup["payload"] = "sh"
+    # launch choices other than the defaults the counters were taken with name themselves, so
+    # that no committed capture matches them
+    for knob in ("key_layout", "insert_mode", "sum_reduction"):
+        if getattr(args, knob):
+            setup[knob] = getattr(args, knob)
     roofline = {"kernel": dominant, "traffic": load_traffic(dominant, staged, setup), "hbm": hbm}
     binding = hbm
     roofline["bound"] = "hbm"
