@@ -595,7 +595,7 @@ def run_psf(args) -> None:
     # coarse levels add few cells (measured live cells over the flat table's: 1.26x at 2
     # levels, 1.35x at 4), so the workload's capacity serves every level count
     log2cap = w["log2_capacity"]
-    fp16 = bool(args.fp16 or w["cache_fp16"])
+    fp16 = bool(args.fp16 or w["cache_fp16"]) and not args.fp32
 
     sh = args.payload == "sh"
     if sh:  # the SH payload keeps no FP16 copy; the paper's 5-d key
@@ -855,7 +855,7 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
         # the cell grid q stays the session's, so every choice gives the same cells
         log2cap = int(math.ceil(math.log2(s["width"] * s["height"] * s["depth"]))) + bits
         return psf.make_config(log2_capacity=log2cap, pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
-                               alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"])
+                               alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"], key_layout=args.key_layout)
 
     outs = [torch.empty((d[0].shape[0], 3), device="cuda") for d in dev]
     # the slot cache (the default): each session's insert notes its vertices' slots and its
@@ -959,6 +959,8 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
     total_bytes = sum(bytes_phase.values())
     setup = {"workload": f"sessions_{len(sessions)}", "slot_cache": bool(args.slot_cache), "capacity_bits": bits,
              "batch_knobs": knobs}
+    if args.key_layout:
+        setup["key_layout"] = args.key_layout
     roofline = {"kernel": "k_batch", "bound": "hbm+l2_atomic (phase sum)",
                 "frac": sum(floor_s.values()) / step_s,
                 "traffic": load_traffic("k_batch", False, setup),
@@ -1217,6 +1219,7 @@ def main(argv=None) -> None:
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--impl", default="psf", choices=["psf", "reference"])
     ap.add_argument("--fp16", action="store_true", help="FP16 copy of the approximant for the query")
+    ap.add_argument("--fp32", action="store_true", help="no FP16 copy: queries read the FP32 approximant")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--insert-mode", type=int, default=0, help="0: warp aggregation of equal keys; 1: none")
