@@ -109,6 +109,22 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6400.0, "source": "fallback"}
 
 
+def key_layout_of(cfg) -> str:
+    """Where the library lays out a configuration's keys: "inline" (inside the 64-byte slot
+    records) or "dense" (an 8-byte array beside them, which adds 8 bytes per slot to the table
+    size); read from psf_table_bytes, so the library's own rule decides."""
+    import ctypes
+
+    from paper_2005_07547_b300 import _abi
+
+    lib = _abi.load()
+    inline = _abi.Config()
+    ctypes.memmove(ctypes.byref(inline), ctypes.byref(cfg), ctypes.sizeof(cfg))
+    inline.key_layout = 2
+    return "inline" if lib.psf_table_bytes(ctypes.byref(cfg)) == lib.psf_table_bytes(ctypes.byref(inline)) \
+        else "dense"
+
+
 def load_traffic(kernel: str, staged: bool, setup: dict) -> float | None:
     """DRAM bytes per launch from the committed ncu summary, if it was captured on the same
     kernels (source hash: the file's own, or a capture's own over the sources it lists) and the
@@ -601,9 +617,10 @@ def run_psf(args) -> None:
     if sh:  # the SH payload keeps no FP16 copy; the paper's 5-d key
         fp16 = False
 
-    def make_cfg(cache_fp16):
+    def make_cfg(cache_fp16, key_layout=None):
         return psf.make_config(log2_capacity=log2cap, pos_bits=w["pos_bits"], dir_bits=w["dir_bits"],
-                               alpha_min=w["alpha_min"], cache_fp16=cache_fp16, key_layout=args.key_layout,
+                               alpha_min=w["alpha_min"], cache_fp16=cache_fp16,
+                               key_layout=args.key_layout if key_layout is None else key_layout,
                                levels=args.levels, payload=1 if sh else 0, sh_ridge=args.sh_ridge,
                                use_normal=not sh)
 
@@ -613,24 +630,35 @@ def run_psf(args) -> None:
     dev = [torch.from_numpy(v).cuda() for v in host]
     tuned = {}
 
-    def knobs_for(cache_fp16):
-        """The launch knobs: the flags' values, or with --tune the autotuner's pick (grid caps and
-        query layout timed on this workload's first batches with the benchmark's own calls)."""
-        if not args.tune:
-            return dict(base_knobs)
+    def tune(cache_fp16):
+        """With --tune the autotuner's pick, timed on this workload's first batches with the
+        benchmark's own calls: grid caps, query layout and, unless --key-layout fixes it, where
+        the table keeps its keys."""
         if cache_fp16 not in tuned:
             from paper_2005_07547_b300 import autotune
 
             space = {"insert_blocks_per_sm": (0, 4), "query_blocks_per_sm": (0, 4, 2),
                      "update_blocks_per_sm": (0, 2, 1), "query_layout": (0, 1)}
+            if args.key_layout == 0 and not sh:
+                space["key_layout"] = (1, 2)
             res = autotune.tune_table(make_cfg(cache_fp16), dev[:min(6, len(dev))], P, D, space=space, warmup=2,
                                       iters=4, slot_cache=bool(args.slot_cache))
-            tuned[cache_fp16] = {"best": {**base_knobs, **res["best"]}, "best_ms": res["best_ms"],
-                                 "candidates": len(res["all"])}
-        return dict(tuned[cache_fp16]["best"])
+            best = dict(res["best"])
+            layout = best.pop("key_layout", args.key_layout)
+            tuned[cache_fp16] = {"best": {**base_knobs, **best}, "key_layout": layout, "best_ms": res["best_ms"],
+                                 "candidates": len(res["all"]), "space": "x".join(space)}
+        return tuned[cache_fp16]
+
+    def knobs_for(cache_fp16):
+        """The launch knobs: the flags' values, or with --tune the autotuner's pick."""
+        return dict(tune(cache_fp16)["best"]) if args.tune else dict(base_knobs)
+
+    def cfg_for(cache_fp16):
+        """The timed table's configuration: the flag's key layout, or with --tune the tuner's."""
+        return make_cfg(cache_fp16, tune(cache_fp16)["key_layout"] if args.tune else None)
 
     def new_table(cache_fp16):
-        t = psf.Table(make_cfg(cache_fp16))
+        t = psf.Table(cfg_for(cache_fp16))
         t.set_launch(**knobs_for(cache_fp16))
         return t
 
@@ -699,9 +727,10 @@ def run_psf(args) -> None:
              "slot_cache": bool(args.slot_cache)}
     if sh:
         setup["payload"] = "sh"
+    setup["key_layout"] = key_layout_of(cfg_for(fp16))
     # launch choices other than the defaults the counters were taken with name themselves, so
     # that no committed capture matches them
-    for knob in ("key_layout", "insert_mode", "sum_reduction"):
+    for knob in ("insert_mode", "sum_reduction"):
         if getattr(args, knob):
             setup[knob] = getattr(args, knob)
     roofline = {"kernel": dominant, "traffic": load_traffic(dominant, staged, setup), "hbm": hbm}
@@ -734,11 +763,11 @@ def run_psf(args) -> None:
                    "insert_mode": args.insert_mode, "vertex_staging": args.staging,
                    "sum_reduction": {0: "bulk (TMA) 32-B reduction", 1: "4 x red.add.u64"}[args.sum_reduction],
                    "launch_knobs": knobs_for(fp16),
-                   "autotune": ({"space": "insert / query / update blocks per SM x query layout",
-                                 "candidates": tuned[fp16]["candidates"], "tuned_ms": tuned[fp16]["best_ms"]}
-                                if args.tune else None),
+                   "autotune": ({"space": tuned[fp16]["space"], "candidates": tuned[fp16]["candidates"],
+                                 "tuned_ms": tuned[fp16]["best_ms"]} if args.tune else None),
                    "slot_cache": bool(args.slot_cache),
-                   "key_layout": {0: "auto", 1: "dense key array", 2: "keys in slot records"}[args.key_layout],
+                   "key_layout": {"inline": "keys in the slot records", "dense": "dense key array"}[
+                       key_layout_of(cfg_for(fp16))],
                    "payload": ("YCoCg two-band SH over the normal, ridge %g, 5-d key" % args.sh_ridge) if sh else "RGB",
                    "parallelism": f"sessions x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -850,12 +879,12 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
     V = sum(s["width"] * s["height"] * s["depth"] for s in sessions)
     dev = [[torch.from_numpy(v).cuda() for v in gen["host"][k]] for k in range(len(sessions))]
 
-    def cfg_of(s, bits=1):
+    def cfg_of(s, bits=1, key_layout=args.key_layout):
         # the load factor: 2^(ceil(log2 V) + bits) slots (the workload's own sizing is bits = 1);
         # the cell grid q stays the session's, so every choice gives the same cells
         log2cap = int(math.ceil(math.log2(s["width"] * s["height"] * s["depth"]))) + bits
         return psf.make_config(log2_capacity=log2cap, pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
-                               alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"], key_layout=args.key_layout)
+                               alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"], key_layout=key_layout)
 
     outs = [torch.empty((d[0].shape[0], 3), device="cuda") for d in dev]
     # the slot cache (the default): each session's insert notes its vertices' slots and its
@@ -875,10 +904,16 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
             table.step(v, P, D, out=outs[i])
 
     if tune:
-        tuned = autotune.tune_batch(lambda bits=1: entries([psf.Table(cfg_of(s, bits)) for s in sessions], 0),
-                                    len(sessions), space={**autotune.BATCH_SPACE, "capacity_bits": (1, 2)})
+        space = {**autotune.BATCH_SPACE, "capacity_bits": (1, 2)}
+        if args.key_layout == 0:
+            space["key_layout"] = (1, 2)
+        tuned = autotune.tune_batch(
+            lambda capacity_bits=1, key_layout=args.key_layout:
+                entries([psf.Table(cfg_of(s, capacity_bits, key_layout)) for s in sessions], 0),
+            len(sessions), space=space)
         knobs = dict(tuned["best"])
         bits = knobs.pop("capacity_bits")
+        layout = knobs.pop("key_layout", args.key_layout)
     else:  # the flags' knobs (fixed launches, e.g. for a profiler capture)
         tuned = {"all": None}
         knobs = {"insert_mode": args.insert_mode, "blocks_per_sm": args.batch_blocks,
@@ -886,7 +921,8 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
         if args.insert_blocks:
             knobs["insert_blocks_per_sm"] = args.insert_blocks
         bits = args.capacity_bits
-    tables = [psf.Table(cfg_of(s, bits)) for s in sessions]
+        layout = args.key_layout
+    tables = [psf.Table(cfg_of(s, bits, layout)) for s in sessions]
     batches = [psf.Batch(len(sessions), **knobs) for _ in range(pool)]
     for it, b in enumerate(batches):
         b.set(entries(tables, it))
@@ -915,14 +951,14 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
         t_batch, per_batch = timed(lambda k: graphs[k % pool].replay(), args.warmup, args.steps)
     status = max(b.status() for b in batches)
 
-    plain_tables = [psf.Table(cfg_of(s, bits)) for s in sessions]
+    plain_tables = [psf.Table(cfg_of(s, bits, layout)) for s in sessions]
 
     def plain(k):
         for i, s in enumerate(sessions):
             plain_step(plain_tables[i], i, dev[i][k % pool], s["width"] * s["height"], s["depth"])
 
     t_plain, per_plain = timed(plain, args.warmup, args.steps)
-    graph_tables = [psf.Table(cfg_of(s, bits)) for s in sessions]
+    graph_tables = [psf.Table(cfg_of(s, bits, layout)) for s in sessions]
     plain_graphs = []
     for it in range(pool):
         g = torch.cuda.CUDAGraph()
@@ -959,8 +995,8 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
     total_bytes = sum(bytes_phase.values())
     setup = {"workload": f"sessions_{len(sessions)}", "slot_cache": bool(args.slot_cache), "capacity_bits": bits,
              "batch_knobs": knobs}
-    if args.key_layout:
-        setup["key_layout"] = args.key_layout
+    if layout:
+        setup["key_layout"] = {1: "dense", 2: "inline"}[layout]
     roofline = {"kernel": "k_batch", "bound": "hbm+l2_atomic (phase sum)",
                 "frac": sum(floor_s.values()) / step_s,
                 "traffic": load_traffic("k_batch", False, setup),
@@ -980,7 +1016,8 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
         "workload": f"{len(sessions)} sessions, width log-uniform 128..1280, 16:9, depth U{{2..6}}, FP16 cache",
         "value": rate(t_batch), "unit": UNIT, "ms_per_step": t_batch / args.steps, "vertices_per_step": V,
         "steps": args.steps, "warmup": args.warmup, "pool": pool, "batch_knobs": knobs,
-        "capacity": f"2^(ceil(log2 V) + {bits}) slots per session (autotuned load factor)",
+        "capacity": f"2^(ceil(log2 V) + {bits}) slots per session ({'autotuned' if tune else 'fixed'} load factor)",
+        "key_layout": {0: "auto", 1: "dense key array", 2: "keys in the slot records"}[layout],
         "slot_cache": bool(args.slot_cache),
         "l2": f"inputs larger than L2: {pool} distinct iterations of {V * 64 / 1e9:.1f} GB",
         "latency_ms": {"p50": float(np.percentile(per_batch, 50)), "p99": float(np.percentile(per_batch, 99))},
@@ -1017,7 +1054,8 @@ def run_sessions(args) -> None:
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64 fixed point", "data": "synthetic",
         "config": {"workload": r["workload"], "vertices_per_step": r["vertices_per_step"], "pool": r["pool"],
-                   "batch_knobs": r["batch_knobs"], "slot_cache": r["slot_cache"], "l2": r["l2"]},
+                   "batch_knobs": r["batch_knobs"], "capacity": r["capacity"], "key_layout": r["key_layout"],
+                   "slot_cache": r["slot_cache"], "l2": r["l2"]},
     }
     line.update({k: r[k] for k in ("latency_ms", "plain_loop", "plain_graph", "speedup_vs_plain_loop",
                                    "speedup_vs_plain_graph", "roofline", "identical_to_plain", "status", "autotune",
@@ -1165,8 +1203,10 @@ def run_serving(args) -> None:
     reqs = [src.fit(r) for r in reqs]
     reports, logs = {}, {}
     for mode in ("batched", "plain"):
+        # keys inside the slot records unless --key-layout says otherwise: the layout the batched
+        # tuner picks on the 64-session workload (like the load factor --capacity-bits 1)
         srv = Server(src, budget_bytes=args.budget_gb * 1e9, mode=mode, slot_cache=bool(args.slot_cache),
-                     capacity_bits=args.capacity_bits, log_ticks=True)
+                     capacity_bits=args.capacity_bits, log_ticks=True, key_layout=args.key_layout or 2)
         with ClockSampler(local) as clocks:
             rep = srv.run(reqs, args.duration)
         rep["clocks"] = clocks.summary()
@@ -1203,7 +1243,9 @@ def run_serving(args) -> None:
         "data": "synthetic",
         "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.duration} s, sessions of 16..128 iterations, "
                                "width log-uniform 128..1280 mapped to the nearest template, depth U{2..6}",
-                   "requests": len(reqs), "budget_gb": args.budget_gb, "templates": len(templates)},
+                   "requests": len(reqs), "budget_gb": args.budget_gb, "templates": len(templates),
+                   "capacity": f"2^(ceil(log2 V) + {args.capacity_bits}) slots per session",
+                   "key_layout": {1: "dense key array", 2: "keys in the slot records"}[args.key_layout or 2]},
         "batched": b, "plain": p, "roofline": b["roofline"],
         "throughput_ratio_batched_over_plain": b["vertices_per_s"] / p["vertices_per_s"] if p["vertices_per_s"] else None,
     }

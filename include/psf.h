@@ -100,10 +100,13 @@ typedef struct {
                                (the blend always keeps the FP32 master, which queries read otherwise) */
     uint32_t blend_mode;    /* 0: eq. (11) square-root blend; 1: constant alpha = alpha_min */
     uint32_t key_layout;    /* where the cell keys live: 1 = a dense 8-byte array, 2 = inside each 64-byte
-                               slot record (an FP32 query reads key and approximant from one sector),
-                               0 = 2 for FP32 tables up to 2^22 slots, else 1 (measured: larger tables
-                               keep more probes in L2 with the dense array, and FP16 queries read the
-                               dense keys beside the compact FP16 copy).  Results do not depend on it. */
+                               slot record (a probe's key shares the record's 64-byte half with the sums
+                               the insert adds to; an FP32 query reads key and approximant from one
+                               sector), 0 = 2 for FP32 tables up to 2^22 slots, else 1: the best choice
+                               for the probing query (psf_query_cv, psf_step), whose large tables keep
+                               more key reads in L2 with the dense array.  With the slot-cache calls
+                               (psf_insert_slots + psf_query_cv_slots) 2 was measured faster on every
+                               workload.  Results do not depend on it. */
     uint32_t levels;        /* hierarchy levels L, 0..4 (0 and 1: a flat table).  Section "Progressive
                                hierarchical solver": level l has cells 2^l times wider in position
                                (x_l = floor(px * 2^(q-l)) + 2^15, likewise y, z; the same normal and

@@ -8,11 +8,13 @@ checks that premise: every candidate has run the same iterations, and its tables
 maps (exported in key order) must be identical, bit for bit.
 
   tune_table(cfg, batches, P, D)   -> insert mode, vertex staging, sum path and per-kernel
-                                      grid caps for psf_step
+                                      grid caps for psf_step, and, when the space holds
+                                      "key_layout", where the table keeps its keys
   tune_capacity(cfg, batches, P, D)-> log2 capacity (load factor) for a session size
   tune_batch(make_entries, n)      -> insert mode, blocks/SM and, when the space holds
-                                      "capacity_bits", the sessions' load factor
-                                      (2^(ceil(log2 V) + bits) slots) for the batched kernel
+                                      "capacity_bits" / "key_layout", the sessions' load
+                                      factor (2^(ceil(log2 V) + bits) slots) and key layout
+                                      for the batched kernel
 
 The probe window is not a knob: every probe visits one slot per step.  Windows of two and
 four consecutive slots per step were measured on the B300 (1280x720, depth 4: 117 and
@@ -40,6 +42,17 @@ TABLE_SPACE = {
 }
 BATCH_SPACE = {"insert_mode": (0, 1), "blocks_per_sm": (0, 3, 2), "update_blocks_per_sm": (0, 2),
                "query_blocks_per_sm": (0, 2)}
+
+# Fields of the table configuration a search space may hold beside the launch knobs: they lay
+# the table out differently (1: a dense key array, 2: keys inside the slot records), so each
+# candidate gets its own table; results do not depend on them either.
+CONFIG_KNOBS = ("key_layout",)
+
+
+def _split(knobs: dict) -> tuple[dict, dict]:
+    """(table-config fields, launch knobs) of a candidate."""
+    conf = {k: v for k, v in knobs.items() if k in CONFIG_KNOBS}
+    return conf, {k: v for k, v in knobs.items() if k not in CONFIG_KNOBS}
 
 
 def _time_ms(fn, iters: int) -> float:
@@ -106,8 +119,9 @@ def tune_table(cfg: _abi.Config, batches, P: int, D: int, space: dict | None = N
 
     for values in itertools.product(*(space[k] for k in keys)):
         knobs = dict(zip(keys, values))
-        t = Table(cfg)
-        t.set_launch(**knobs)
+        conf, launch = _split(knobs)
+        t = Table(_clone_config(cfg, **conf) if conf else cfg)
+        t.set_launch(**launch)
         for k in range(warmup):
             step(t, batches[k % len(batches)])
         ms = _time_ms(lambda k: step(t, batches[(warmup + k) % len(batches)]), iters)
@@ -145,18 +159,19 @@ def tune_capacity(cfg: _abi.Config, batches, P: int, D: int, extra_bits=(1, 2), 
 
 def tune_batch(make_entries, n_items: int, space: dict | None = None, warmup: int = 2, iters: int = 3,
                verify: bool = False) -> dict:
-    """Fastest batched-kernel knobs.  make_entries() must return fresh (table, vertices, out, P, D
-    [, slots]) entries (scratch tables) for each candidate; when the space holds
-    "capacity_bits", make_entries(capacity_bits) sizes each session's table at
-    2^(ceil(log2 V) + capacity_bits) slots."""
+    """Fastest batched-kernel knobs.  make_entries(**fields) must return fresh (table, vertices,
+    out, P, D [, slots]) entries (scratch tables) for each candidate; the space's table fields
+    are passed to it by name: "capacity_bits" (each session's table gets 2^(ceil(log2 V) +
+    capacity_bits) slots) and "key_layout" (where its keys live)."""
     space = space or BATCH_SPACE
     keys = list(space)
     results = []
     same = _Same(verify)
+    table_fields = ("capacity_bits",) + CONFIG_KNOBS
     for values in itertools.product(*(space[k] for k in keys)):
         knobs = dict(zip(keys, values))
-        bits = knobs.pop("capacity_bits", None)
-        entries = make_entries(bits) if bits is not None else make_entries()
+        fields = {k: knobs.pop(k) for k in table_fields if k in knobs}
+        entries = make_entries(**fields)
         b = Batch(n_items, **knobs)
         b.set(entries)
         for _ in range(warmup):
@@ -164,8 +179,7 @@ def tune_batch(make_entries, n_items: int, space: dict | None = None, warmup: in
         ms = _time_ms(lambda k: b.launch(), iters)
         if b.status() != 0:
             ms = float("inf")
-        if bits is not None:
-            knobs["capacity_bits"] = bits
+        knobs.update(fields)
         same([e[0] for e in entries], knobs)
         b.close()
         for e in entries:

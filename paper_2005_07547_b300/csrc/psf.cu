@@ -100,11 +100,17 @@ struct Layout {
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
-// Measured on the B300: with keys in the slot records an FP32 query reads key and
-// approximant from one sector (1280x720: 12.8 -> 13.4 G vertices/s at 2^22 slots); for 2^24
-// slots a dense 128 MB key array still partly stays in L2 while probes into 1 GB of records
-// all go to DRAM (1920x1080: 7.1 vs 6.25 G vertices/s); and an FP16 query reads the compact
-// copy, so its keys are best in the dense array beside it (12.95 vs 12.34 G vertices/s).
+// Where the keys live (no result depends on it), measured on the B300.  Keys inside the slot
+// records put a probe's key in the same 64-byte half of the record as the sums that its bulk
+// reduction adds to, so the insert touches one DRAM atom per group instead of two; a dense
+// key array packs four keys per sector, which keeps a probing query's key reads in L2 longer.
+// With the slot-cache calls (no key read in the query) the keys in the records win on every
+// workload measured: 1920x1080 with the FP16 copy 12.56 vs 12.41 G vertices/s, with FP32
+// 12.08 vs 11.51; 1280x720 FP16 17.34 vs 16.76; 64 batched sessions 13.92 vs 13.70.  With the
+// probing query (psf_query_cv, psf_step) the dense array wins at 2^24 slots (1920x1080 FP16:
+// 10.38 vs 9.65) and the records win for FP32 tables up to 2^22 slots (1280x720: 13.4 vs
+// 12.8).  The default (key_layout 0) follows the probing path, which needs no caller buffer;
+// callers of the slot-cache calls set 2, as the autotuner chooses for them.
 bool keys_inline(const psf_config* c) {
     if (c->payload == psf::kPayloadSH) return false;  // SH records have no key field
     return c->key_layout == 2 || (c->key_layout == 0 && c->log2_capacity <= 22 && !c->cache_fp16);

@@ -51,35 +51,38 @@ class Session:
     latencies_ms: list = field(default_factory=list)
 
 
-def table_config(req: dict, capacity_bits: int | None = None) -> _abi.Config:
+def table_config(req: dict, capacity_bits: int | None = None, key_layout: int = 0) -> _abi.Config:
     """A request's table: its own log2_capacity, or with capacity_bits (the load factor an
     autotuner chose) 2^(ceil(log2 V) + capacity_bits) slots for its V vertices per iteration;
-    the cell grid is the request's either way."""
+    the cell grid is the request's either way; key_layout as in psf_config (0: the library's
+    rule, 1: a dense key array, 2: keys inside the slot records)."""
     log2cap = req["log2_capacity"]
     if capacity_bits is not None:
         log2cap = max(4, int(math.ceil(math.log2(max(2, req["width"] * req["height"] * req["depth"]))))
                       + capacity_bits)
     return _abi.make_config(log2_capacity=log2cap, pos_bits=req["pos_bits"], dir_bits=req["dir_bits"],
-                            alpha_min=req["alpha_min"], cache_fp16=req.get("cache_fp16", True))
+                            alpha_min=req["alpha_min"], cache_fp16=req.get("cache_fp16", True), key_layout=key_layout)
 
 
-def table_bytes(req: dict, capacity_bits: int | None = None) -> int:
+def table_bytes(req: dict, capacity_bits: int | None = None, key_layout: int = 0) -> int:
     import ctypes
 
-    return int(_abi.load().psf_table_bytes(ctypes.byref(table_config(req, capacity_bits))))
+    return int(_abi.load().psf_table_bytes(ctypes.byref(table_config(req, capacity_bits, key_layout))))
 
 
 class Server:
     def __init__(self, vertex_source, budget_bytes: float = 60e9, max_live: int = _abi.MAX_BATCH,
                  mode: str = "batched", use_graph: bool = True, batch_knobs: dict | None = None,
                  on_retire=None, slot_cache: bool = True, capacity_bits: int | None = None,
-                 log_ticks: bool = False):
+                 log_ticks: bool = False, key_layout: int = 0):
         """vertex_source(request, iteration) -> (P*D, 16) float32 CUDA tensor of that iteration;
         on_retire(session), if given, sees each session (table still open) before it is freed;
         slot_cache: each session's insert notes its vertices' slots and its query reads them
         (psf_insert_slots / psf_query_cv_slots, or the batch item's slots), in both modes;
         capacity_bits: each session's table gets 2^(ceil(log2 V) + capacity_bits) slots (the
         load factor, e.g. autotune.tune_batch's choice) instead of its request's log2_capacity;
+        key_layout: where each session's table keeps its keys (psf_config.key_layout, e.g. the
+        tuner's choice);
         log_ticks: keep, per completed tick, its device time and the (request, iteration, log2
         capacity) of every session it ran (`tick_log`, for a roofline of the served form)."""
         if mode not in ("batched", "plain"):
@@ -100,6 +103,7 @@ class Server:
         self.on_retire = on_retire
         self.slot_cache = slot_cache
         self.capacity_bits = capacity_bits
+        self.key_layout = key_layout
         self._inflight: deque = deque()  # (start event, end event(s), sessions, retiring sessions, items)
         self.tick_log: list | None = [] if log_ticks else None
 
@@ -110,12 +114,12 @@ class Server:
         changed = False
         while queue and len(self.live) < self.max_live:
             req = queue[0]
-            need = table_bytes(req, self.capacity_bits)
+            need = table_bytes(req, self.capacity_bits, self.key_layout)
             if self.used + need > self.budget:
                 break
             queue.popleft()
             P, D = req["width"] * req["height"], req["depth"]
-            t = Table(table_config(req, self.capacity_bits))
+            t = Table(table_config(req, self.capacity_bits, self.key_layout))
             out = self._empty((P * D, 3), torch.float32)
             slots = self._empty((P * D,), torch.int32) if self.slot_cache else None
             self.live.append(Session(req, t, out, P, D, req["arrival_s"], now, slots))

@@ -33,6 +33,10 @@ def test_every_table_candidate_gives_identical_tables(psf_mod, fp16):
     n = int(np.prod([len(v) for v in autotune.TABLE_SPACE.values()]))
     assert res["verified"] == len(res["all"]) == n
     assert res["best"] in [{k: r[k] for k in autotune.TABLE_SPACE} for r in res["all"]]
+    # the key layout is a table field: each candidate gets a table laid out its way
+    res = autotune.tune_table(cfg, batches, P, D, space={"key_layout": (1, 2), "query_layout": (0, 1)}, warmup=2,
+                              iters=2, verify=True, slot_cache=True)
+    assert res["verified"] == len(res["all"]) == 4 and res["best"]["key_layout"] in (1, 2)
     cap = autotune.tune_capacity(cfg, batches, P, D, extra_bits=(1, 2, 3), verify=True)
     assert cap["verified"] == 3 and cap["best"] in [r["log2_capacity"] for r in cap["all"]]
 
@@ -54,13 +58,13 @@ def test_every_batch_candidate_gives_identical_tables(psf_mod):
     outs = [torch.empty((d.shape[0], 3), device="cuda") for d in data]
     slots = [torch.empty(d.shape[0], dtype=torch.int32, device="cuda") for d in data]
 
-    def make(bits=1):
+    def make(capacity_bits=1, key_layout=0):
         tables = []
         for s in sessions:
             V = s["width"] * s["height"] * s["depth"]
             tables.append(psf_mod.Table(psf_mod.make_config(
-                log2_capacity=int(math.ceil(math.log2(V))) + bits, pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
-                alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"])))
+                log2_capacity=int(math.ceil(math.log2(V))) + capacity_bits, pos_bits=s["pos_bits"],
+                dir_bits=s["dir_bits"], alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"], key_layout=key_layout)))
         return [(tables[k], data[k], outs[k], s["width"] * s["height"], s["depth"], slots[k])
                 for k, s in enumerate(sessions)]
 
@@ -70,3 +74,8 @@ def test_every_batch_candidate_gives_identical_tables(psf_mod):
     assert res["verified"] == len(res["all"]) == n
     assert all(math.isfinite(r["ms"]) for r in res["all"])
     assert "capacity_bits" in res["best"]
+    # the key layout as a table field of the search, with the load factor
+    space = {"capacity_bits": (1, 2), "key_layout": (1, 2)}
+    res = autotune.tune_batch(make, len(sessions), space=space, verify=True)
+    assert res["verified"] == len(res["all"]) == 4
+    assert {(r["capacity_bits"], r["key_layout"]) for r in res["all"]} == {(1, 1), (1, 2), (2, 1), (2, 2)}

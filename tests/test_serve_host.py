@@ -102,7 +102,7 @@ def fakes(monkeypatch):
     monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
     monkeypatch.setattr(serve, "Table", FakeTable)
     monkeypatch.setattr(serve, "Batch", FakeBatch)
-    monkeypatch.setattr(serve, "table_bytes", lambda req, bits=None: 1000 * req["log2_capacity"])
+    monkeypatch.setattr(serve, "table_bytes", lambda req, bits=None, key_layout=0: 1000 * req["log2_capacity"])
     yield
 
 
