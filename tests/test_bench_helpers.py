@@ -27,11 +27,12 @@ def test_committed_traffic_applies_to_its_own_setup_only():
         assert bench.load_traffic("k_insert", False, {}) is None  # stale counters are never used
         return
     cap = d["captures"][0]
-    setup = {k: cap[k] for k in ("workload", "cache", "levels", "log2_capacity", "slot_cache")}
+    setup = {k: cap[k] for k in ("workload", "cache", "levels", "log2_capacity", "slot_cache", "key_layout")}
     got = bench.load_traffic("k_insert", False, setup)
     assert got == cap["kernels"]["k_insert"]["bytes_per_launch"] and got > 0
     for key, other in (("workload", "64x64_d3"), ("cache", "other"), ("levels", 7), ("log2_capacity", 3),
-                       ("slot_cache", not setup["slot_cache"])):
+                       ("slot_cache", not setup["slot_cache"]),
+                       ("key_layout", {"inline": "dense", "dense": "inline"}[setup["key_layout"]])):
         assert bench.load_traffic("k_insert", False, dict(setup, **{key: other})) is None, key
     # the staged insert is a different kernel: only its own capture counts
     assert bench.load_traffic("k_insert", True, setup) == cap["kernels"].get("k_insert_staged", {}).get("bytes_per_launch")
