@@ -1,9 +1,10 @@
 """Full-size serving parity: Poisson arrivals at 200 per second for half a second (about 100
 render sessions of 16..128 iterations, width log-uniform 128..1280, 16:9, depth 2..6, each
 at its own size with two generated inputs that its iterations alternate), a 60 GB table
-budget, the continuous-batching server with its CUDA graph and slot cache.  Every
-finished session's table and last outputs equal, bit for bit, those of the same session
-run alone through plain psf_step calls; four sessions spread over the size range are also
+budget, the continuous-batching server with its CUDA graph, slot cache and the keys in the
+slot records (the benchmark's served configuration).  Every finished session's table and
+last outputs equal, bit for bit, those of the same session run alone through plain psf_step
+calls on a table with the library's default key layout; four sessions spread over the size range are also
 checked against the oracle over all their iterations (spawned workers)."""
 
 import hashlib
@@ -51,7 +52,8 @@ def test_served_sessions_at_full_size_equal_alone_and_oracle(psf_mod, oracle_mod
         if r["name"] in picked:
             keep[r["name"]] = {"table": rec, "out": fullsize.sample_out(sess.out, sess.P, sess.D, STRIDE)}
 
-    srv = Server(source, budget_bytes=60e9, mode="batched", use_graph=True, on_retire=on_retire, slot_cache=True)
+    srv = Server(source, budget_bytes=60e9, mode="batched", use_graph=True, on_retire=on_retire, slot_cache=True,
+                 key_layout=2)
     rep = srv.run(reqs, duration_s=ARRIVALS_S, drain=True)
     srv.close()
     print({k: rep[k] for k in ("ticks", "vertices", "vertices_per_s", "sessions_finished", "iteration_latency_ms")})

@@ -2,8 +2,8 @@
 (width log-uniform 128..1280, 16:9, depth 2..6, 2^(ceil(log2 V) + 1) slots each, FP16
 query copy; about 46 M vertices per iteration), 3 iterations of one fused persistent
 launch each, captured once in a CUDA graph and replayed with the descriptors re-set
-between iterations, with the autotuner's knobs and the slot cache -- the configuration
-the benchmark times.  After every iteration every session's table and the
+between iterations, with the autotuner's knobs and key layout and the slot cache -- the
+configuration the benchmark times.  After every iteration every session's table and the
 control-variate outputs of every 16th path are compared with that session's own oracle
 (spawned workers, one session each)."""
 
@@ -28,9 +28,9 @@ def test_64_batched_sessions_each_against_its_oracle(psf_mod, oracle_mod):
     sessions = session_workloads(64)
     shape = [(s["width"] * s["height"], s["depth"]) for s in sessions]
 
-    def cfg_of(s):
+    def cfg_of(s, key_layout=0):
         return psf_mod.make_config(log2_capacity=s["log2_capacity"], pos_bits=s["pos_bits"], dir_bits=s["dir_bits"],
-                                   alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"])
+                                   alpha_min=s["alpha_min"], cache_fp16=s["cache_fp16"], key_layout=key_layout)
 
     data = {0: [torch.from_numpy(v).cuda() for v in fullsize.session_iterations(sessions, 0)]}
     outs = [torch.empty((P * D, 3), dtype=torch.float32, device="cuda") for P, D in shape]
@@ -39,9 +39,12 @@ def test_64_batched_sessions_each_against_its_oracle(psf_mod, oracle_mod):
     def entries(tables, it):
         return [(tables[k], data[it][k], outs[k], P, D, slots[k]) for k, (P, D) in enumerate(shape)]
 
-    tuned = autotune.tune_batch(lambda: entries([psf_mod.Table(cfg_of(s)) for s in sessions], 0), len(sessions))
-    tables = [psf_mod.Table(cfg_of(s)) for s in sessions]
-    batch = psf_mod.Batch(len(sessions), **tuned["best"])
+    tuned = autotune.tune_batch(lambda key_layout=0: entries([psf_mod.Table(cfg_of(s, key_layout)) for s in sessions], 0),
+                                len(sessions), space={**autotune.BATCH_SPACE, "key_layout": (1, 2)})
+    knobs = dict(tuned["best"])
+    layout = knobs.pop("key_layout")
+    tables = [psf_mod.Table(cfg_of(s, layout)) for s in sessions]
+    batch = psf_mod.Batch(len(sessions), **knobs)
     batch.set(entries(tables, 0))
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
