@@ -414,8 +414,7 @@ int psf_batch_destroy(psf_batch* b);
  *   - n > PSF_NOALLOC_MAX_ITEMS returns PSF_ERR_TOO_MANY (with a message in
  *     psf_last_cuda_error) and enqueues nothing; n = 0 is a no-op.
  *   - The first call on a device resolves the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call before any
- *     stream capture.
+ *     (cudaGetSymbolAddress) with that device current.
  *   - Every call on a device shares the one array: the barrier words and the status are
  *     cleared at the start of each call, the descriptors overwritten.  Calls whose work
  *     could overlap on the GPU (different streams without ordering between them) race on
