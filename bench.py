@@ -259,10 +259,14 @@ class ClockSampler:
                 "power_w_max": max(s[2] for s in self.samples), "source": "NVML (libnvidia-ml), 1 ms"}
 
 
-def atomic_probe_rates(modes=(0, 1, 2, 3, 4, 5), n_words: int = 1 << 25, reps: int = 3, n_distinct: int = 0) -> dict:
+def atomic_probe_rates(modes=(0, 1, 2, 3, 4, 5), n_words: int = 1 << 25, reps: int = 3, n_distinct: int = 0,
+                       n_groups: int = 0) -> dict:
     """Measured L2 64-bit atomic throughput (ops/s) on this GPU, per probe mode, on a buffer of
     n_words 64-bit words (2^25 words = 256 MB, larger than L2, like a 2^22-slot table).  With
-    n_distinct > 0 the sector patterns (modes 2, 4, 5) target that many fixed random sectors."""
+    n_distinct > 0 the sector patterns (modes 2, 4, 5) target that many fixed random sectors;
+    n_groups > 0 sets how many groups one launch issues (else 2^24 for the sector patterns,
+    2^26 for the others), so that a launch can match a kernel's own count of groups over its
+    own distinct sectors (the same reuse of each sector, hence the same share of L2 hits)."""
     import ctypes
 
     import torch
@@ -282,7 +286,7 @@ def atomic_probe_rates(modes=(0, 1, 2, 3, 4, 5), n_words: int = 1 << 25, reps: i
     names = {0: "red_random_u64", 1: "atom_random_u64", 2: "insert_pattern_4red_1or", 3: "red_warp_contended_u64",
              4: "insert_pattern_bulk32_1or", 5: "bulk32_only"}
     for mode in modes:
-        groups = (1 << 24) if mode in (2, 4, 5) else (1 << 26)
+        groups = int(n_groups) if n_groups > 0 else ((1 << 24) if mode in (2, 4, 5) else (1 << 26))
         ops_per_group = 5 if mode in (2, 4, 5) else 1
         args = (buf.data_ptr(), n_words, groups, n_distinct, mode, sms * 8, stream.cuda_stream)
         if lib.atomic_probe(*args) != 0:
@@ -701,21 +705,28 @@ def run_psf(args) -> None:
     achieved = alg[dominant] / (avg[dominant] / 1e3) / 1e9
     # atomic roofline of the insert: one update of a random 32-byte sector per (warp, key)
     # group plus one bitmap reduction, against the probe's rate for the same pattern on a
-    # buffer the size of the table's slot records with the insert's footprint (targets drawn
-    # from as many fixed random sectors as the insert touches cells); mode 4: the sums as one
-    # bulk reduction, the default; mode 2: as four 64-bit reductions
+    # buffer the size of the table's slot records with the insert's footprint: as many groups
+    # per launch as the insert issues, on as many fixed random sectors as it touches cells;
+    # mode 4: the sums as one bulk reduction, the default; mode 2: as four 64-bit reductions.
+    # The probe at its fixed 2^24 groups (more visits per sector, so more L2 hits) is kept
+    # beside it for comparison with earlier lines.
     probe_words = 8 << log2cap
     mode = 4 if args.sum_reduction == 0 else 2
     pname = {4: "insert_pattern_bulk32_1or", 2: "insert_pattern_4red_1or"}[mode]
-    probe = (atomic_probe_rates(modes=(mode,), n_words=probe_words, n_distinct=max(1, int(touched)))
-             if rank == 0 and not sh else {})
+    run_probe = rank == 0 and not sh
+    probe = (atomic_probe_rates(modes=(mode,), n_words=probe_words, n_distinct=max(1, int(touched)),
+                                n_groups=max(1, int(leaders)), reps=5) if run_probe else {})
+    probe_fixed = (atomic_probe_rates(modes=(mode,), n_words=probe_words, n_distinct=max(1, int(touched)))
+                   if run_probe else {})
     peak_groups = probe[pname] / 5.0 if probe else float("nan")
     group_rate = leaders / (avg["k_insert"] / 1e3)
     atomic_roofline = {"kernel": "k_insert", "achieved": group_rate / 1e9, "unit": "G groups/s",
                        "peak": peak_groups / 1e9, "frac": group_rate / peak_groups if probe else None,
                        "leader_groups_per_launch": leaders,
                        "peak_source": f"live probe: random 32-B sector, {'one bulk (TMA) reduction' if mode == 4 else '4 x red.add.u64'} + red.or, "
-                                      f"{int(touched)} distinct sectors of {probe_words * 8 / 1e6:.0f} MB (the touched cells of the slot records)"}
+                                      f"{int(leaders)} groups on {int(touched)} distinct sectors of "
+                                      f"{probe_words * 8 / 1e6:.0f} MB (the insert's groups and touched cells of the slot records)",
+                       "peak_fixed_2p24_groups": probe_fixed[pname] / 5.0 / 1e9 if probe_fixed else None}
     kernels = {k: {"avg_ms": avg[k], "share": avg[k] / sum(avg.values()),
                    "algorithmic_GBps": alg[k] / (avg[k] / 1e3) / 1e9,
                    "frac_of_hbm": alg[k] / (avg[k] / 1e3) / 1e9 / peaks["hbm_gbs"]} for k in avg}
@@ -986,7 +997,8 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
         for k, b in algorithmic_bytes(s["width"] * s["height"] * s["depth"], touched, bool(s["cache_fp16"]),
                                       bool(args.slot_cache)).items():
             bytes_phase[k] += b
-    probe = atomic_probe_rates(modes=(4,), n_words=slot_bytes // 8, n_distinct=max(1, int(touched_all)))
+    probe = atomic_probe_rates(modes=(4,), n_words=slot_bytes // 8, n_distinct=max(1, int(touched_all)),
+                               n_groups=max(1, int(groups)), reps=5)
     group_peak = probe["insert_pattern_bulk32_1or"] / 5.0
     hbm = peaks["hbm_gbs"] * 1e9
     floor_s = {"k_insert": max(bytes_phase["k_insert"] / hbm, groups / group_peak),
@@ -1006,8 +1018,8 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
                         "frac": total_bytes / step_s / hbm, "algorithmic_bytes_per_step": total_bytes,
                         "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"},
                 "l2_atomic": {"groups_per_step": groups, "probe_peak_G_groups_per_s": group_peak / 1e9,
-                              "peak_note": f"of measured (live probe: {int(touched_all)} distinct sectors of "
-                                           f"{slot_bytes / 1e9:.1f} GB)"}}
+                              "peak_note": f"of measured (live probe: {int(groups)} groups on {int(touched_all)} "
+                                           f"distinct sectors of {slot_bytes / 1e9:.1f} GB)"}}
 
     def rate(ms):
         return V * args.steps / (ms / 1e3)
@@ -1222,7 +1234,10 @@ def run_serving(args) -> None:
     slot_bytes = sum(sum(64 << c for _, _, c in t["items"]) for t in ticks) / max(1, len(ticks))
     touched = sum(sum(stats[(q["width"], q["depth"], it % n_iter)][0] for q, it, _ in t["items"]) for t in ticks) \
         / max(1, len(ticks))
-    probe = atomic_probe_rates(modes=(4,), n_words=max(1 << 20, int(slot_bytes) // 8), n_distinct=max(1, int(touched)))
+    groups_tick = sum(sum(stats[(q["width"], q["depth"], it % n_iter)][1] for q, it, _ in t["items"]) for t in ticks) \
+        / max(1, len(ticks))
+    probe = atomic_probe_rates(modes=(4,), n_words=max(1 << 20, int(slot_bytes) // 8), n_distinct=max(1, int(touched)),
+                               n_groups=max(1, int(groups_tick)), reps=5)
     group_peak = probe["insert_pattern_bulk32_1or"] / 5.0
     hbm = load_peaks()["hbm_gbs"] * 1e9
     for mode, rep in reports.items():
@@ -1232,8 +1247,9 @@ def run_serving(args) -> None:
                             "hbm+l2_atomic (sum over launches)",
                    "device_busy": rl["device_ms"] / 1e3 / rep["wall_s"] if rep["wall_s"] else None,
                    "peak_note": f"of measured (MEASURED_PEAKS.json hbm_gbs; live bulk-reduction probe "
-                                f"{group_peak / 1e9:.1f} G groups/s on the mean live footprint, "
-                                f"{int(touched)} distinct sectors of {slot_bytes / 1e9:.1f} GB)"})
+                                f"{group_peak / 1e9:.1f} G groups/s on a mean tick's groups and footprint, "
+                                f"{int(groups_tick)} groups on {int(touched)} distinct sectors of "
+                                f"{slot_bytes / 1e9:.1f} GB)"})
         rep["roofline"] = rl
     b, p = reports["batched"], reports["plain"]
     line = {
