@@ -1,0 +1,58 @@
+"""Full-size parity of the YCoCg two-band SH payload (Section "Basis functions and data
+structures: spatio-directional hashing", last paragraph): the 1280x720, depth-4 workload
+(3,686,400 vertices per iteration, 2^22 slots, the paper's 5-d key, ridge 0.01) over its
+first 8 iterations, in the launch configuration the benchmark's SH line times (the
+slot-cache insert, the blend with its 3x3 ridge solve, the slot-cache query).
+
+Every iteration the whole table is compared with the SH oracle after the blend (keys and
+c_old exactly, the six coefficients within the SH bound), the sixteen fixed-point sums
+after the insert on the first and the last iteration (exactly), and the control-variate
+outputs of every 16th path, all depths (within the SH bound)."""
+
+import numpy as np
+import pytest
+
+import fullsize
+from sh_parity import check_coef, check_cv_sh, check_sums, sh_pair, tol_sh
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+NAME, ITERATIONS, STRIDE, RIDGE = "1280x720_d4", 8, 16, 0.01
+
+
+def test_sh_payload_1280x720_depth4_full_size(psf_mod, oracle_mod):
+    import torch
+
+    from synth.scene import workload
+
+    w = workload(NAME)
+    P, D = w["width"] * w["height"], w["depth"]
+    cfg, table, ora = sh_pair(psf_mod, oracle_mod, w["log2_capacity"], w["pos_bits"], w["dir_bits"], RIDGE,
+                              alpha_min=w["alpha_min"])
+    tol = tol_sh(RIDGE)
+    slots = torch.empty(P * D, dtype=torch.int32, device="cuda")
+    out = torch.empty((P * D, 3), dtype=torch.float32, device="cuda")
+    worst = [0.0, 0.0]
+    for it, v in enumerate(fullsize.named_iterations(NAME, ITERATIONS)):
+        dv = torch.from_numpy(v).cuda()
+        table.insert_slots(dv, P, D, slots=slots)
+        st = ora.insert(v)
+        if it in (0, ITERATIONS - 1):
+            check_sums(table.export(), ora.export())
+        table.update()
+        ora.update()
+        worst[0] = max(worst[0], check_coef(table.export(), ora.export(), tol))
+        table.query_cv_slots(dv, slots, P, D, out=out)
+        vs, Ps = fullsize.sample_paths(v, P, D, STRIDE)
+        worst[1] = max(worst[1], check_cv_sh(oracle_mod, ora, fullsize.sample_out(out, P, D, STRIDE), vs, Ps, D,
+                                             float(cfg.beta), tol))
+        stats = table.stats()
+        assert stats["status"] == st == 0
+        assert (stats["dropped_vertices"], stats["zero_weight_vertices"]) == ora.counters()
+        assert stats["live_cells"] == len(ora) and stats["iterations"] == it + 1
+        print(f"iteration {it}: cells {len(ora)}, worst err/bound coefficients {worst[0]:.3g}, cv {worst[1]:.3g}")
+        del dv
+    # cells that see several normals use band 1
+    g = table.export()["coef"][:, 1:4]
+    assert np.mean(np.any(g != 0.0, axis=1)) > 0.1
+    table.close()
