@@ -109,6 +109,27 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6400.0, "source": "fallback"}
 
 
+class GroupRates:
+    """The bulk-reduction probe's sustained group rate (groups/s) on one table's footprint --
+    its slot records and its touched sectors -- memoised per footprint.  The fused kernel
+    hands out its warp units in session order, so at any moment its warps add into one or
+    two sessions' tables: each session's insert is bound by the rate its own footprint
+    allows (a small table stays in L2), not by a probe spread over all tables at once.  A
+    launch issues at least 2^22 groups so that the rate is a sustained one."""
+
+    def __init__(self, min_groups: int = 1 << 22):
+        self.memo: dict = {}
+        self.min_groups = min_groups
+
+    def __call__(self, slot_bytes: int, distinct: float, groups: float) -> float:
+        key = (int(slot_bytes), max(1, int(distinct)))
+        if key not in self.memo:
+            r = atomic_probe_rates(modes=(4,), n_words=key[0] // 8, n_distinct=key[1],
+                                   n_groups=max(int(groups), self.min_groups), reps=3)
+            self.memo[key] = r["insert_pattern_bulk32_1or"] / 5.0
+        return self.memo[key]
+
+
 def key_layout_of(cfg) -> str:
     """Where the library lays out a configuration's keys: "inline" (inside the 64-byte slot
     records) or "dense" (an 8-byte array beside them, which adds 8 bytes per slot to the table
@@ -984,32 +1005,33 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
     # per-iteration work of every session, counted by the plain tables (the batched kernel
     # does not count (warp, key) groups); every table ran warmup + steps identical iterations
     peaks = load_peaks()
+    hbm = peaks["hbm_gbs"] * 1e9
+    rates = GroupRates()
     bytes_phase = {"k_insert": 0.0, "k_update": 0.0, "k_query": 0.0}
-    groups = touched_all = 0.0
+    insert_floor = groups = touched_all = 0.0
     slot_bytes = 0
     for i, s in enumerate(sessions):
         st = plain_tables[i].stats()
         its = max(1, st["iterations"])
         touched = st["touched_cells"] / its
-        groups += st["leader_groups"] / its
+        g = st["leader_groups"] / its
+        groups += g
         touched_all += touched
-        slot_bytes += 64 << int(plain_tables[i].cfg.log2_capacity)
-        for k, b in algorithmic_bytes(s["width"] * s["height"] * s["depth"], touched, bool(s["cache_fp16"]),
-                                      bool(args.slot_cache)).items():
-            bytes_phase[k] += b
-    probe = atomic_probe_rates(modes=(4,), n_words=slot_bytes // 8, n_distinct=max(1, int(touched_all)),
-                               n_groups=max(1, int(groups)), reps=5)
-    group_peak = probe["insert_pattern_bulk32_1or"] / 5.0
-    hbm = peaks["hbm_gbs"] * 1e9
-    floor_s = {"k_insert": max(bytes_phase["k_insert"] / hbm, groups / group_peak),
-               "k_update": bytes_phase["k_update"] / hbm, "k_query": bytes_phase["k_query"] / hbm}
+        sb = 64 << int(plain_tables[i].cfg.log2_capacity)
+        slot_bytes += sb
+        b = algorithmic_bytes(s["width"] * s["height"] * s["depth"], touched, bool(s["cache_fp16"]), bool(args.slot_cache))
+        for k in bytes_phase:
+            bytes_phase[k] += b[k]
+        insert_floor += max(b["k_insert"] / hbm, g / rates(sb, touched, g))
+    floor_s = {"k_insert": insert_floor, "k_update": bytes_phase["k_update"] / hbm,
+               "k_query": bytes_phase["k_query"] / hbm}
     step_s = t_batch / args.steps / 1e3
     total_bytes = sum(bytes_phase.values())
     setup = {"workload": f"sessions_{len(sessions)}", "slot_cache": bool(args.slot_cache), "capacity_bits": bits,
              "batch_knobs": knobs}
     if layout:
         setup["key_layout"] = {1: "dense", 2: "inline"}[layout]
-    roofline = {"kernel": "k_batch", "bound": "hbm+l2_atomic (phase sum)",
+    roofline = {"kernel": "k_batch", "bound": "hbm+l2_atomic (phase sum, insert per session)",
                 "frac": sum(floor_s.values()) / step_s,
                 "traffic": load_traffic("k_batch", False, setup),
                 "algorithmic_bytes_per_launch": total_bytes,
@@ -1017,9 +1039,11 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
                 "hbm": {"achieved": total_bytes / step_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": total_bytes / step_s / hbm, "algorithmic_bytes_per_step": total_bytes,
                         "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"},
-                "l2_atomic": {"groups_per_step": groups, "probe_peak_G_groups_per_s": group_peak / 1e9,
-                              "peak_note": f"of measured (live probe: {int(groups)} groups on {int(touched_all)} "
-                                           f"distinct sectors of {slot_bytes / 1e9:.1f} GB)"}}
+                "l2_atomic": {"groups_per_step": groups, "touched_per_step": touched_all, "slot_bytes": slot_bytes,
+                              "probes": len(rates.memo),
+                              "peak_note": "of measured (live bulk-reduction probe per session on its own slot "
+                                           "records and touched sectors; the insert floor sums each session's "
+                                           "max(bytes at the HBM rate, groups at its probe rate))"}}
 
     def rate(ms):
         return V * args.steps / (ms / 1e3)
@@ -1164,32 +1188,25 @@ def template_stats(src: "TemplateSource", reqs: list[dict]) -> dict:
     return out
 
 
-def served_roofline(tick_log: list, stats: dict, n_iter: int, hbm_bps: float, group_peak: float,
-                    fused: bool, slot_cache: bool) -> dict:
-    """Roofline of a served run from its completed ticks.  A tick's floor: fused (one kernel,
-    phases back to back) the sum over phases of that phase's floor over the tick's sessions;
-    plain (three kernels per session) the sum of every launch's own floor.  A phase's floor is
-    its algorithmic bytes at the HBM rate, and for the insert at least its (warp, key) groups at
-    the bulk-reduction probe's rate.  frac = total floor / total device time of the ticks;
-    device_busy = device time over the wall time is reported by the caller."""
+def served_roofline(tick_log: list, stats: dict, n_iter: int, hbm_bps: float, rate_of,
+                    slot_cache: bool) -> dict:
+    """Roofline of a served run from its completed ticks.  A tick's floor is the sum over its
+    sessions of each session's insert floor -- the larger of its algorithmic bytes at the HBM
+    rate and its (warp, key) groups at the bulk-reduction probe's rate on its own footprint,
+    rate_of(slot_bytes, touched, groups) -- and its blend and query bytes at the HBM rate.
+    It is the same for the fused kernel (which takes the sessions one after the other in each
+    phase) and the plain launches.  frac = total floor / total device time of the ticks;
+    the caller reports device_busy = device time over the wall time."""
     floor = dev_ms = total_bytes = groups_all = 0.0
     for tick in tick_log:
         dev_ms += tick["ms"]
-        ph = {"k_insert": 0.0, "k_update": 0.0, "k_query": 0.0}
-        groups = 0.0
-        for req, it, _ in tick["items"]:
+        for req, it, log2cap in tick["items"]:
             touched, g = stats[(req["width"], req["depth"], it % n_iter)]
             b = algorithmic_bytes(req["width"] * req["height"] * req["depth"], touched, True, slot_cache)
-            if fused:
-                for k in ph:
-                    ph[k] += b[k]
-                groups += g
-            else:
-                floor += max(b["k_insert"] / hbm_bps, g / group_peak) + (b["k_update"] + b["k_query"]) / hbm_bps
+            floor += max(b["k_insert"] / hbm_bps, g / rate_of(64 << log2cap, touched, g)) \
+                + (b["k_update"] + b["k_query"]) / hbm_bps
             total_bytes += sum(b.values())
             groups_all += g
-        if fused:
-            floor += max(ph["k_insert"] / hbm_bps, groups / group_peak) + (ph["k_update"] + ph["k_query"]) / hbm_bps
     dev_s = dev_ms / 1e3
     return {"frac": floor / dev_s if dev_s > 0 else None, "floor_ms": 1e3 * floor, "device_ms": dev_ms,
             "ticks": len(tick_log), "algorithmic_bytes": total_bytes, "groups": groups_all,
@@ -1227,29 +1244,18 @@ def run_serving(args) -> None:
         torch.cuda.synchronize()
         reports[mode] = rep
     # the rooflines (untimed): every template iteration's touched cells and groups, and the
-    # bulk-reduction probe on the batched run's mean live footprint
+    # bulk-reduction probe on each session footprint the trace ran
     stats = template_stats(src, reqs)
     n_iter = len(next(iter(templates.values())))
-    ticks = logs["batched"] or logs["plain"]
-    slot_bytes = sum(sum(64 << c for _, _, c in t["items"]) for t in ticks) / max(1, len(ticks))
-    touched = sum(sum(stats[(q["width"], q["depth"], it % n_iter)][0] for q, it, _ in t["items"]) for t in ticks) \
-        / max(1, len(ticks))
-    groups_tick = sum(sum(stats[(q["width"], q["depth"], it % n_iter)][1] for q, it, _ in t["items"]) for t in ticks) \
-        / max(1, len(ticks))
-    probe = atomic_probe_rates(modes=(4,), n_words=max(1 << 20, int(slot_bytes) // 8), n_distinct=max(1, int(touched)),
-                               n_groups=max(1, int(groups_tick)), reps=5)
-    group_peak = probe["insert_pattern_bulk32_1or"] / 5.0
+    rates = GroupRates()
     hbm = load_peaks()["hbm_gbs"] * 1e9
     for mode, rep in reports.items():
-        rl = served_roofline(logs[mode], stats, n_iter, hbm, group_peak, mode == "batched", bool(args.slot_cache))
+        rl = served_roofline(logs[mode], stats, n_iter, hbm, rates, bool(args.slot_cache))
         rl.update({"kernel": "k_batch" if mode == "batched" else "k_insert + k_update + k_query per session",
-                   "bound": "hbm+l2_atomic (phase sum per tick)" if mode == "batched" else
-                            "hbm+l2_atomic (sum over launches)",
+                   "bound": "hbm+l2_atomic (sum over each tick's sessions)",
                    "device_busy": rl["device_ms"] / 1e3 / rep["wall_s"] if rep["wall_s"] else None,
-                   "peak_note": f"of measured (MEASURED_PEAKS.json hbm_gbs; live bulk-reduction probe "
-                                f"{group_peak / 1e9:.1f} G groups/s on a mean tick's groups and footprint, "
-                                f"{int(groups_tick)} groups on {int(touched)} distinct sectors of "
-                                f"{slot_bytes / 1e9:.1f} GB)"})
+                   "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs; live bulk-reduction probe on each "
+                                f"session footprint: {len(rates.memo)} probes)"})
         rep["roofline"] = rl
     b, p = reports["batched"], reports["plain"]
     line = {

@@ -76,27 +76,45 @@ def test_capture_with_its_own_sources_is_keyed_to_them(tmp_path, monkeypatch):
 
 
 def test_served_roofline_floors():
-    """The served form's floor per tick: fused, the phase sums over the tick's sessions; plain,
-    the sum of every launch's own floor (never below the fused one)."""
+    """The served form's floor per tick: the sum over the tick's sessions of each one's insert
+    floor (bytes at the HBM rate or groups at the probe rate of its own footprint, whichever
+    is larger) and its blend and query bytes at the HBM rate."""
     a = dict(width=4, height=2, depth=2)  # V = 16
     b = dict(width=8, height=2, depth=1)  # V = 16
     stats = {(4, 2, 0): (10, 1000), (4, 2, 1): (12, 1000), (8, 1, 0): (6, 2), (8, 1, 1): (6, 2)}
-    log = [{"ms": 2.0, "items": [(a, 0, 8), (b, 0, 8)]}, {"ms": 1.0, "items": [(a, 3, 8)]}]
-    hbm, gp = 1e3, 1e3  # bytes/s, groups/s
-    fused = bench.served_roofline(log, stats, 2, hbm, gp, True, True)
-    plain = bench.served_roofline(log, stats, 2, hbm, gp, False, True)
+    log = [{"ms": 2.0, "items": [(a, 0, 8), (b, 0, 9)]}, {"ms": 1.0, "items": [(a, 3, 8)]}]
+    hbm = 1e3  # bytes/s
+    seen = []
+
+    def rate_of(slot_bytes, touched, groups):
+        seen.append((slot_bytes, touched, groups))
+        return 1e3 if slot_bytes == 64 << 8 else 4e3
+
+    r = bench.served_roofline(log, stats, 2, hbm, rate_of, True)
 
     def ab(V, C):
         return bench.algorithmic_bytes(V, C, True, True)
 
-    a0, b0, a1 = ab(16, 10), ab(16, 6), ab(16, 12)
-    t0 = max((a0["k_insert"] + b0["k_insert"]) / hbm, 1002 / gp) + (a0["k_update"] + b0["k_update"] + a0["k_query"]
-                                                                   + b0["k_query"]) / hbm
-    t1 = max(a1["k_insert"] / hbm, 1000 / gp) + (a1["k_update"] + a1["k_query"]) / hbm
-    assert fused["floor_ms"] == pytest.approx(1e3 * (t0 + t1))
-    assert fused["frac"] == pytest.approx((t0 + t1) / 3e-3)
-    p0 = (max(a0["k_insert"] / hbm, 1000 / gp) + (a0["k_update"] + a0["k_query"]) / hbm
-          + max(b0["k_insert"] / hbm, 2 / gp) + (b0["k_update"] + b0["k_query"]) / hbm)
-    assert plain["floor_ms"] == pytest.approx(1e3 * (p0 + t1))
-    assert plain["floor_ms"] >= fused["floor_ms"]
-    assert fused["groups"] == plain["groups"] == 2002 and fused["device_ms"] == 3.0
+    def one(x, g, rate):
+        return max(x["k_insert"] / hbm, g / rate) + (x["k_update"] + x["k_query"]) / hbm
+
+    want = one(ab(16, 10), 1000, 1e3) + one(ab(16, 6), 2, 4e3) + one(ab(16, 12), 1000, 1e3)
+    assert r["floor_ms"] == pytest.approx(1e3 * want)
+    assert r["frac"] == pytest.approx(want / 3e-3)
+    assert r["groups"] == 2002 and r["device_ms"] == 3.0 and r["ticks"] == 2
+    assert seen == [(64 << 8, 10, 1000), (64 << 9, 6, 2), (64 << 8, 12, 1000)]
+
+
+def test_group_rates_probe_each_footprint_once(monkeypatch):
+    calls = []
+
+    def fake_probe(modes, n_words, n_distinct, n_groups, reps):
+        calls.append((n_words, n_distinct, n_groups))
+        return {"insert_pattern_bulk32_1or": 5.0 * n_words}
+
+    monkeypatch.setattr(bench, "atomic_probe_rates", fake_probe)
+    rates = bench.GroupRates()
+    assert rates(8 * 1024, 10.4, 5) == 1024.0
+    assert rates(8 * 1024, 10.9, 7e6) == 1024.0  # same footprint: memoised
+    assert rates(8 * 2048, 3, 5) == 2048.0
+    assert calls == [(1024, 10, 1 << 22), (2048, 3, 1 << 22)]
