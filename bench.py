@@ -899,9 +899,10 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
     against the plain per-session loop (three launches per session), eager and
     graph-captured, on the same resident iterations.  The fused kernel's roofline: its
     phases run back to back, so its floor is the sum of each phase's own floor over all
-    sessions (insert: the larger of its algorithmic bytes at the measured HBM rate and its
-    (warp, key) groups at the live bulk-reduction probe's rate on the sessions' footprint;
-    blend and query: their algorithmic bytes at the HBM rate), against the measured step."""
+    sessions (insert: per session, the larger of its algorithmic bytes at the measured HBM
+    rate and its (warp, key) groups at the bulk-reduction probe's rate on its own footprint,
+    since the phase takes the sessions in order; blend and query: their algorithmic bytes at
+    the HBM rate), against the measured step."""
     import torch
 
     import paper_2005_07547_b300 as psf
@@ -955,6 +956,9 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
         bits = args.capacity_bits
         layout = args.key_layout
     tables = [psf.Table(cfg_of(s, bits, layout)) for s in sessions]
+    if args.sum_reduction:  # the sessions' sum path (the fused kernel reads it from each table)
+        for t in tables:
+            t.set_launch(sum_reduction=args.sum_reduction)
     batches = [psf.Batch(len(sessions), **knobs) for _ in range(pool)]
     for it, b in enumerate(batches):
         b.set(entries(tables, it))
@@ -984,6 +988,8 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
     status = max(b.status() for b in batches)
 
     plain_tables = [psf.Table(cfg_of(s, bits, layout)) for s in sessions]
+    for t in plain_tables if args.sum_reduction else ():
+        t.set_launch(sum_reduction=args.sum_reduction)
 
     def plain(k):
         for i, s in enumerate(sessions):
@@ -991,6 +997,8 @@ def measure_sessions(args, gen: dict, local: int, tune: bool = True) -> dict:
 
     t_plain, per_plain = timed(plain, args.warmup, args.steps)
     graph_tables = [psf.Table(cfg_of(s, bits, layout)) for s in sessions]
+    for t in graph_tables if args.sum_reduction else ():
+        t.set_launch(sum_reduction=args.sum_reduction)
     plain_graphs = []
     for it in range(pool):
         g = torch.cuda.CUDAGraph()
