@@ -349,7 +349,7 @@ def generate(name: str, iterations: list[int], procs: int) -> list[np.ndarray]:
 # ---------------------------------------------------------------------------
 
 def run_reference(args) -> None:
-    rank, world, _ = dist_env()
+    rank, _, _ = dist_env()
     if rank != 0:
         return
     from synth.scene import workload

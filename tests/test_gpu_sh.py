@@ -21,7 +21,7 @@ def test_sh_payload_64x64_all_iterations(psf_mod, oracle_mod, ridge, insert_mode
     w = workload("64x64_d3")
     scene = make_scene(w["seed"])
     P, D = w["width"] * w["height"], w["depth"]
-    cfg, table, ora = sh_pair(psf_mod, oracle_mod, w["log2_capacity"], w["pos_bits"], w["dir_bits"], ridge,
+    _, table, ora = sh_pair(psf_mod, oracle_mod, w["log2_capacity"], w["pos_bits"], w["dir_bits"], ridge,
                             alpha_min=w["alpha_min"])
     table.set_launch(insert_mode=insert_mode)
     tol = tol_sh(ridge)
@@ -55,7 +55,7 @@ def test_sh_payload_ragged_crowded_cells(psf_mod, oracle_mod, n):
     v = random_vertices(rng, n, q=3, cells_per_axis=3, zero_weight_fraction=0.02)
     D = next((d for d in (4, 3, 2) if n % d == 0), 1)
     P = n // D
-    cfg, table, ora = sh_pair(psf_mod, oracle_mod, 14, 3, 2, 0.02, beta=0.75)
+    _, table, ora = sh_pair(psf_mod, oracle_mod, 14, 3, 2, 0.02, beta=0.75)
     tol = tol_sh(0.02)
     for it in range(3):
         vi = v if it % 2 == 0 else v[::-1].copy()
@@ -81,7 +81,7 @@ def test_sh_payload_reset_and_edge_vertices(psf_mod, oracle_mod):
             vertex((0.3, 0.3, 0.3), L=(1.0, np.nan, 1.0)), vertex((0.3, 0.3, 0.3), n=(0.6, 0.8, 0.0)),
             vertex((0.3, 0.3, 0.3), w=2.0, L=(16384.0, -16384.0, 0.0), n=(0.0, 0.6, 0.8))]
     v = stack(recs)
-    cfg, table, ora = sh_pair(psf_mod, oracle_mod, 8, 2, 1, 0.01)
+    _, table, ora = sh_pair(psf_mod, oracle_mod, 8, 2, 1, 0.01)
     for it in range(3):
         if it == 2:
             table.reset()
@@ -109,7 +109,6 @@ def test_sh_tables_are_rejected_where_the_payload_does_not_apply(psf_mod):
     t = psf_mod.Table(psf_mod.make_config(log2_capacity=10, payload=1))
     dv = torch.zeros((4, 16), dtype=torch.float32, device="cuda")
     out = torch.zeros((4, 3), dtype=torch.float32, device="cuda")
-    slots = torch.zeros(4, dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
     bad = _abi.PSF_ERR_INVALID_ARG
     assert lib.psf_insert_progressive(t.handle, dv.data_ptr(), 4, 1, 0, s) == bad

@@ -118,7 +118,7 @@ def test_cv_depth_limit_absent_cells_and_single_vertex_paths(oracle_mod):
 def test_biased_estimator_mean_matches_closed_form(oracle_mod, gamma):
     """BiasedEstimator: mean(gamma (L - t C_next) + C) = gamma mean(L) + (1 - gamma) I_h,
     with I_h = 2 pi / 33 from the cos^32 quadrature."""
-    mu, wq = _nodes()
+    _, wq = _nodes()
     o = _filled_oracle(oracle_mod, 1.0)
     rng = np.random.default_rng(6)
     t0 = np.outer(2.0 * math.pi * wq * K, np.ones(3))
