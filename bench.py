@@ -672,8 +672,10 @@ def run_psf(args) -> None:
                      "update_blocks_per_sm": (0, 2, 1), "query_layout": (0, 1)}
             if args.key_layout == 0 and not sh:
                 space["key_layout"] = (1, 2)
+            # 8 timed steps per candidate: the key layouts differ by about 1%, which fewer steps
+            # do not resolve from run to run
             res = autotune.tune_table(make_cfg(cache_fp16), dev[:min(6, len(dev))], P, D, space=space, warmup=2,
-                                      iters=4, slot_cache=bool(args.slot_cache))
+                                      iters=8, slot_cache=bool(args.slot_cache))
             best = dict(res["best"])
             layout = best.pop("key_layout", args.key_layout)
             tuned[cache_fp16] = {"best": {**base_knobs, **best}, "key_layout": layout, "best_ms": res["best_ms"],
