@@ -18,7 +18,11 @@ maps (exported in key order) must be identical, bit for bit.
 
 The probe window is not a knob: every probe visits one slot per step.  Windows of two and
 four consecutive slots per step were measured on the B300 (1280x720, depth 4: 117 and
-143 us against 112 us for the insert) and lost to the extra loads and registers.
+143 us against 112 us for the insert) and lost to the extra loads and registers.  The block
+shape is searched as the grid: resident blocks per SM per kernel (the *_blocks_per_sm knobs)
+set each kernel's resident warps; the threads per block stay 256, since 128-thread blocks
+with retuned caps were measured slower (1920x1080: blend 144 -> 152 us, query 202 -> 213 us;
+64 sessions 13.9 -> 13.6 G vertices/s).
 """
 
 from __future__ import annotations

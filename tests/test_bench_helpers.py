@@ -31,9 +31,13 @@ def test_committed_traffic_applies_to_its_own_setup_only():
     got = bench.load_traffic("k_insert", False, setup)
     assert got == cap["kernels"]["k_insert"]["bytes_per_launch"] and got > 0
     for key, other in (("workload", "64x64_d3"), ("cache", "other"), ("levels", 7), ("log2_capacity", 3),
-                       ("slot_cache", not setup["slot_cache"]),
-                       ("key_layout", {"inline": "dense", "dense": "inline"}[setup["key_layout"]])):
+                       ("slot_cache", not setup["slot_cache"])):
         assert bench.load_traffic("k_insert", False, dict(setup, **{key: other})) is None, key
+    # the other key layout reads its own capture, if there is one
+    other = {"inline": "dense", "dense": "inline"}[setup["key_layout"]]
+    twin = [c for c in d["captures"] if c.get("key_layout") == other and c["workload"] == setup["workload"]]
+    want = twin[0]["kernels"]["k_insert"]["bytes_per_launch"] if twin else None
+    assert bench.load_traffic("k_insert", False, dict(setup, key_layout=other)) == want
     # the staged insert is a different kernel: only its own capture counts
     assert bench.load_traffic("k_insert", True, setup) == cap["kernels"].get("k_insert_staged", {}).get("bytes_per_launch")
 
