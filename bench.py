@@ -679,7 +679,7 @@ def run_psf(args) -> None:
             best = dict(res["best"])
             layout = best.pop("key_layout", args.key_layout)
             tuned[cache_fp16] = {"best": {**base_knobs, **best}, "key_layout": layout, "best_ms": res["best_ms"],
-                                 "candidates": len(res["all"]), "space": "x".join(space)}
+                                 "candidates": len(res["all"]), "space": " x ".join(space)}
         return tuned[cache_fp16]
 
     def knobs_for(cache_fp16):
