@@ -74,3 +74,37 @@ def test_slots_of_dropped_vertices_fall_back_to_probing(psf_mod):
     cached.update()
     assert cached.query_cv(dv, P, D).cpu().numpy().tobytes() == cached.query_cv_slots(dv, slots, P, D).cpu().numpy().tobytes()
     cached.close()
+
+
+@pytest.mark.parametrize("over", [dict(), dict(cache_fp16=True), dict(key_layout=2, cache_fp16=True)])
+def test_query_before_the_update_reads_the_old_approximant(psf_mod, oracle_mod, over):
+    """The strictly unbiased order (Section "Temporal averaging" read with the control variate
+    of the previous iteration): insert, query, then update.  The query reads the approximant
+    blended up to the previous iteration (0 for a cell first touched now), through the probing
+    query and the slot cache alike, and the oracle queried in the same order agrees."""
+    import torch
+
+    w, batches = _workload_batches("64x64_d3", 4)
+    cfg = _cfg_for(psf_mod, w, **over)
+    P, D = w["width"] * w["height"], w["depth"]
+    plain, cached = psf_mod.Table(cfg), psf_mod.Table(cfg)
+    ora = _oracle_for(oracle_mod, cfg)
+    for k, v in enumerate(batches):
+        dv = torch.from_numpy(v).cuda()
+        plain.insert(dv)
+        slots = cached.insert_slots(dv, P, D)
+        a = plain.query_cv(dv, P, D).cpu().numpy()
+        b = cached.query_cv_slots(dv, slots, P, D).cpu().numpy()
+        assert a.tobytes() == b.tobytes()
+        ora.insert(v)
+        old = ora.lookup(v, P, D)
+        if k == 0:
+            assert not np.any(old)  # nothing blended yet: every cell reads 0
+        check_cv(b, ora.query_cv(v, P, D), v, old, P, D, float(cfg.beta), cfg.cv_max_depth, ora.export()["L"],
+                 fp16=bool(cfg.cache_fp16))
+        plain.update()
+        cached.update()
+        ora.update()
+        assert plain.export().tobytes() == cached.export().tobytes()
+    plain.close()
+    cached.close()
